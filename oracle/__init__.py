@@ -1,0 +1,214 @@
+"""CPU oracle of the PanDelos-plus hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, the smoke check and the CPU-baseline leg of the benchmark may
+import this package.  The product (the CUDA library and its binding) never
+does; the two share no code.
+
+The arithmetic lives in ``pd_oracle.c`` (plain C, compiled here with gcc);
+this module builds it and marshals numpy arrays through ctypes.  Every
+function follows the passage of the paper named in its docstring:
+
+* ``choose_k``     Eq. (4), read as the smallest k with 20^k >= total residues
+                   (PARITY UNPINNED: the paper prints no k for any dataset);
+* ``Profiles``     Eqs. (1)-(3) and Algorithm 1 (multiplicity vectors);
+* ``summin``       Eq. (5) numerator and denominator of one gene pair;
+* ``pair``         Algorithm 2 (S_ij, Best Hits of rows, Eq. (8)) and
+                   Algorithm 3 (Bidirectional Best Hits, Eq. (9)).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pd_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libpd_oracle.so")
+# A test may point the loader at another compiled copy (used to check that the
+# pins reject deliberately broken oracles).
+_LIB_OVERRIDE = os.environ.get("PD_ORACLE_LIB")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_ALPHABET, ERR_IDENTITY, ERR_OOM = 0, 1, 2, 3, 4
+
+
+def build(force: bool = False) -> str:
+    """Compile pd_oracle.c into a shared library (gcc, plain C11)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        lib = C.CDLL(_LIB_OVERRIDE if _LIB_OVERRIDE else build())
+        P, u8p, i64p, i32p, u32p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_int64), \
+            C.POINTER(C.c_int32), C.POINTER(C.c_uint32)
+        lib.orc_choose_k.restype = C.c_int
+        lib.orc_choose_k.argtypes = [C.c_uint64, C.c_int]
+        lib.orc_build.restype = P
+        lib.orc_build.argtypes = [u8p, C.c_uint64, i64p, C.c_uint32, C.c_int, C.POINTER(C.c_int)]
+        lib.orc_free.argtypes = [P]
+        lib.orc_mv_len.restype = C.c_uint32
+        lib.orc_mv_len.argtypes = [P, C.c_uint32]
+        lib.orc_La.restype = C.c_uint32
+        lib.orc_La.argtypes = [P, C.c_uint32]
+        lib.orc_mv_get.argtypes = [P, C.c_uint32, u8p, u32p]
+        lib.orc_summin.restype = C.c_int
+        lib.orc_summin.argtypes = [P, C.c_uint32, C.c_uint32, u32p, u32p]
+        lib.orc_pair_run.restype = P
+        lib.orc_pair_run.argtypes = [P, i32p, C.c_uint32, C.c_uint32, C.c_int]
+        lib.orc_pair_status.restype = C.c_int
+        lib.orc_pair_status.argtypes = [P]
+        lib.orc_pair_free.argtypes = [P]
+        lib.orc_pair_sizes.argtypes = [P, u32p, u32p, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64),
+                                       C.POINTER(C.c_uint64)]
+        lib.orc_pair_matrix.argtypes = [P, u32p, u32p]
+        lib.orc_pair_row_bh.argtypes = [P, i64p, i32p, u32p, u32p]
+        lib.orc_pair_col_bh.argtypes = [P, i64p, i32p, u32p, u32p]
+        lib.orc_pair_bbh.argtypes = [P, i32p, i32p]
+        _lib = lib
+        return lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"oracle {what} failed with status {code}")
+        self.code = code
+
+
+def choose_k(total_residues: int, alphabet: int = 20) -> int:
+    """Eq. (4) reading: smallest k with alphabet**k >= total residues."""
+    return int(_load().orc_choose_k(int(total_residues), int(alphabet)))
+
+
+class Profiles:
+    """Multiplicity vectors of every gene of a dataset (Algorithm 1)."""
+
+    def __init__(self, residues: np.ndarray, gene_ptr: np.ndarray, k: int):
+        lib = _load()
+        self._res = np.ascontiguousarray(residues, dtype=np.uint8)
+        self._gptr = np.ascontiguousarray(gene_ptr, dtype=np.int64)
+        self.k = int(k)
+        self.n_genes = int(self._gptr.shape[0] - 1)
+        st = C.c_int(0)
+        res = self._res if self._res.size else np.zeros(1, np.uint8)
+        self._h = lib.orc_build(_ptr(res, C.c_uint8), self._res.size, _ptr(self._gptr, C.c_int64),
+                                self.n_genes, self.k, C.byref(st))
+        if not self._h:
+            raise OracleError(st.value, "build")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_free(h)
+            self._h = None
+
+    def La(self, g: int) -> int:
+        """Number of windows of gene g: |g|-k+1, or 0 when |g| < k."""
+        return int(_lib.orc_La(self._h, g))
+
+    def mv(self, g: int):
+        """(k-mer strings as bytes, counts) of gene g, ascending by k-mer."""
+        n = int(_lib.orc_mv_len(self._h, g))
+        kmers = np.zeros(max(1, n * self.k), np.uint8)
+        cnt = np.zeros(max(1, n), np.uint32)
+        _lib.orc_mv_get(self._h, g, _ptr(kmers, C.c_uint8), _ptr(cnt, C.c_uint32))
+        kb = kmers[: n * self.k].tobytes()
+        return [kb[e * self.k:(e + 1) * self.k] for e in range(n)], cnt[:n].copy()
+
+    def summin(self, a: int, b: int):
+        """(sum of min(mult) over shared k-mers, sum of max(mult) over the union)."""
+        s, d = C.c_uint32(0), C.c_uint32(0)
+        st = _lib.orc_summin(self._h, a, b, C.byref(s), C.byref(d))
+        if st != OK:
+            raise OracleError(st, "summin")
+        return int(s.value), int(d.value)
+
+
+@dataclass
+class PairResult:
+    """One genome pair (G_i rows, G_j columns); gene indices are local."""
+    S: np.ndarray          # uint32 [n_rows, n_cols]: sum min (Eq. (5) numerator)
+    Den: np.ndarray        # uint32 [n_rows, n_cols]: sum max (Eq. (5) denominator)
+    row_ptr: np.ndarray    # int64 [n_rows+1]: A_ij as CSR
+    row_col: np.ndarray    # int32
+    row_best_s: np.ndarray
+    row_best_den: np.ndarray
+    col_ptr: np.ndarray    # int64 [n_cols+1]: A_ji as CSR
+    col_row: np.ndarray
+    col_best_s: np.ndarray
+    col_best_den: np.ndarray
+    bbh: np.ndarray        # int32 [n_bbh, 2]: (a, b) ascending
+
+    def row_bh(self, a: int):
+        return self.row_col[self.row_ptr[a]:self.row_ptr[a + 1]]
+
+    def col_bh(self, b: int):
+        return self.col_row[self.col_ptr[b]:self.col_ptr[b + 1]]
+
+
+def pair(prof: Profiles, genome_ptr: np.ndarray, gi: int, gj: int, n_threads: int = 1) -> PairResult:
+    """Algorithms 2 and 3 for genomes gi (rows) and gj (columns)."""
+    lib = _load()
+    gp = np.ascontiguousarray(genome_ptr, dtype=np.int32)
+    h = lib.orc_pair_run(prof._h, _ptr(gp, C.c_int32), gi, gj, int(n_threads))
+    if not h:
+        raise OracleError(ERR_OOM, "pair")
+    try:
+        st = lib.orc_pair_status(h)
+        if st != OK:
+            raise OracleError(st, "pair")
+        nr, nc = C.c_uint32(0), C.c_uint32(0)
+        nrb, ncb, nbbh = C.c_uint64(0), C.c_uint64(0), C.c_uint64(0)
+        lib.orc_pair_sizes(h, C.byref(nr), C.byref(nc), C.byref(nrb), C.byref(ncb), C.byref(nbbh))
+        nr, nc, nrb, ncb, nbbh = nr.value, nc.value, nrb.value, ncb.value, nbbh.value
+        S = np.zeros((max(nr, 1), max(nc, 1)), np.uint32)
+        D = np.zeros_like(S)
+        lib.orc_pair_matrix(h, _ptr(S, C.c_uint32), _ptr(D, C.c_uint32))
+        rp = np.zeros(nr + 1, np.int64)
+        rc = np.zeros(max(nrb, 1), np.int32)
+        rbs = np.zeros(max(nr, 1), np.uint32)
+        rbd = np.zeros(max(nr, 1), np.uint32)
+        lib.orc_pair_row_bh(h, _ptr(rp, C.c_int64), _ptr(rc, C.c_int32), _ptr(rbs, C.c_uint32),
+                            _ptr(rbd, C.c_uint32))
+        cp = np.zeros(nc + 1, np.int64)
+        cr = np.zeros(max(ncb, 1), np.int32)
+        cbs = np.zeros(max(nc, 1), np.uint32)
+        cbd = np.zeros(max(nc, 1), np.uint32)
+        lib.orc_pair_col_bh(h, _ptr(cp, C.c_int64), _ptr(cr, C.c_int32), _ptr(cbs, C.c_uint32),
+                            _ptr(cbd, C.c_uint32))
+        ba = np.zeros(max(nbbh, 1), np.int32)
+        bb = np.zeros(max(nbbh, 1), np.int32)
+        lib.orc_pair_bbh(h, _ptr(ba, C.c_int32), _ptr(bb, C.c_int32))
+        return PairResult(S=S[:nr, :nc], Den=D[:nr, :nc], row_ptr=rp, row_col=rc[:nrb],
+                          row_best_s=rbs[:nr], row_best_den=rbd[:nr], col_ptr=cp, col_row=cr[:ncb],
+                          col_best_s=cbs[:nc], col_best_den=cbd[:nc],
+                          bbh=np.stack([ba[:nbbh], bb[:nbbh]], axis=1))
+    finally:
+        lib.orc_pair_free(h)
+
+
+def pair_for_dataset(ds, gi: int, gj: int, k: int, n_threads: int = 1) -> PairResult:
+    """Algorithms 1-3 on genomes gi and gj of a dataset (only their genes are profiled)."""
+    sub = ds.subset([gi, gj]) if gi != gj else ds.subset([gi])
+    prof = Profiles(sub.residues, sub.gene_ptr, k)
+    if gi == gj:
+        return pair(prof, sub.genome_ptr, 0, 0, n_threads)
+    return pair(prof, sub.genome_ptr, 0, 1, n_threads)
