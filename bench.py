@@ -1,0 +1,339 @@
+"""Benchmark: all-against-all gene similarity, Best Hits and BBH on one GB300.
+
+One step = the whole hot path over one seeded synthetic pangenome: k-mer
+profiles (encode, dictionary, multiplicity vectors, inverted index), sum-min
+of every cross-genome gene pair sharing a k-mer, Best Hits of every gene in
+every other genome, and Bidirectional Best Hits of every genome pair.
+
+Prints one JSON line.  `value` is logical gene pairs (sum_{i<j} |G_i||G_j|)
+per second with inputs resident in HBM; `e2e` is the same metric through the
+public C ABI from pinned host buffers (host->device copy of the residues and
+offsets and device->host copy of the BBH pairs inside the timed region).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload pan50x3000]
+  python bench.py --impl reference ...   (the CPU oracle on bounded samples)
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_2510_23679_gb300 import synth  # noqa: E402
+
+L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="pan50x3000", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), \
+        int(os.environ.get("LOCAL_RANK", 0))
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def make_workload(name, rank):
+    ds = synth.workload(name) if rank == 0 else synth.workload(name, seed=synth.WORKLOADS[name]["seed"] + 1000 * rank)
+    return ds
+
+
+def config_of(ds, name, k, flush):
+    return {"workload": f"{name}: {ds.n_genomes} genomes, {ds.n_genes} genes, {ds.n_residues} residues, "
+                        f"k={k}, amino-acid alphabet, all {ds.n_genomes * (ds.n_genomes - 1) // 2} genome pairs",
+            "n_genomes": ds.n_genomes, "n_genes": ds.n_genes, "n_residues": ds.n_residues, "k": k,
+            "logical_pairs_per_step": ds.logical_pairs(), "l2": flush, "parallelism": "replicas"}
+
+
+# --------------------------------------------------------------------------- CPU oracle sample
+def oracle_sample(ds, k, seconds, threads):
+    """Time the oracle (as it stands) on whole genome pairs until `seconds` pass."""
+    import oracle
+    n = ds.n_genomes
+    pairs = [(i, i + 1) for i in range(0, n - 1, 2)]
+    done, pairs_done, t0 = [], 0, time.perf_counter()
+    for gi, gj in pairs:
+        oracle.pair_for_dataset(ds, gi, gj, k, n_threads=threads)
+        done.append((gi, gj))
+        pairs_done += int(ds.genome_ptr[gi + 1] - ds.genome_ptr[gi]) * int(ds.genome_ptr[gj + 1] - ds.genome_ptr[gj])
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return pairs_done / dt, dt, done, pairs_done
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.idx = device_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    ds = make_workload(args.workload, 0)
+    import oracle
+    k = oracle.choose_k(ds.n_residues)
+    cores = host_cores()
+    per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle_sample(ds, k, 0.0, cores)  # one genome pair each
+    rates, samples = [], []
+    for _ in range(args.steps):
+        r, dt, done, npairs = oracle_sample(ds, k, per_step, cores)
+        rates.append(r)
+        samples.append(npairs)
+    value = statistics.median(rates)
+    ms = ds.logical_pairs() / value * 1e3
+    line = {"metric": "gene-pair GJ evals/s", "value": value, "unit": "gene-pairs/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "impl": "reference", "config": config_of(ds, args.workload, k, "n/a (CPU)"),
+            "cpu_baseline": {"value": value, "unit": "gene-pairs/s", "cores": cores, "kind": "oracle",
+                             "sample": f"whole genome pairs of the workload per step (~{per_step:.0f} s each, "
+                                       f"{statistics.median(samples):.3g} gene pairs), oracle threads={cores}"},
+            "e2e": {"value": value, "unit": "gene-pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------------- our arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    from paper_2510_23679_gb300 import pd
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ds = make_workload(args.workload, rank)
+    k = pd.pd_choose_k(ds.n_residues)
+    ctx = pd.pd_ctx_create(local)
+    stream = torch.cuda.current_stream(dev)
+
+    res_d = torch.from_numpy(ds.residues).to(dev)
+    gp_d = torch.from_numpy(ds.gene_ptr).to(dev)
+    gn_d = torch.from_numpy(ds.genome_ptr).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step_device():
+        prof = pd.pd_build_profiles(ctx, res_d, gp_d, gn_d, k)
+        hits = pd.pd_best_hits_all(ctx, prof)
+        bbh = pd.pd_bbh_all(ctx, prof, hits)
+        return prof, hits, bbh
+
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # ---- device-resident timed region
+    pd.pd_ctx_reset_timing(ctx)
+    pd.pd_ctx_set_timing(ctx, True)
+    launches0 = pd.pd_ctx_launch_count(ctx)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize()
+    keep = None
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i)  # evict the previous step's data from L2 (not timed)
+            ev[i][0].record(stream)
+            keep = step_device()
+            ev[i][1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    gpu_launches = pd.pd_ctx_launch_count(ctx) - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    k_ms, k_n = pd.pd_ctx_kernel_time(ctx, "summin_bh")
+    pd.pd_ctx_set_timing(ctx, False)
+    ms_per_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms_per_step])
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    pairs = ds.logical_pairs()
+    value = pairs * world / (ms_per_step / 1e3)
+
+    prof, hits, bbh = keep
+    pinfo = pd.pd_profiles_get_info(prof)
+    hinfo = pd.pd_hits_get_info(hits)
+    n_bbh = pd.pd_bbh_count(bbh)
+
+    # ---- roofline of the dominant kernel (sum-min + Best Hits), algorithmic bytes per launch
+    E = pinfo.n_entries
+    J = hinfo.postings_walked
+    alg_bytes = E * 6 + E * 8 + J * 4 + hinfo.n_hits * 8 + pinfo.n_genes * 12
+    k_avg_ms = k_ms / max(1, k_n)
+    achieved = alg_bytes / (k_avg_ms / 1e3) / 1e9
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # ---- end to end through the C ABI from pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        res_h = torch.from_numpy(ds.residues).pin_memory()
+        gp_h = torch.from_numpy(ds.gene_ptr).pin_memory()
+        gn_h = torch.from_numpy(ds.genome_ptr).pin_memory()
+        out_a = torch.empty(max(n_bbh, 1) * 2, dtype=torch.int32).pin_memory()
+        out_b = torch.empty(max(n_bbh, 1) * 2, dtype=torch.int32).pin_memory()
+        d2h = 0
+
+        def step_e2e():
+            nonlocal d2h
+            p = pd.pd_build_profiles(ctx, res_h, gp_h, gn_h, k)
+            h = pd.pd_best_hits_all(ctx, p)
+            b = pd.pd_bbh_all(ctx, p, h)
+            n = pd.pd_bbh_count(b)
+            oa = out_a if n <= out_a.numel() else torch.empty(n, dtype=torch.int32).pin_memory()
+            ob = out_b if n <= out_b.numel() else torch.empty(n, dtype=torch.int32).pin_memory()
+            pd.pd_bbh_copy(ctx, b, oa, ob)
+            d2h = 8 * n
+
+        for _ in range(2):
+            step_e2e()
+        torch.cuda.synchronize()
+        barrier()
+        times = []
+        for i in range(args.steps):
+            flush.fill_(i)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            step_e2e()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        e2e_s = sum(times) / len(times)
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e2e_s])
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": pairs * world / e2e_s, "unit": "gene-pairs/s",
+               "h2d_bytes_per_step": int(ds.residues.nbytes + ds.gene_ptr.nbytes + ds.genome_ptr.nbytes),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = host_cores()
+        rate, dt, done, npairs = oracle_sample(ds, k, args.cpu_seconds, cores)
+        cpu = {"value": rate, "unit": "gene-pairs/s", "cores": cores, "kind": "oracle",
+               "sample": f"genome pairs {done} of the same workload ({npairs} gene pairs, {dt:.1f} s, "
+                         f"profiles of both genomes included), oracle threads={cores}"}
+
+    if rank == 0:
+        line = {
+            "metric": "gene-pair GJ evals/s", "value": value, "unit": "gene-pairs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": config_of(ds, args.workload, k, f"flushed ({L2_FLUSH_BYTES >> 20} MB write) between steps"),
+            "genome_pairs_per_s": ds.n_genomes * (ds.n_genomes - 1) / 2 * world / (ms_per_step / 1e3),
+            "step_ms": step_ms,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "kernel": "summin_bh",
+                         "kernel_ms": k_avg_ms, "alg_bytes": alg_bytes, "peak_source": peak_src},
+            "e2e": e2e,
+            "gpu_launches": gpu_launches,
+            "cpu_baseline": cpu,
+            "clocks": clk.summary(),
+            "stats": {"n_distinct_kmers": pinfo.n_distinct, "mv_entries": E, "postings_walked": J,
+                      "best_hits": hinfo.n_hits, "bbh_pairs": n_bbh, "deferred_queries": hinfo.n_deferred,
+                      "max_posting": pinfo.max_posting, "profile_bytes": pinfo.device_bytes},
+        }
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,226 @@
+/*
+ * pd.h -- C ABI of the GB300 PanDelos-plus hot path (libpandelos_gpu.so).
+ *
+ * The library computes, for genomes made of amino-acid genes:
+ *   - per-gene k-mer multiplicity vectors (Eqs. (1)-(3), Algorithm 1);
+ *   - for every cross-genome gene pair (a, b) the exact integer numerator of
+ *     the generalized Jaccard similarity, s = sum over shared k-mers of
+ *     min(mult_a, mult_b), whose denominator is La + Lb - s (Eq. (5); La is the
+ *     number of k-mer windows of a);
+ *   - Best Hits: for a gene a and a target genome G_j, all genes of G_j whose
+ *     similarity to a equals the maximum (Eq. (8), Algorithm 2);
+ *   - Bidirectional Best Hits: pairs (a, b) with b in BH(a, G_j) and a in
+ *     BH(b, G_i) (Eq. (9), Algorithm 3).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a pd_status; no C++ exception crosses this ABI.
+ *     On failure pd_last_error(ctx) holds a one-line message.
+ *   - Inputs may live in host or device memory (detected per pointer); the
+ *     library copies host inputs to the device on the context's stream.
+ *   - Handles (pd_profiles, pd_hits, pd_bbh_set) own device memory obtained
+ *     from the context's allocator until the matching *_free call.  A handle
+ *     must be freed before its context is destroyed.  Caller buffers are only
+ *     borrowed for the duration of a call.
+ *   - All work of one context runs on its CUDA stream.  Calls that produce
+ *     data-dependent sizes synchronize that stream before they return.  One
+ *     context must not be used by two host threads at once.
+ *   - Gene indices: inside a dataset genes are numbered 0..n_genes-1 in input
+ *     order ("global" ids); genome i holds the contiguous genes
+ *     genome_ptr[i] .. genome_ptr[i+1]-1.  Per-pair results use "local"
+ *     indices (position inside the genome).
+ *   - Exactness: every value is an integer; ratios s1/d1 and s2/d2 are
+ *     compared by 64-bit cross-multiplication, so ties are exact.
+ *   - Candidates: a pair with s = 0 is never a hit (a minimum k-mer overlap is
+ *     required, "PanDelos methodology"); a gene with no candidate in G_j has an
+ *     empty Best Hit set, and a gene shorter than k never hits.
+ */
+#ifndef PD_H_
+#define PD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PD_OK = 0,
+  PD_ERR_ARG = 1,            /* invalid pointer, size, index, range or handle */
+  PD_ERR_ALPHABET = 2,       /* a residue is not one of ACDEFGHIKLMNPQRSTVWY */
+  PD_ERR_GENE_TOO_LONG = 3,  /* a gene has more than PD_MAX_WINDOWS k-mer windows */
+  PD_ERR_K_RANGE = 4,        /* k outside [1, PD_MAX_K] */
+  PD_ERR_OOM = 5,            /* the allocator returned NULL */
+  PD_ERR_BUDGET = 6,         /* reserved: request over a memory budget */
+  PD_ERR_CUDA = 7,           /* a CUDA runtime call or kernel launch failed */
+  PD_ERR_TIMEOUT = 8,        /* reserved: a bounded device wait expired */
+  PD_ERR_BUSY = 9,           /* reserved: no free slot */
+  PD_ERR_INTERNAL = 10       /* an internal invariant failed (a bug) */
+} pd_status;
+
+/* Largest k: the k-mer dictionary is a bitmap over all 20^k codes. */
+#define PD_MAX_K 8
+/* Largest number of windows (|g| - k + 1) of one gene: counts are 16-bit. */
+#define PD_MAX_WINDOWS 65535u
+/* Largest number of genomes in one dataset (per-genome maxima live in shared memory). */
+#define PD_MAX_GENOMES 4096u
+
+typedef struct pd_ctx pd_ctx;
+typedef struct pd_profiles pd_profiles;
+typedef struct pd_hits pd_hits;
+typedef struct pd_bbh_set pd_bbh_set;
+
+/* Device allocator hooks.  alloc returns a device pointer usable on `stream`
+ * (aligned to at least 256 bytes) or NULL; free releases it.  Passing NULL
+ * hooks selects cudaMallocAsync / cudaFreeAsync on the context's stream. */
+typedef void* (*pd_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*pd_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context; on failure *out is NULL. */
+pd_status pd_ctx_create(int device, void* cuda_stream, pd_alloc_fn alloc, pd_free_fn free_fn,
+                        void* user, pd_ctx** out);
+/* Destroy a context (synchronizes its stream).  NULL is ignored. */
+void pd_ctx_destroy(pd_ctx* ctx);
+/* Replace the stream used by later calls. */
+pd_status pd_ctx_set_stream(pd_ctx* ctx, void* cuda_stream);
+/* Last error message of this context ("" if none); owned by the context. */
+const char* pd_last_error(const pd_ctx* ctx);
+/* Number of kernels this library has launched through `ctx` so far. */
+uint64_t pd_ctx_launch_count(const pd_ctx* ctx);
+/* Per-kernel device timing.  When enabled, every launch is bracketed by CUDA
+ * events recorded on the launching stream.  pd_ctx_kernel_time synchronizes
+ * the stream and returns the summed milliseconds and launch count of kernel
+ * `name` since the last reset (name = NULL: all kernels). */
+pd_status pd_ctx_set_timing(pd_ctx* ctx, int enable);
+pd_status pd_ctx_kernel_time(pd_ctx* ctx, const char* name, double* ms, uint64_t* launches);
+pd_status pd_ctx_reset_timing(pd_ctx* ctx);
+
+/* ---------------------------------------------------------------- k rule */
+
+/* Eq. (4), "Basic notions": k = log_|Gamma| of the dataset size.  Read as the
+ * smallest integer k >= 1 with alphabet^k >= total_residues (exact integer
+ * powers).  Returns -1 if alphabet < 2. */
+int pd_choose_k(uint64_t total_residues, int alphabet);
+
+/* ---------------------------------------------------------------- profiles */
+
+/* Build the k-mer profiles of a dataset ("Multiplicity vector building
+ * phase", Algorithm 1; steps: residue mapping, rolling base-20 k-mer codes,
+ * dictionary of distinct codes -> dense ids, per-gene sorted (id, count)
+ * vectors, and the inverted index id -> (gene, count) postings).
+ *   residues   n_res bytes, all genes concatenated, letters ACDEFGHIKLMNPQRSTVWY
+ *   gene_ptr   n_genes+1 int64: gene g is residues[gene_ptr[g] .. gene_ptr[g+1])
+ *              (gene_ptr[0] = 0, non-decreasing, gene_ptr[n_genes] = n_res)
+ *   genome_ptr n_genomes+1 int32: genome i holds genes genome_ptr[i] ..
+ *              genome_ptr[i+1]-1 (genome_ptr[0] = 0, non-decreasing,
+ *              genome_ptr[n_genomes] = n_genes)
+ *   k          1..PD_MAX_K
+ * Errors: PD_ERR_ALPHABET (a byte outside the alphabet), PD_ERR_GENE_TOO_LONG,
+ * PD_ERR_K_RANGE, PD_ERR_ARG (malformed offsets, n_genomes > PD_MAX_GENOMES,
+ * more than 2^32-1 windows in total), PD_ERR_OOM, PD_ERR_CUDA.
+ * *out receives a device-resident handle. */
+pd_status pd_build_profiles(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res,
+                            const int64_t* gene_ptr, uint32_t n_genes, const int32_t* genome_ptr,
+                            uint32_t n_genomes, int k, pd_profiles** out);
+
+typedef struct {
+  int k;
+  uint32_t n_genes, n_genomes;
+  uint64_t n_windows;   /* sum of La over genes */
+  uint64_t n_distinct;  /* distinct k-mers of the dataset (dictionary size D) */
+  uint64_t n_entries;   /* sum over genes of distinct k-mers (MV entries = postings) */
+  uint32_t max_posting; /* longest posting list */
+  uint32_t count_bits;  /* bits of the count field in a packed posting */
+  uint64_t device_bytes;/* device memory held by the handle */
+} pd_profiles_info;
+
+pd_status pd_profiles_get_info(const pd_profiles* prof, pd_profiles_info* info);
+
+/* Copy the multiplicity vector of every gene (test and inspection hook).
+ *   mv_ptr  n_genes+1 int64 (CSR offsets), codes n_entries uint64 (base-20
+ *   k-mer code, first letter most significant, letters numbered in the order
+ *   ACDEFGHIKLMNPQRSTVWY), counts n_entries uint32, La n_genes uint32.
+ * Each gene's entries are in ascending code order.  Any pointer may be NULL
+ * to skip that array; pointers may be host or device. */
+pd_status pd_profiles_copy_mv(pd_ctx* ctx, const pd_profiles* prof, int64_t* mv_ptr,
+                              uint64_t* codes, uint32_t* counts, uint32_t* La);
+
+/* Copy the inverted index (test and inspection hook): for each distinct
+ * k-mer in ascending code order, its postings (gene, count) in ascending
+ * gene order.  post_ptr n_distinct+1 int64, codes n_distinct uint64,
+ * genes n_entries int32, counts n_entries uint32.  NULL skips an array. */
+pd_status pd_profiles_copy_index(pd_ctx* ctx, const pd_profiles* prof, int64_t* post_ptr,
+                                 uint64_t* codes, int32_t* genes, uint32_t* counts);
+
+void pd_profiles_free(pd_profiles* prof);
+
+/* ---------------------------------------------------------------- hits */
+
+/* Best Hits of every gene against every other genome of the dataset
+ * (all-against-all, "PanDelos-plus pipeline overview" phase (b) for all
+ * genome pairs at once).  Row a of the result lists, for every genome j other
+ * than a's own, the global ids of BH(a, G_j) (Eq. (8)); rows are grouped by
+ * target genome because global ids are contiguous per genome, and ascending. */
+pd_status pd_best_hits_all(pd_ctx* ctx, const pd_profiles* prof, pd_hits** out);
+
+/* Best Hits BH(a, G_gj) of every gene a of genome gi (Algorithm 2 for one
+ * genome pair).  Rows are the genes of G_gi (local), columns local to G_gj.
+ * gi == gj is PD_ERR_ARG. */
+pd_status pd_best_hits(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32_t gj,
+                       pd_hits** out);
+
+typedef struct {
+  uint32_t n_rows;      /* number of query genes */
+  uint64_t n_hits;      /* total Best Hit entries */
+  uint32_t row_base;    /* global id of row 0 (pair form), 0 for the all form */
+  uint32_t col_base;    /* global id subtracted from columns (pair form), 0 for all */
+  uint32_t n_deferred;  /* rows that took the large-accumulator path */
+  uint64_t postings_walked; /* (query k-mer, posting) matches visited */
+} pd_hits_info;
+
+pd_status pd_hits_get_info(const pd_hits* hits, pd_hits_info* info);
+
+/* Copy Best Hits as CSR: row_ptr n_rows+1 int64, cols n_hits int32 (local
+ * for the pair form, global for the all form), s n_hits uint32 (the pair's
+ * sum-min; its Eq. (5) denominator is La + Lb - s).  NULL skips an array;
+ * pointers may be host or device.  *n_hits (if not NULL) receives the count. */
+pd_status pd_hits_copy(pd_ctx* ctx, const pd_hits* hits, int64_t* row_ptr, int32_t* cols,
+                       uint32_t* s, uint64_t* n_hits);
+void pd_hits_free(pd_hits* hits);
+
+/* ---------------------------------------------------------------- BBH */
+
+/* Bidirectional Best Hits of all genome pairs from an all-against-all
+ * Best Hit result (Eq. (9), Algorithm 3).  Pairs (a, b) are global ids with
+ * genome(a) < genome(b), in ascending (a, b) order. */
+pd_status pd_bbh_all(pd_ctx* ctx, const pd_profiles* prof, const pd_hits* hits, pd_bbh_set** out);
+
+/* Bidirectional Best Hits of one genome pair (gi, gj), gi != gj: both Best
+ * Hit directions and the mutual check.  Pairs (a, b) are local (a in G_gi,
+ * b in G_gj), ascending. */
+pd_status pd_bbh(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32_t gj, pd_bbh_set** out);
+
+/* Copy pairs: a and b n_pairs int32 each (host or device, NULL to skip);
+ * *n_pairs (if not NULL) receives the count. */
+pd_status pd_bbh_copy(pd_ctx* ctx, const pd_bbh_set* set, int32_t* a, int32_t* b, uint64_t* n_pairs);
+uint64_t pd_bbh_count(const pd_bbh_set* set);
+void pd_bbh_free(pd_bbh_set* set);
+
+/* ---------------------------------------------------------------- sum-min */
+
+/* Every pair (a in G_gi, b in G_gj) with s >= 1 and its s (Eq. (5)
+ * numerator), local indices, ascending (a, b).  Two-phase: with a == NULL
+ * only *n is written; otherwise a, b, s must hold *n entries (host or device)
+ * and the call fills them.  Exposes the sum-min step for checking. */
+pd_status pd_summin_pairs(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32_t gj,
+                          int32_t* a, int32_t* b, uint32_t* s, uint64_t* n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PD_H_ */

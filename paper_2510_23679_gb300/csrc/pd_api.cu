@@ -1,0 +1,973 @@
+// pd_api.cu -- host side of the C ABI declared in include/pd.h.
+//
+// Orchestrates the kernels of k_profiles.cu, k_summin.cu, k_bbh.cu and
+// k_scan.cu on the context's stream, owns device memory through the
+// context's allocator hooks, and turns every failure into a pd_status with a
+// message (no exception crosses the ABI).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pd.h"
+#include "pd_internal.cuh"
+
+#define PD_API extern "C" __attribute__((visibility("default")))
+
+struct pd_ctx;
+
+namespace pdg {
+
+struct Launcher {
+  pd_ctx* ctx;
+};
+
+}  // namespace pdg
+
+struct PendingTiming {
+  std::string name;
+  cudaEvent_t start, stop;
+};
+
+struct pd_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  pd_alloc_fn alloc = nullptr;
+  pd_free_fn free_fn = nullptr;
+  void* user = nullptr;
+  std::string err;
+  uint64_t launches = 0;
+  bool timing = false;
+  std::vector<PendingTiming> pending;
+  std::vector<cudaEvent_t> event_pool;
+  std::map<std::string, std::pair<double, uint64_t>> kernel_ms;
+  pdg::Launcher L{nullptr};
+  pdg::DevErr* d_err = nullptr;  // device error block
+  pdg::DevErr* h_err = nullptr;  // pinned host mirror
+};
+
+// ------------------------------------------------------------------ launches
+namespace pdg {
+
+static cudaEvent_t take_event(pd_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+cudaError_t launch_begin(Launcher* L, const char* name) {
+  pd_ctx* c = L->ctx;
+  if (c->timing) {
+    PendingTiming t{name, take_event(c), take_event(c)};
+    if (!t.start || !t.stop) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaEventRecord(t.start, c->stream);
+    if (e != cudaSuccess) return e;
+    c->pending.push_back(t);
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_end(Launcher* L, const char* name) {
+  pd_ctx* c = L->ctx;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  c->launches += 1;
+  if (c->timing && !c->pending.empty() && c->pending.back().name == name)
+    return cudaEventRecord(c->pending.back().stop, c->stream);
+  return cudaSuccess;
+}
+
+}  // namespace pdg
+
+// ------------------------------------------------------------------ helpers
+namespace {
+
+using pdg::DevErr;
+
+pd_status fail(pd_ctx* c, pd_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+pd_status fail_cuda(pd_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+  cudaGetLastError();
+  return fail(c, PD_ERR_CUDA, m);
+}
+
+#define CK(expr)                                      \
+  do {                                                \
+    cudaError_t e_ = (expr);                          \
+    if (e_ != cudaSuccess) return fail_cuda(c, e_, #expr); \
+  } while (0)
+
+// Device buffer owned through the context's allocator.
+struct Buf {
+  pd_ctx* c = nullptr;
+  void* p = nullptr;
+  size_t n = 0;
+  Buf() = default;
+  Buf(const Buf&) = delete;
+  Buf& operator=(const Buf&) = delete;
+  Buf(Buf&& o) noexcept : c(o.c), p(o.p), n(o.n) { o.p = nullptr; }
+  Buf& operator=(Buf&& o) noexcept {
+    if (this != &o) {
+      release();
+      c = o.c;
+      p = o.p;
+      n = o.n;
+      o.p = nullptr;
+    }
+    return *this;
+  }
+  ~Buf() { release(); }
+  bool alloc(pd_ctx* ctx, size_t bytes) {
+    release();
+    c = ctx;
+    n = (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
+    if (c->alloc) {
+      p = c->alloc(n, (void*)c->stream, c->user);
+    } else if (cudaMallocAsync(&p, n, c->stream) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return p != nullptr;
+  }
+  void release() {
+    if (p && c) {
+      if (c->free_fn) c->free_fn(p, n, (void*)c->stream, c->user);
+      else cudaFreeAsync(p, c->stream);
+    }
+    p = nullptr;
+  }
+  template <typename T>
+  T* as() const {
+    return (T*)p;
+  }
+};
+
+#define ALLOC(buf, bytes)                                                                        \
+  do {                                                                                           \
+    if (!(buf).alloc(c, (bytes))) return fail(c, PD_ERR_OOM, "device allocation of " +           \
+                                                             std::to_string((size_t)(bytes)) +   \
+                                                             " bytes failed (" #buf ")");        \
+  } while (0)
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+uint32_t bits_for(uint32_t max_value) {
+  uint32_t b = 1;
+  while (b < 32 && (max_value >> b) != 0) ++b;
+  return b;
+}
+
+uint64_t pow_u64(uint64_t b, int e) {
+  uint64_t r = 1;
+  for (int i = 0; i < e; ++i) r *= b;
+  return r;
+}
+
+// Reads the device error block; returns PD_OK or the recorded error.
+pd_status check_dev_err(pd_ctx* c) {
+  CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(DevErr), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (c->h_err->code != 0) {
+    const int code = c->h_err->code;
+    const unsigned long long det = c->h_err->detail;
+    CK(cudaMemsetAsync(c->d_err, 0, sizeof(DevErr), c->stream));
+    if (code == PD_ERR_ALPHABET)
+      return fail(c, PD_ERR_ALPHABET, "residue at offset " + std::to_string(det) +
+                                          " is not one of ACDEFGHIKLMNPQRSTVWY");
+    return fail(c, (pd_status)code, "device reported error " + std::to_string(code) + " (detail " +
+                                        std::to_string(det) + ")");
+  }
+  return PD_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handles
+struct pd_profiles {
+  pd_ctx* ctx = nullptr;
+  pdg::ProfilesView view{};
+  pd_profiles_info info{};
+  Buf genome_ptr, La, win_off, mv_len, mv_id, mv_cnt, gene_genome, bitmap, word_rank, post_ptr, post;
+  std::vector<int32_t> h_genome_ptr;
+};
+
+struct pd_hits {
+  pd_ctx* ctx = nullptr;
+  int all_pairs = 0;
+  uint32_t n_rows = 0, row_base = 0, col_base = 0;
+  uint32_t nA = 0, qa0 = 0, qb0 = 0;  // pair form with both directions (internal)
+  uint64_t n_hits = 0, walked = 0;
+  uint32_t n_deferred = 0;
+  Buf row_off, row_len, out_b, out_s;
+};
+
+struct pd_bbh_set {
+  pd_ctx* ctx = nullptr;
+  uint64_t n = 0;
+  Buf a, b;
+};
+
+// ------------------------------------------------------------------ context
+PD_API pd_status pd_ctx_create(int device, void* cuda_stream, pd_alloc_fn alloc, pd_free_fn free_fn, void* user,
+                               pd_ctx** out) {
+  if (!out) return PD_ERR_ARG;
+  *out = nullptr;
+  if ((alloc == nullptr) != (free_fn == nullptr)) return PD_ERR_ARG;
+  pd_ctx* c = nullptr;
+  try {
+    c = new pd_ctx();
+  } catch (...) {
+    return PD_ERR_OOM;
+  }
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->alloc = alloc;
+  c->free_fn = free_fn;
+  c->user = user;
+  c->L.ctx = c;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(DevErr));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(DevErr));
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(DevErr));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (c->d_err) cudaFree(c->d_err);
+    if (c->h_err) cudaFreeHost(c->h_err);
+    delete c;
+    return PD_ERR_CUDA;
+  }
+  *out = c;
+  return PD_OK;
+}
+
+PD_API void pd_ctx_destroy(pd_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  for (auto& t : c->pending) {
+    cudaEventDestroy(t.start);
+    cudaEventDestroy(t.stop);
+  }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
+  cudaFree(c->d_err);
+  cudaFreeHost(c->h_err);
+  delete c;
+}
+
+PD_API pd_status pd_ctx_set_stream(pd_ctx* c, void* cuda_stream) {
+  if (!c) return PD_ERR_ARG;
+  c->stream = (cudaStream_t)cuda_stream;
+  return PD_OK;
+}
+
+PD_API const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+PD_API uint64_t pd_ctx_launch_count(const pd_ctx* c) { return c ? c->launches : 0; }
+
+PD_API pd_status pd_ctx_set_timing(pd_ctx* c, int enable) {
+  if (!c) return PD_ERR_ARG;
+  c->timing = enable != 0;
+  return PD_OK;
+}
+
+static pd_status drain_timing(pd_ctx* c) {
+  CK(cudaStreamSynchronize(c->stream));
+  for (auto& t : c->pending) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, t.start, t.stop));
+    auto& acc = c->kernel_ms[t.name];
+    acc.first += ms;
+    acc.second += 1;
+    c->event_pool.push_back(t.start);
+    c->event_pool.push_back(t.stop);
+  }
+  c->pending.clear();
+  return PD_OK;
+}
+
+PD_API pd_status pd_ctx_kernel_time(pd_ctx* c, const char* name, double* ms, uint64_t* launches) {
+  if (!c) return PD_ERR_ARG;
+  try {
+    pd_status st = drain_timing(c);
+    if (st != PD_OK) return st;
+    double t = 0;
+    uint64_t n = 0;
+    for (auto& kv : c->kernel_ms) {
+      if (name == nullptr || kv.first == name) {
+        t += kv.second.first;
+        n += kv.second.second;
+      }
+    }
+    if (ms) *ms = t;
+    if (launches) *launches = n;
+    return PD_OK;
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_ctx_kernel_time");
+  }
+}
+
+PD_API pd_status pd_ctx_reset_timing(pd_ctx* c) {
+  if (!c) return PD_ERR_ARG;
+  pd_status st = drain_timing(c);
+  c->kernel_ms.clear();
+  return st;
+}
+
+PD_API int pd_choose_k(uint64_t total, int alphabet) {
+  if (alphabet < 2) return -1;
+  int k = 1;
+  unsigned __int128 p = (unsigned __int128)alphabet;
+  while (p < total) {
+    p *= (unsigned)alphabet;
+    ++k;
+  }
+  return k;
+}
+
+// ------------------------------------------------------------------ profiles
+static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                                     uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
+                                     pd_profiles** out) {
+  if (k < 1 || k > PD_MAX_K) return fail(c, PD_ERR_K_RANGE, "k must be in [1, " + std::to_string(PD_MAX_K) + "]");
+  if (!gene_ptr || !genome_ptr || (n_res > 0 && !residues))
+    return fail(c, PD_ERR_ARG, "null residues, gene_ptr or genome_ptr");
+  if (n_genomes < 1 || n_genomes > PD_MAX_GENOMES)
+    return fail(c, PD_ERR_ARG, "n_genomes must be in [1, " + std::to_string(PD_MAX_GENOMES) + "]");
+  if (n_genes > 0x7FFFFFFFu) return fail(c, PD_ERR_ARG, "too many genes");
+  CK(cudaSetDevice(c->device));
+
+  // ---- offsets on the host (validated; they size every buffer)
+  std::vector<int64_t> hg(n_genes + 1);
+  std::vector<int32_t> hgn(n_genomes + 1);
+  const bool gp_dev = is_device_ptr(gene_ptr), gn_dev = is_device_ptr(genome_ptr);
+  CK(cudaMemcpyAsync(hg.data(), gene_ptr, sizeof(int64_t) * (n_genes + 1), cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(hgn.data(), genome_ptr, sizeof(int32_t) * (n_genomes + 1), cudaMemcpyDefault, c->stream));
+  if (gp_dev || gn_dev) CK(cudaStreamSynchronize(c->stream));
+  if (hg[0] != 0 || (uint64_t)hg[n_genes] != n_res) return fail(c, PD_ERR_ARG, "gene_ptr must run from 0 to n_res");
+  if (hgn[0] != 0 || (uint32_t)hgn[n_genomes] != n_genes)
+    return fail(c, PD_ERR_ARG, "genome_ptr must run from 0 to n_genes");
+  for (uint32_t i = 0; i < n_genomes; ++i)
+    if (hgn[i + 1] < hgn[i]) return fail(c, PD_ERR_ARG, "genome_ptr is decreasing at " + std::to_string(i));
+  std::vector<uint32_t> La(n_genes), win_off(n_genes + 1);
+  uint64_t W = 0;
+  std::vector<uint32_t> long_genes, long_off;
+  uint64_t long_total = 0;
+  const uint32_t kMaxSmemSort = 8192;
+  for (uint32_t g = 0; g < n_genes; ++g) {
+    const int64_t len = hg[g + 1] - hg[g];
+    if (len < 0) return fail(c, PD_ERR_ARG, "gene_ptr is decreasing at " + std::to_string(g));
+    const uint64_t w = (len >= k) ? (uint64_t)(len - k + 1) : 0;
+    if (w > PD_MAX_WINDOWS)
+      return fail(c, PD_ERR_GENE_TOO_LONG, "gene " + std::to_string(g) + " has " + std::to_string(w) +
+                                               " windows (max " + std::to_string(PD_MAX_WINDOWS) + ")");
+    La[g] = (uint32_t)w;
+    win_off[g] = (uint32_t)W;
+    W += w;
+    if (W > 0xFFFFFFF0ull) return fail(c, PD_ERR_ARG, "more than 2^32 k-mer windows in the dataset");
+    if (pdg::next_pow2((uint32_t)w) > kMaxSmemSort) {
+      long_genes.push_back(g);
+      long_off.push_back((uint32_t)long_total);
+      long_total += pdg::next_pow2((uint32_t)w);
+    }
+  }
+  win_off[n_genes] = (uint32_t)W;
+
+  pd_profiles* P = new pd_profiles();
+  P->ctx = c;
+  P->h_genome_ptr = hgn;
+  std::unique_ptr<pd_profiles> guard(P);
+  const uint64_t n_codes = pow_u64(20, k);
+  const uint64_t n_words = (n_codes + 63) / 64;
+
+  // ---- inputs on the device
+  Buf d_res, d_gene_ptr, d_long, d_long_off, d_long_scratch, tmp;
+  const uint8_t* res_dev = residues;
+  const int64_t* gp_devp = gene_ptr;
+  if (n_res > 0 && !is_device_ptr(residues)) {
+    ALLOC(d_res, n_res);
+    CK(cudaMemcpyAsync(d_res.p, residues, n_res, cudaMemcpyHostToDevice, c->stream));
+    res_dev = d_res.as<uint8_t>();
+  }
+  if (!gp_dev) {
+    ALLOC(d_gene_ptr, sizeof(int64_t) * (n_genes + 1));
+    CK(cudaMemcpyAsync(d_gene_ptr.p, hg.data(), sizeof(int64_t) * (n_genes + 1), cudaMemcpyHostToDevice,
+                       c->stream));
+    gp_devp = d_gene_ptr.as<int64_t>();
+  }
+  ALLOC(P->genome_ptr, sizeof(int32_t) * (n_genomes + 1));
+  ALLOC(P->La, sizeof(uint32_t) * std::max<uint32_t>(n_genes, 1));
+  ALLOC(P->win_off, sizeof(uint32_t) * (n_genes + 1));
+  ALLOC(P->gene_genome, sizeof(uint16_t) * std::max<uint32_t>(n_genes, 1));
+  CK(cudaMemcpyAsync(P->genome_ptr.p, hgn.data(), sizeof(int32_t) * (n_genomes + 1), cudaMemcpyHostToDevice,
+                     c->stream));
+  if (n_genes) CK(cudaMemcpyAsync(P->La.p, La.data(), sizeof(uint32_t) * n_genes, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(P->win_off.p, win_off.data(), sizeof(uint32_t) * (n_genes + 1), cudaMemcpyHostToDevice,
+                     c->stream));
+  // host vectors must outlive the async copies: synchronize before they go
+  pdg::Launcher* L = &c->L;
+  if (n_genomes) CK(pdg::run_gene_genome(L, P->genome_ptr.as<int32_t>(), n_genomes, P->gene_genome.as<uint16_t>(),
+                                          c->stream));
+
+  // ---- dictionary: bitmap of present codes and word ranks
+  ALLOC(P->bitmap, sizeof(unsigned long long) * n_words);
+  ALLOC(P->word_rank, sizeof(uint32_t) * n_words);
+  CK(cudaMemsetAsync(P->bitmap.p, 0, sizeof(unsigned long long) * n_words, c->stream));
+  if (n_genes)
+    CK(pdg::run_encode_mark(L, res_dev, gp_devp, n_genes, k, P->bitmap.as<unsigned long long>(), c->d_err,
+                            c->stream));
+  ALLOC(tmp, pdg::scan_temp_bytes(std::max<uint64_t>(n_words, W + 1)) + 64);
+  Buf d_counts;  // [0] = D, [1] = max posting
+  ALLOC(d_counts, 4 * sizeof(uint32_t));
+  CK(cudaMemsetAsync(d_counts.p, 0, 4 * sizeof(uint32_t), c->stream));
+  CK(pdg::scan_popc_words(L, P->bitmap.as<unsigned long long>(), n_words, P->word_rank.as<uint32_t>(),
+                          d_counts.as<uint32_t>(), tmp.p, c->stream));
+  uint32_t h_counts[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(h_counts, d_counts.p, sizeof(h_counts), cudaMemcpyDeviceToHost, c->stream));
+  pd_status st = check_dev_err(c);  // synchronizes
+  if (st != PD_OK) return st;
+  const uint64_t D = h_counts[0];
+
+  // ---- multiplicity vectors and posting counts per id
+  Buf hist;
+  ALLOC(hist, sizeof(uint32_t) * (D + 1));
+  CK(cudaMemsetAsync(hist.p, 0, sizeof(uint32_t) * (D + 1), c->stream));
+  ALLOC(P->mv_id, sizeof(uint32_t) * std::max<uint64_t>(W, 1));
+  ALLOC(P->mv_cnt, sizeof(uint16_t) * std::max<uint64_t>(W, 1));
+  ALLOC(P->mv_len, sizeof(uint32_t) * std::max<uint32_t>(n_genes, 1));
+  if (!long_genes.empty()) {
+    ALLOC(d_long, sizeof(uint32_t) * long_genes.size());
+    ALLOC(d_long_off, sizeof(uint32_t) * long_off.size());
+    ALLOC(d_long_scratch, sizeof(uint32_t) * long_total);
+    CK(cudaMemcpyAsync(d_long.p, long_genes.data(), sizeof(uint32_t) * long_genes.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemcpyAsync(d_long_off.p, long_off.data(), sizeof(uint32_t) * long_off.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+  }
+  if (n_genes)
+    CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
+                         P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), P->mv_id.as<uint32_t>(),
+                         P->mv_cnt.as<uint16_t>(), P->mv_len.as<uint32_t>(), hist.as<uint32_t>(),
+                         d_long.as<uint32_t>(), (uint32_t)long_genes.size(), d_long_scratch.as<uint32_t>(),
+                         d_long_off.as<uint32_t>(), kMaxSmemSort, c->stream));
+  ALLOC(P->post_ptr, sizeof(uint32_t) * (D + 1));
+  CK(pdg::scan_u32(L, hist.as<uint32_t>(), D, P->post_ptr.as<uint32_t>(), tmp.p, c->stream));
+  if (D) CK(pdg::run_max_u32(L, hist.as<uint32_t>(), D, d_counts.as<uint32_t>() + 1, c->stream));
+  uint32_t E32 = 0;
+  CK(cudaMemcpyAsync(&E32, P->post_ptr.as<uint32_t>() + D, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(h_counts, d_counts.p, sizeof(h_counts), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  const uint64_t E = E32;
+  const uint32_t max_posting = h_counts[1];
+
+  // ---- inverted index
+  const uint32_t gene_bits = bits_for(n_genes > 0 ? n_genes - 1 : 0);
+  const uint32_t cnt_bits = 32 - gene_bits;
+  const uint32_t cnt_cap = std::min<uint32_t>((1u << cnt_bits) - 1u, 65535u);
+  ALLOC(P->post, sizeof(uint32_t) * std::max<uint64_t>(E, 1));
+  if (n_genes)
+    CK(pdg::run_post_fill(L, P->win_off.as<uint32_t>(), P->mv_len.as<uint32_t>(), P->mv_id.as<uint32_t>(),
+                          P->mv_cnt.as<uint16_t>(), n_genes, P->post_ptr.as<uint32_t>(), hist.as<uint32_t>(),
+                          P->post.as<uint32_t>(), cnt_bits, cnt_cap, c->stream));
+  if (D) {
+    Buf queue, qlen, lscr;
+    ALLOC(queue, sizeof(uint32_t) * (E / 33 + 1));
+    ALLOC(qlen, sizeof(uint32_t));
+    CK(cudaMemsetAsync(qlen.p, 0, sizeof(uint32_t), c->stream));
+    if (pdg::next_pow2(max_posting) > 8192) ALLOC(lscr, sizeof(uint32_t) * pdg::next_pow2(max_posting));
+    CK(pdg::run_post_sort(L, P->post_ptr.as<uint32_t>(), D, P->post.as<uint32_t>(), queue.as<uint32_t>(),
+                          qlen.as<uint32_t>(), max_posting, lscr.as<uint32_t>(), c->stream));
+    CK(cudaStreamSynchronize(c->stream));  // scratch lifetime
+  }
+  st = check_dev_err(c);
+  if (st != PD_OK) return st;
+
+  pdg::ProfilesView& v = P->view;
+  v.k = k;
+  v.n_genes = n_genes;
+  v.n_genomes = n_genomes;
+  v.n_windows = W;
+  v.n_distinct = D;
+  v.n_entries = E;
+  v.cnt_bits = cnt_bits;
+  v.cnt_cap = cnt_cap;
+  v.max_posting = max_posting;
+  v.win_off = P->win_off.as<uint32_t>();
+  v.mv_len = P->mv_len.as<uint32_t>();
+  v.mv_id = P->mv_id.as<uint32_t>();
+  v.mv_cnt = P->mv_cnt.as<uint16_t>();
+  v.La = P->La.as<uint32_t>();
+  v.gene_genome = P->gene_genome.as<uint16_t>();
+  v.genome_ptr = P->genome_ptr.as<int32_t>();
+  v.bitmap = P->bitmap.as<unsigned long long>();
+  v.word_rank = P->word_rank.as<uint32_t>();
+  v.n_words = n_words;
+  v.post_ptr = P->post_ptr.as<uint32_t>();
+  v.post = P->post.as<uint32_t>();
+  pd_profiles_info& in = P->info;
+  in.k = k;
+  in.n_genes = n_genes;
+  in.n_genomes = n_genomes;
+  in.n_windows = W;
+  in.n_distinct = D;
+  in.n_entries = E;
+  in.max_posting = max_posting;
+  in.count_bits = cnt_bits;
+  in.device_bytes = P->genome_ptr.n + P->La.n + P->win_off.n + P->mv_len.n + P->mv_id.n + P->mv_cnt.n +
+                    P->gene_genome.n + P->bitmap.n + P->word_rank.n + P->post_ptr.n + P->post.n;
+  *out = guard.release();
+  return PD_OK;
+}
+
+PD_API pd_status pd_build_profiles(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                                   uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
+                                   pd_profiles** out) {
+  if (!c || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    return build_profiles_impl(c, residues, n_res, gene_ptr, n_genes, genome_ptr, n_genomes, k, out);
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_build_profiles");
+  }
+}
+
+PD_API pd_status pd_profiles_get_info(const pd_profiles* P, pd_profiles_info* info) {
+  if (!P || !info) return PD_ERR_ARG;
+  *info = P->info;
+  return PD_OK;
+}
+
+PD_API void pd_profiles_free(pd_profiles* P) { delete P; }
+
+// Copy `bytes` from a device buffer to a caller pointer (host or device).
+static pd_status copy_out(pd_ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!dst || bytes == 0) return PD_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
+  return PD_OK;
+}
+
+namespace {
+__global__ void k_u32_to_i64(const uint32_t* __restrict__ a, uint64_t n, int64_t* __restrict__ out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (int64_t)a[i];
+}
+__global__ void k_row_ids(uint32_t n_rows, const unsigned long long* __restrict__ row_ptr, int32_t* __restrict__ out) {
+  for (uint32_t x = blockIdx.x; x < n_rows; x += gridDim.x)
+    for (unsigned long long e = row_ptr[x] + threadIdx.x; e < row_ptr[x + 1]; e += blockDim.x) out[e] = (int32_t)x;
+}
+}  // namespace
+
+PD_API pd_status pd_profiles_copy_mv(pd_ctx* c, const pd_profiles* P, int64_t* mv_ptr, uint64_t* codes,
+                                     uint32_t* counts, uint32_t* La) {
+  if (!c || !P) return PD_ERR_ARG;
+  try {
+    CK(cudaSetDevice(c->device));
+    const pdg::ProfilesView& v = P->view;
+    pdg::Launcher* L = &c->L;
+    Buf ptr, tmp, code_of_id, d_codes, d_counts;
+    ALLOC(ptr, sizeof(unsigned long long) * (v.n_genes + 1));
+    ALLOC(tmp, pdg::scan_temp_bytes(v.n_genes + 1) + 64);
+    CK(pdg::scan_u32_to_u64(L, v.mv_len, v.n_genes, ptr.as<unsigned long long>(), tmp.p, c->stream));
+    if (codes) {
+      ALLOC(code_of_id, sizeof(unsigned long long) * std::max<uint64_t>(v.n_distinct, 1));
+      CK(pdg::run_select_codes(L, v.bitmap, v.word_rank, v.n_words, code_of_id.as<unsigned long long>(), c->stream));
+      ALLOC(d_codes, sizeof(unsigned long long) * std::max<uint64_t>(v.n_entries, 1));
+    }
+    if (counts) ALLOC(d_counts, sizeof(uint32_t) * std::max<uint64_t>(v.n_entries, 1));
+    if ((codes || counts) && v.n_genes)
+      CK(pdg::run_export_mv(L, v, ptr.as<unsigned long long>(), code_of_id.as<unsigned long long>(),
+                            d_codes.as<unsigned long long>(), d_counts.as<uint32_t>(), c->stream));
+    pd_status st;
+    if ((st = copy_out(c, mv_ptr, ptr.p, sizeof(int64_t) * (v.n_genes + 1))) != PD_OK) return st;
+    if ((st = copy_out(c, codes, d_codes.p, sizeof(uint64_t) * v.n_entries)) != PD_OK) return st;
+    if ((st = copy_out(c, counts, d_counts.p, sizeof(uint32_t) * v.n_entries)) != PD_OK) return st;
+    if ((st = copy_out(c, La, v.La, sizeof(uint32_t) * v.n_genes)) != PD_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return PD_OK;
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_profiles_copy_mv");
+  }
+}
+
+PD_API pd_status pd_profiles_copy_index(pd_ctx* c, const pd_profiles* P, int64_t* post_ptr, uint64_t* codes,
+                                        int32_t* genes, uint32_t* counts) {
+  if (!c || !P) return PD_ERR_ARG;
+  try {
+    CK(cudaSetDevice(c->device));
+    const pdg::ProfilesView& v = P->view;
+    pdg::Launcher* L = &c->L;
+    Buf ptr64, code_of_id, d_genes, d_counts;
+    pd_status st;
+    if (post_ptr) {
+      ALLOC(ptr64, sizeof(int64_t) * (v.n_distinct + 1));
+      const unsigned grid = (unsigned)std::min<uint64_t>((v.n_distinct + 256) / 256 + 1, 152u * 16u);
+      CK(pdg::launch_begin(L, "u32_to_i64"));
+      k_u32_to_i64<<<grid, 256, 0, c->stream>>>(v.post_ptr, v.n_distinct + 1, ptr64.as<int64_t>());
+      CK(pdg::launch_end(L, "u32_to_i64"));
+    }
+    if (codes) {
+      ALLOC(code_of_id, sizeof(unsigned long long) * std::max<uint64_t>(v.n_distinct, 1));
+      CK(pdg::run_select_codes(L, v.bitmap, v.word_rank, v.n_words, code_of_id.as<unsigned long long>(), c->stream));
+    }
+    if (genes) ALLOC(d_genes, sizeof(int32_t) * std::max<uint64_t>(v.n_entries, 1));
+    if (counts) ALLOC(d_counts, sizeof(uint32_t) * std::max<uint64_t>(v.n_entries, 1));
+    if ((genes || counts) && v.n_entries)
+      CK(pdg::run_export_index(L, v, d_genes.as<int32_t>(), d_counts.as<uint32_t>(), c->stream));
+    if ((st = copy_out(c, post_ptr, ptr64.p, sizeof(int64_t) * (v.n_distinct + 1))) != PD_OK) return st;
+    if ((st = copy_out(c, codes, code_of_id.p, sizeof(uint64_t) * v.n_distinct)) != PD_OK) return st;
+    if ((st = copy_out(c, genes, d_genes.p, sizeof(int32_t) * v.n_entries)) != PD_OK) return st;
+    if ((st = copy_out(c, counts, d_counts.p, sizeof(uint32_t) * v.n_entries)) != PD_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return PD_OK;
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_profiles_copy_index");
+  }
+}
+
+// ------------------------------------------------------------------ sum-min + Best Hits
+// Runs the shared tier, then (if needed) the global tier for deferred queries,
+// growing the output until every row fits.  The result rows live in H.
+static pd_status run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& Q, bool emit_all, pd_hits* H) {
+  const pdg::ProfilesView& v = P->view;
+  pdg::Launcher* L = &c->L;
+  const uint32_t nq = Q.n_queries;
+  uint64_t cap;
+  if (Q.all_pairs)
+    cap = (uint64_t)nq * std::max<uint32_t>(v.n_genomes - 1, 1) * 3 / 2 + 4096;
+  else
+    cap = (uint64_t)nq * 4 + 4096;
+  if (emit_all) cap = (uint64_t)nq * 64 + 4096;
+  Buf counters, deferred;
+  ALLOC(counters, 4 * sizeof(unsigned long long));
+  ALLOC(H->row_off, sizeof(unsigned long long) * std::max<uint32_t>(nq, 1));
+  ALLOC(H->row_len, sizeof(uint32_t) * std::max<uint32_t>(nq, 1));
+  ALLOC(deferred, sizeof(uint32_t) * std::max<uint32_t>(nq, 1));
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    ALLOC(H->out_b, sizeof(uint32_t) * cap);
+    ALLOC(H->out_s, sizeof(uint32_t) * cap);
+    CK(cudaMemsetAsync(counters.p, 0, 4 * sizeof(unsigned long long), c->stream));
+    CK(cudaMemsetAsync(H->row_len.p, 0, sizeof(uint32_t) * std::max<uint32_t>(nq, 1), c->stream));
+    unsigned long long* cnt = counters.as<unsigned long long>();
+    pdg::HitsOut O;
+    O.out_b = H->out_b.as<uint32_t>();
+    O.out_s = H->out_s.as<uint32_t>();
+    O.out_cap = cap;
+    O.cursor = cnt + 0;
+    O.walked = cnt + 1;
+    O.n_deferred = (uint32_t*)(cnt + 2);
+    O.row_off = H->row_off.as<unsigned long long>();
+    O.row_len = H->row_len.as<uint32_t>();
+    O.deferred = deferred.as<uint32_t>();
+    CK(pdg::run_summin_bh(L, v, Q, O, c->d_err, emit_all, c->stream));
+    unsigned long long h[4];
+    CK(cudaMemcpyAsync(h, counters.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    pd_status st = check_dev_err(c);
+    if (st != PD_OK) return st;
+    const uint32_t n_def = (uint32_t)h[2];
+    if (n_def > 0) {
+      pdg::BigScratch B;
+      const uint32_t targets = std::max<uint32_t>(v.n_genes, 2);
+      B.cap = pdg::next_pow2(2 * targets);
+      B.out_cap = pdg::next_pow2(targets);
+      const uint32_t n_ctas = std::min<uint32_t>(n_def, 64);
+      Buf bk, bv, bo;
+      ALLOC(bk, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
+      ALLOC(bv, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
+      ALLOC(bo, sizeof(unsigned long long) * (size_t)B.out_cap * n_ctas);
+      B.keys = bk.as<uint32_t>();
+      B.vals = bv.as<uint32_t>();
+      B.out = bo.as<unsigned long long>();
+      CK(pdg::run_summin_bh_big(L, v, Q, O, B, n_ctas, c->d_err, emit_all, c->stream));
+      CK(cudaMemcpyAsync(h, counters.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+      st = check_dev_err(c);  // synchronizes (scratch lifetime)
+      if (st != PD_OK) return st;
+    }
+    if (h[0] <= cap) {
+      H->n_hits = h[0];
+      H->walked = h[1];
+      H->n_deferred = n_def;
+      H->n_rows = nq;
+      return PD_OK;
+    }
+    cap = h[0] + 4096;  // output did not fit: rerun with the exact size
+  }
+  return fail(c, PD_ERR_INTERNAL, "Best Hit output did not converge");
+}
+
+static pd_status hits_pair_impl(pd_ctx* c, const pd_profiles* P, uint32_t gi, uint32_t gj, bool both, bool emit_all,
+                                pd_hits* H) {
+  const auto& gp = P->h_genome_ptr;
+  if (gi >= P->view.n_genomes || gj >= P->view.n_genomes || gi == gj)
+    return fail(c, PD_ERR_ARG, "genome indices must be distinct and < n_genomes");
+  pdg::QuerySet Q{};
+  Q.all_pairs = 0;
+  Q.qa0 = (uint32_t)gp[gi];
+  Q.nA = (uint32_t)(gp[gi + 1] - gp[gi]);
+  Q.ta0 = (uint32_t)gp[gj];
+  Q.ta1 = (uint32_t)gp[gj + 1];
+  Q.qb0 = (uint32_t)gp[gj];
+  Q.tb0 = (uint32_t)gp[gi];
+  Q.tb1 = (uint32_t)gp[gi + 1];
+  Q.n_queries = Q.nA + (both ? (uint32_t)(gp[gj + 1] - gp[gj]) : 0u);
+  H->ctx = c;
+  H->all_pairs = 0;
+  H->row_base = Q.qa0;
+  H->col_base = Q.ta0;
+  H->nA = Q.nA;
+  H->qa0 = Q.qa0;
+  H->qb0 = Q.qb0;
+  return run_hits(c, P, Q, emit_all, H);
+}
+
+PD_API pd_status pd_best_hits_all(pd_ctx* c, const pd_profiles* P, pd_hits** out) {
+  if (!c || !P || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    CK(cudaSetDevice(c->device));
+    std::unique_ptr<pd_hits> H(new pd_hits());
+    H->ctx = c;
+    H->all_pairs = 1;
+    pdg::QuerySet Q{};
+    Q.all_pairs = 1;
+    Q.q0 = 0;
+    Q.n_queries = P->view.n_genes;
+    pd_status st = run_hits(c, P, Q, false, H.get());
+    if (st != PD_OK) return st;
+    *out = H.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_best_hits_all");
+  }
+}
+
+PD_API pd_status pd_best_hits(pd_ctx* c, const pd_profiles* P, uint32_t gi, uint32_t gj, pd_hits** out) {
+  if (!c || !P || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    CK(cudaSetDevice(c->device));
+    std::unique_ptr<pd_hits> H(new pd_hits());
+    pd_status st = hits_pair_impl(c, P, gi, gj, false, false, H.get());
+    if (st != PD_OK) return st;
+    *out = H.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_best_hits");
+  }
+}
+
+PD_API pd_status pd_hits_get_info(const pd_hits* H, pd_hits_info* info) {
+  if (!H || !info) return PD_ERR_ARG;
+  info->n_rows = H->all_pairs ? H->n_rows : H->nA;
+  info->n_hits = H->n_hits;
+  info->row_base = H->all_pairs ? 0 : H->row_base;
+  info->col_base = H->all_pairs ? 0 : H->col_base;
+  info->n_deferred = H->n_deferred;
+  info->postings_walked = H->walked;
+  return PD_OK;
+}
+
+// CSR of the first n_rows rows of H into device buffers.
+static pd_status hits_to_csr(pd_ctx* c, const pd_hits* H, uint32_t n_rows, uint32_t col_base, Buf& row_ptr,
+                             Buf& cols, Buf& s, uint64_t* n_out) {
+  pdg::Launcher* L = &c->L;
+  Buf tmp;
+  ALLOC(row_ptr, sizeof(unsigned long long) * (n_rows + 1));
+  ALLOC(tmp, pdg::scan_temp_bytes(n_rows + 1) + 64);
+  CK(pdg::scan_u32_to_u64(L, H->row_len.as<uint32_t>(), n_rows, row_ptr.as<unsigned long long>(), tmp.p,
+                          c->stream));
+  unsigned long long n = 0;
+  CK(cudaMemcpyAsync(&n, row_ptr.as<unsigned long long>() + n_rows, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  ALLOC(cols, sizeof(int32_t) * std::max<uint64_t>(n, 1));
+  ALLOC(s, sizeof(uint32_t) * std::max<uint64_t>(n, 1));
+  if (n_rows)
+    CK(pdg::run_gather_rows(L, n_rows, H->row_off.as<unsigned long long>(), H->row_len.as<uint32_t>(),
+                            row_ptr.as<unsigned long long>(), H->out_b.as<uint32_t>(), H->out_s.as<uint32_t>(),
+                            col_base, cols.as<int32_t>(), s.as<uint32_t>(), c->stream));
+  *n_out = n;
+  return PD_OK;
+}
+
+PD_API pd_status pd_hits_copy(pd_ctx* c, const pd_hits* H, int64_t* row_ptr, int32_t* cols, uint32_t* s,
+                              uint64_t* n_hits) {
+  if (!c || !H) return PD_ERR_ARG;
+  try {
+    CK(cudaSetDevice(c->device));
+    const uint32_t n_rows = H->all_pairs ? H->n_rows : H->nA;
+    Buf rp, cb, sb;
+    uint64_t n = 0;
+    pd_status st = hits_to_csr(c, H, n_rows, H->all_pairs ? 0 : H->col_base, rp, cb, sb, &n);
+    if (st != PD_OK) return st;
+    if (n_hits) *n_hits = n;
+    if ((st = copy_out(c, row_ptr, rp.p, sizeof(int64_t) * (n_rows + 1))) != PD_OK) return st;
+    if ((st = copy_out(c, cols, cb.p, sizeof(int32_t) * n)) != PD_OK) return st;
+    if ((st = copy_out(c, s, sb.p, sizeof(uint32_t) * n)) != PD_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return PD_OK;
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_hits_copy");
+  }
+}
+
+PD_API void pd_hits_free(pd_hits* H) { delete H; }
+
+// ------------------------------------------------------------------ BBH
+static pd_status bbh_impl(pd_ctx* c, const pdg::BbhRows& R, uint64_t n_hit_slots, uint32_t a_base, uint32_t b_base,
+                          pd_bbh_set* S) {
+  pdg::Launcher* L = &c->L;
+  Buf flags, row_cnt, row_start, tmp;
+  ALLOC(flags, std::max<uint64_t>(n_hit_slots, 1));
+  ALLOC(row_cnt, sizeof(uint32_t) * std::max<uint32_t>(R.n_rows, 1));
+  ALLOC(row_start, sizeof(uint32_t) * (R.n_rows + 1));
+  ALLOC(tmp, pdg::scan_temp_bytes(R.n_rows + 1) + 64);
+  if (R.n_rows) CK(pdg::run_bbh_count(L, R, flags.as<uint8_t>(), row_cnt.as<uint32_t>(), c->stream));
+  CK(pdg::scan_u32(L, row_cnt.as<uint32_t>(), R.n_rows, row_start.as<uint32_t>(), tmp.p, c->stream));
+  uint32_t n = 0;
+  CK(cudaMemcpyAsync(&n, row_start.as<uint32_t>() + R.n_rows, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  S->ctx = c;
+  S->n = n;
+  ALLOC(S->a, sizeof(int32_t) * std::max<uint32_t>(n, 1));
+  ALLOC(S->b, sizeof(int32_t) * std::max<uint32_t>(n, 1));
+  if (R.n_rows && n)
+    CK(pdg::run_bbh_write(L, R, flags.as<uint8_t>(), row_start.as<uint32_t>(), a_base, b_base, S->a.as<int32_t>(),
+                          S->b.as<int32_t>(), c->stream));
+  CK(cudaStreamSynchronize(c->stream));  // scratch lifetime
+  return PD_OK;
+}
+
+PD_API pd_status pd_bbh_all(pd_ctx* c, const pd_profiles* P, const pd_hits* H, pd_bbh_set** out) {
+  if (!c || !P || !H || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  if (!H->all_pairs) return fail(c, PD_ERR_ARG, "pd_bbh_all needs the result of pd_best_hits_all");
+  try {
+    CK(cudaSetDevice(c->device));
+    pdg::BbhRows R{};
+    R.all_pairs = 1;
+    R.n_rows = H->n_rows;
+    R.gene_genome = P->view.gene_genome;
+    R.row_off = H->row_off.as<unsigned long long>();
+    R.row_len = H->row_len.as<uint32_t>();
+    R.hit_b = H->out_b.as<uint32_t>();
+    std::unique_ptr<pd_bbh_set> S(new pd_bbh_set());
+    pd_status st = bbh_impl(c, R, H->out_b.n / sizeof(uint32_t), 0, 0, S.get());
+    if (st != PD_OK) return st;
+    *out = S.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_bbh_all");
+  }
+}
+
+PD_API pd_status pd_bbh(pd_ctx* c, const pd_profiles* P, uint32_t gi, uint32_t gj, pd_bbh_set** out) {
+  if (!c || !P || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    CK(cudaSetDevice(c->device));
+    pd_hits H;
+    pd_status st = hits_pair_impl(c, P, gi, gj, true, false, &H);
+    if (st != PD_OK) return st;
+    pdg::BbhRows R{};
+    R.all_pairs = 0;
+    R.n_rows = H.n_rows;
+    R.nA = H.nA;
+    R.qa0 = H.qa0;
+    R.qb0 = H.qb0;
+    R.row_off = H.row_off.as<unsigned long long>();
+    R.row_len = H.row_len.as<uint32_t>();
+    R.hit_b = H.out_b.as<uint32_t>();
+    std::unique_ptr<pd_bbh_set> S(new pd_bbh_set());
+    st = bbh_impl(c, R, H.out_b.n / sizeof(uint32_t), H.qa0, H.qb0, S.get());
+    if (st != PD_OK) return st;
+    *out = S.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_bbh");
+  }
+}
+
+PD_API pd_status pd_bbh_copy(pd_ctx* c, const pd_bbh_set* S, int32_t* a, int32_t* b, uint64_t* n_pairs) {
+  if (!c || !S) return PD_ERR_ARG;
+  try {
+    if (n_pairs) *n_pairs = S->n;
+    pd_status st;
+    if ((st = copy_out(c, a, S->a.p, sizeof(int32_t) * S->n)) != PD_OK) return st;
+    if ((st = copy_out(c, b, S->b.p, sizeof(int32_t) * S->n)) != PD_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return PD_OK;
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_bbh_copy");
+  }
+}
+
+PD_API uint64_t pd_bbh_count(const pd_bbh_set* S) { return S ? S->n : 0; }
+
+PD_API void pd_bbh_free(pd_bbh_set* S) { delete S; }
+
+// ------------------------------------------------------------------ sum-min pairs
+PD_API pd_status pd_summin_pairs(pd_ctx* c, const pd_profiles* P, uint32_t gi, uint32_t gj, int32_t* a, int32_t* b,
+                                 uint32_t* s, uint64_t* n) {
+  if (!c || !P) return PD_ERR_ARG;
+  try {
+    CK(cudaSetDevice(c->device));
+    pd_hits H;
+    pd_status st = hits_pair_impl(c, P, gi, gj, false, true, &H);
+    if (st != PD_OK) return st;
+    Buf rp, cb, sb;
+    uint64_t total = 0;
+    st = hits_to_csr(c, &H, H.nA, H.col_base, rp, cb, sb, &total);
+    if (st != PD_OK) return st;
+    if (!a) {
+      if (n) *n = total;
+      return PD_OK;
+    }
+    if (n && *n < total) return fail(c, PD_ERR_ARG, "output holds fewer entries than pd_summin_pairs produces");
+    if (n) *n = total;
+    Buf ra;
+    ALLOC(ra, sizeof(int32_t) * std::max<uint64_t>(total, 1));
+    if (H.nA) {
+      CK(pdg::launch_begin(&c->L, "row_ids"));
+      k_row_ids<<<std::min<uint32_t>(H.nA, 152u * 8u), 128, 0, c->stream>>>(H.nA, rp.as<unsigned long long>(),
+                                                                            ra.as<int32_t>());
+      CK(pdg::launch_end(&c->L, "row_ids"));
+    }
+    if ((st = copy_out(c, a, ra.p, sizeof(int32_t) * total)) != PD_OK) return st;
+    if ((st = copy_out(c, b, cb.p, sizeof(int32_t) * total)) != PD_OK) return st;
+    if ((st = copy_out(c, s, sb.p, sizeof(uint32_t) * total)) != PD_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return PD_OK;
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_summin_pairs");
+  }
+}

@@ -1,0 +1,269 @@
+// pd_internal.cuh -- shared declarations of the CUDA implementation of pd.h.
+//
+// Device data layout of a profiled dataset (all arrays in HBM, built once by
+// pd_build_profiles and read by every later call):
+//
+//   gene g (global id, 0..G-1) has La[g] = max(0, |g|-k+1) k-mer windows.
+//   win_off[G+1]   uint32  exclusive prefix of La: window range of each gene.
+//   mv_len[G]      uint32  distinct k-mers of the gene (E_g <= La[g]).
+//   mv_id[W]       uint32  dense k-mer id, gene g at win_off[g] .. +mv_len[g],
+//                          ascending (the multiplicity vector of Algorithm 1,
+//                          stored in the gene's window range: "padded CSR").
+//   mv_cnt[W]      uint16  multiplicity of that k-mer in the gene.
+//   gene_genome[G] uint16  genome of each gene.
+//   bitmap[20^k/64] uint64 one bit per possible k-mer code: set if it occurs.
+//   word_rank[...]  uint32 number of set bits before each bitmap word, so the
+//                          dense id of code c is word_rank[c>>6] +
+//                          popc(bitmap[c>>6] & ((1<<(c&63))-1)); ids are
+//                          therefore ascending in code order.
+//   post_ptr[D+1]  uint32  inverted index: postings of id w are
+//   post[E]        uint32  post[post_ptr[w] .. post_ptr[w+1]), ascending by
+//                          gene, each packed as (gene << cnt_bits) | min(count,
+//                          cnt_cap) with cnt_bits = 32 - bits(G-1).  A count
+//                          equal to cnt_cap is saturated; the exact value is
+//                          in the gene's multiplicity vector.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pd.h"
+
+namespace pdg {
+
+constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+constexpr int kAlphabetSize = 20;
+
+// ---------------------------------------------------------------- errors
+// Device error block: kernels record the first error code and a detail value
+// (e.g. the offending residue position) and skip the faulty item.
+struct DevErr {
+  int code;
+  int pad;
+  unsigned long long detail;
+};
+
+__device__ __forceinline__ void raise_error(DevErr* e, int code, unsigned long long detail) {
+  if (atomicCAS(&e->code, 0, code) == 0) e->detail = detail;
+}
+
+// ---------------------------------------------------------------- helpers
+__host__ __device__ __forceinline__ uint32_t next_pow2(uint32_t x) {
+  if (x <= 1) return 1;
+  --x;
+  x |= x >> 1;
+  x |= x >> 2;
+  x |= x >> 4;
+  x |= x >> 8;
+  x |= x >> 16;
+  return x + 1;
+}
+
+// Letter -> 0..19 in ACDEFGHIKLMNPQRSTVWY order, 255 otherwise; built per block.
+__device__ __forceinline__ void init_letter_table(uint8_t* lut) {
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = 255;
+  __syncthreads();
+  if (threadIdx.x < kAlphabetSize) lut[(uint8_t)("ACDEFGHIKLMNPQRSTVWY"[threadIdx.x])] = (uint8_t)threadIdx.x;
+  __syncthreads();
+}
+
+// Ascending bitonic sort of n (a power of two) keys by the whole block.
+template <typename K>
+__device__ __forceinline__ void block_bitonic_sort(K* a, uint32_t n) {
+  for (uint32_t size = 2; size <= n; size <<= 1) {
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      for (uint32_t i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
+        uint32_t lo = 2 * i - (i & (stride - 1));
+        uint32_t hi = lo + stride;
+        bool asc = (lo & size) == 0;
+        K x = a[lo], y = a[hi];
+        if ((x > y) == asc) {
+          a[lo] = y;
+          a[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// Ascending sort of one key per lane across a full warp.
+__device__ __forceinline__ uint32_t warp_sort32(uint32_t x) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (uint32_t size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      uint32_t y = __shfl_xor_sync(0xffffffffu, x, stride);
+      bool lower = (lane & stride) == 0;
+      bool asc = (lane & size) == 0;
+      x = (lower == asc) ? min(x, y) : max(x, y);
+    }
+  }
+  return x;
+}
+
+// Inclusive warp scan of v.
+__device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v) {
+  const uint32_t lane = threadIdx.x & 31u;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= (uint32_t)o) v += y;
+  }
+  return v;
+}
+
+// Exclusive block scan; `warp_tmp` holds at least blockDim.x/32 + 1 words.
+// Returns the exclusive prefix of v; *total receives the block sum.
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tmp, uint32_t* total) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+  const uint32_t n_warps = (blockDim.x + 31) >> 5;
+  uint32_t inc = warp_inclusive_scan(v);
+  if (lane == 31) warp_tmp[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = (lane < n_warps) ? warp_tmp[lane] : 0u;
+    uint32_t wi = warp_inclusive_scan(w);
+    if (lane < n_warps) warp_tmp[lane] = wi - w;
+    if (lane == n_warps - 1) warp_tmp[n_warps] = wi;
+  }
+  __syncthreads();
+  uint32_t r = warp_tmp[warp] + inc - v;
+  *total = warp_tmp[n_warps];
+  __syncthreads();
+  return r;
+}
+
+// Exact ratio order: s1/d1 > s2/d2 by 64-bit cross-multiplication.
+__host__ __device__ __forceinline__ bool ratio_greater(uint32_t s1, uint32_t d1, uint32_t s2, uint32_t d2) {
+  return (uint64_t)s1 * (uint64_t)d2 > (uint64_t)s2 * (uint64_t)d1;
+}
+__host__ __device__ __forceinline__ bool ratio_equal(uint32_t s1, uint32_t d1, uint32_t s2, uint32_t d2) {
+  return (uint64_t)s1 * (uint64_t)d2 == (uint64_t)s2 * (uint64_t)d1;
+}
+
+// ---------------------------------------------------------------- views
+struct ProfilesView {
+  int k;
+  uint32_t n_genes, n_genomes;
+  uint64_t n_windows, n_distinct, n_entries;
+  uint32_t cnt_bits, cnt_cap, max_posting;
+  const uint32_t* win_off;
+  const uint32_t* mv_len;
+  const uint32_t* mv_id;
+  const uint16_t* mv_cnt;
+  const uint32_t* La;
+  const uint16_t* gene_genome;
+  const int32_t* genome_ptr;  // device copy, n_genomes+1
+  const unsigned long long* bitmap;
+  const uint32_t* word_rank;
+  uint64_t n_words;
+  const uint32_t* post_ptr;
+  const uint32_t* post;
+};
+
+// Target selection of one sum-min launch.
+//   all_pairs = 1: queries are genes q0..q0+n_queries-1 and each query targets
+//                  every genome except its own.
+//   all_pairs = 0: query index x < nA is gene qa0 + x targeting genes
+//                  [ta0, ta1); index x >= nA is gene qb0 + (x - nA) targeting
+//                  [tb0, tb1).
+struct QuerySet {
+  int all_pairs;
+  uint32_t q0, n_queries;
+  uint32_t qa0, nA, ta0, ta1;
+  uint32_t qb0, tb0, tb1;
+};
+
+struct HitsOut {
+  uint32_t* out_b;                   // global target gene id
+  uint32_t* out_s;                   // sum-min
+  unsigned long long out_cap;        // capacity of out_b / out_s
+  unsigned long long* cursor;        // append cursor (keeps counting past cap)
+  unsigned long long* row_off;       // per query index
+  uint32_t* row_len;                 // per query index
+  uint32_t* deferred;                // query indices for the large path
+  uint32_t* n_deferred;
+  unsigned long long* walked;        // postings visited
+};
+
+// Large-accumulator (global memory) scratch of the second tier.
+struct BigScratch {
+  uint32_t* keys;        // n_ctas * cap
+  uint32_t* vals;        // n_ctas * cap
+  unsigned long long* out;  // n_ctas * out_cap
+  uint32_t cap;          // power of two
+  uint32_t out_cap;      // power of two
+};
+
+// ---------------------------------------------------------------- launchers
+// Every launcher enqueues on `stream` and returns the launch error (if any).
+struct Launcher;  // opaque: pd_ctx side (timing + launch counting)
+cudaError_t launch_begin(Launcher* L, const char* name);
+cudaError_t launch_end(Launcher* L, const char* name);
+
+// scans (k_scan.cu)
+size_t scan_temp_bytes(uint64_t n);
+cudaError_t scan_popc_words(Launcher* L, const unsigned long long* words, uint64_t n, uint32_t* out_excl,
+                            uint32_t* total, void* temp, cudaStream_t s);
+cudaError_t scan_u32(Launcher* L, const uint32_t* in, uint64_t n, uint32_t* out_excl_np1, void* temp,
+                     cudaStream_t s);
+cudaError_t scan_u32_to_u64(Launcher* L, const uint32_t* in, uint64_t n, unsigned long long* out_excl_np1,
+                            void* temp, cudaStream_t s);
+
+// profiles (k_profiles.cu)
+cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
+                            unsigned long long* bitmap, DevErr* err, cudaStream_t s);
+cudaError_t run_mv_build(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, const uint32_t* win_off,
+                         uint32_t n_genes, int k, const unsigned long long* bitmap, const uint32_t* word_rank,
+                         uint32_t* mv_id, uint16_t* mv_cnt, uint32_t* mv_len, uint32_t* hist,
+                         const uint32_t* long_genes, uint32_t n_long, uint32_t* long_scratch,
+                         const uint32_t* long_scratch_off, uint32_t max_smem_sort, cudaStream_t s);
+cudaError_t run_post_fill(Launcher* L, const uint32_t* win_off, const uint32_t* mv_len, const uint32_t* mv_id,
+                          const uint16_t* mv_cnt, uint32_t n_genes, const uint32_t* post_ptr, uint32_t* fill,
+                          uint32_t* post, uint32_t cnt_bits, uint32_t cnt_cap, cudaStream_t s);
+cudaError_t run_post_sort(Launcher* L, const uint32_t* post_ptr, uint64_t n_lists, uint32_t* post,
+                          uint32_t* queue, uint32_t* queue_len, uint32_t max_posting, uint32_t* long_scratch,
+                          cudaStream_t s);
+cudaError_t run_max_u32(Launcher* L, const uint32_t* a, uint64_t n, uint32_t* out, cudaStream_t s);
+cudaError_t run_gene_genome(Launcher* L, const int32_t* genome_ptr, uint32_t n_genomes, uint16_t* gene_genome,
+                            cudaStream_t s);
+cudaError_t run_select_codes(Launcher* L, const unsigned long long* bitmap, const uint32_t* word_rank,
+                             uint64_t n_words, unsigned long long* code_of_id, cudaStream_t s);
+cudaError_t run_export_mv(Launcher* L, const ProfilesView& P, const unsigned long long* mv_ptr,
+                          const unsigned long long* code_of_id, unsigned long long* codes, uint32_t* counts,
+                          cudaStream_t s);
+cudaError_t run_export_index(Launcher* L, const ProfilesView& P, int32_t* genes, uint32_t* counts,
+                             cudaStream_t s);
+
+// sum-min and Best Hits (k_summin.cu)
+size_t summin_smem_bytes(uint32_t n_genomes, bool emit_all);
+cudaError_t run_summin_bh(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O, DevErr* err,
+                          bool emit_all, cudaStream_t s);
+cudaError_t run_summin_bh_big(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O,
+                              const BigScratch& B, uint32_t n_ctas, DevErr* err, bool emit_all,
+                              cudaStream_t s);
+
+// BBH and result gathering (k_bbh.cu)
+cudaError_t run_gather_rows(Launcher* L, uint32_t n_rows, const unsigned long long* row_off,
+                            const uint32_t* row_len, const unsigned long long* row_ptr, const uint32_t* in_b,
+                            const uint32_t* in_s, uint32_t col_base, int32_t* out_cols, uint32_t* out_s,
+                            cudaStream_t s);
+// BBH from Best Hit rows.  Row x belongs to gene row_gene(x); the partner row
+// of a target gene b is row_of_gene(b).  See k_bbh.cu for the two forms.
+struct BbhRows {
+  int all_pairs;               // 1: rows = all genes (row x = gene x)
+  uint32_t n_rows;
+  uint32_t nA, qa0, qb0;       // pair form: rows 0..nA-1 = genes qa0.., rest = genes qb0..
+  const uint16_t* gene_genome; // all form: genome of each gene
+  const unsigned long long* row_off;
+  const uint32_t* row_len;
+  const uint32_t* hit_b;
+};
+cudaError_t run_bbh_count(Launcher* L, const BbhRows& R, uint8_t* flags_by_hit, uint32_t* row_cnt,
+                          cudaStream_t s);
+cudaError_t run_bbh_write(Launcher* L, const BbhRows& R, const uint8_t* flags_by_hit, const uint32_t* row_start,
+                          uint32_t a_base, uint32_t b_base, int32_t* out_a, int32_t* out_b, cudaStream_t s);
+
+}  // namespace pdg

@@ -1,0 +1,367 @@
+"""Thin Python binding of libpandelos_gpu.so (the C ABI of include/pd.h).
+
+Every function keeps the C name and only marshals arguments: numpy arrays or
+torch tensors become pointers, handles stay opaque, and a non-OK status raises
+``PdError`` with the library's message.  All computation happens in the CUDA
+library; there is no Python or CPU fallback -- if the library cannot be built
+or loaded, ``load()`` raises.
+
+Device memory is taken from PyTorch's caching allocator (through the
+library's allocator hooks) and work runs on PyTorch's current CUDA stream
+unless another stream is given.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+PD_OK = 0
+STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_ALPHABET", 3: "PD_ERR_GENE_TOO_LONG",
+                4: "PD_ERR_K_RANGE", 5: "PD_ERR_OOM", 6: "PD_ERR_BUDGET", 7: "PD_ERR_CUDA",
+                8: "PD_ERR_TIMEOUT", 9: "PD_ERR_BUSY", 10: "PD_ERR_INTERNAL"}
+PD_MAX_K = 8
+PD_MAX_WINDOWS = 65535
+PD_MAX_GENOMES = 4096
+
+
+class PdError(RuntimeError):
+    def __init__(self, status: int, func: str, msg: str):
+        super().__init__(f"{func}: {STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class ProfilesInfo(C.Structure):
+    _fields_ = [("k", C.c_int), ("n_genes", C.c_uint32), ("n_genomes", C.c_uint32),
+                ("n_windows", C.c_uint64), ("n_distinct", C.c_uint64), ("n_entries", C.c_uint64),
+                ("max_posting", C.c_uint32), ("count_bits", C.c_uint32), ("device_bytes", C.c_uint64)]
+
+
+class HitsInfo(C.Structure):
+    _fields_ = [("n_rows", C.c_uint32), ("n_hits", C.c_uint64), ("row_base", C.c_uint32),
+                ("col_base", C.c_uint32), ("n_deferred", C.c_uint32), ("postings_walked", C.c_uint64)]
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) of every exported function
+_P = C.c_void_p
+_PP = C.POINTER(C.c_void_p)
+_SIGNATURES = [
+    ("pd_ctx_create", C.c_int, [C.c_int, _P, ALLOC_FN, FREE_FN, _P, _PP]),
+    ("pd_ctx_destroy", None, [_P]),
+    ("pd_ctx_set_stream", C.c_int, [_P, _P]),
+    ("pd_last_error", C.c_char_p, [_P]),
+    ("pd_ctx_launch_count", C.c_uint64, [_P]),
+    ("pd_ctx_set_timing", C.c_int, [_P, C.c_int]),
+    ("pd_ctx_kernel_time", C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
+    ("pd_ctx_reset_timing", C.c_int, [_P]),
+    ("pd_choose_k", C.c_int, [C.c_uint64, C.c_int]),
+    ("pd_build_profiles", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, C.c_int, _PP]),
+    ("pd_profiles_get_info", C.c_int, [_P, C.POINTER(ProfilesInfo)]),
+    ("pd_profiles_copy_mv", C.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("pd_profiles_copy_index", C.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("pd_profiles_free", None, [_P]),
+    ("pd_best_hits_all", C.c_int, [_P, _P, _PP]),
+    ("pd_best_hits", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _PP]),
+    ("pd_hits_get_info", C.c_int, [_P, C.POINTER(HitsInfo)]),
+    ("pd_hits_copy", C.c_int, [_P, _P, _P, _P, _P, C.POINTER(C.c_uint64)]),
+    ("pd_hits_free", None, [_P]),
+    ("pd_bbh_all", C.c_int, [_P, _P, _P, _PP]),
+    ("pd_bbh", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _PP]),
+    ("pd_bbh_copy", C.c_int, [_P, _P, _P, _P, C.POINTER(C.c_uint64)]),
+    ("pd_bbh_count", C.c_uint64, [_P]),
+    ("pd_bbh_free", None, [_P]),
+    ("pd_summin_pairs", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _P, _P, _P, C.POINTER(C.c_uint64)]),
+]
+EXPORTED = [s[0] for s in _SIGNATURES]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True) -> C.CDLL:
+    """Load libpandelos_gpu.so (building it first if needed); raises if impossible."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libpandelos_gpu.so not found at {path}; build it with __graft_entry__.build()")
+        lib = C.CDLL(path)
+        for name, res, args in _SIGNATURES:
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _ptr(x):
+    """Raw address of a numpy array or torch tensor (contiguous), or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to the library must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to the library must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, int):
+        return x
+    raise TypeError(f"cannot pass {type(x)} to the library")
+
+
+def _check(ctx, st, func):
+    if st != PD_OK:
+        msg = _lib.pd_last_error(ctx.handle if ctx is not None else None)
+        raise PdError(st, func, msg.decode() if msg else "")
+
+
+# ---------------------------------------------------------------- context
+class Ctx:
+    """Owns a pd_ctx*; device memory comes from torch's caching allocator."""
+
+    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True):
+        import torch
+        lib = load()
+        self.device = int(device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        elif hasattr(stream, "cuda_stream"):
+            stream = stream.cuda_stream
+        self._keep = []
+        if use_torch_allocator:
+            dev = self.device
+
+            def _alloc(nbytes, strm, user):
+                try:
+                    return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm or 0)
+                except Exception:
+                    return None
+
+            def _free(p, nbytes, strm, user):
+                torch.cuda.caching_allocator_delete(p)
+
+            a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+            self._keep = [a, f]
+        else:
+            a, f = ALLOC_FN(), FREE_FN()
+        h = C.c_void_p()
+        st = lib.pd_ctx_create(self.device, stream, a, f, None, C.byref(h))
+        if st != PD_OK:
+            raise PdError(st, "pd_ctx_create", "context creation failed")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.pd_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def pd_ctx_create(device: int = 0, stream=None, use_torch_allocator: bool = True) -> Ctx:
+    return Ctx(device, stream, use_torch_allocator)
+
+
+def pd_ctx_destroy(ctx: Ctx) -> None:
+    ctx.close()
+
+
+def pd_ctx_set_stream(ctx: Ctx, stream) -> None:
+    s = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+    _check(ctx, _lib.pd_ctx_set_stream(ctx.handle, s), "pd_ctx_set_stream")
+
+
+def pd_last_error(ctx: Ctx) -> str:
+    return _lib.pd_last_error(ctx.handle).decode()
+
+
+def pd_ctx_launch_count(ctx: Ctx) -> int:
+    return int(_lib.pd_ctx_launch_count(ctx.handle))
+
+
+def pd_ctx_set_timing(ctx: Ctx, enable: bool) -> None:
+    _check(ctx, _lib.pd_ctx_set_timing(ctx.handle, int(bool(enable))), "pd_ctx_set_timing")
+
+
+def pd_ctx_kernel_time(ctx: Ctx, name: str | None = None):
+    """(milliseconds, launches) summed over kernel `name` (None: all)."""
+    ms, n = C.c_double(0), C.c_uint64(0)
+    _check(ctx, _lib.pd_ctx_kernel_time(ctx.handle, name.encode() if name else None, C.byref(ms), C.byref(n)),
+           "pd_ctx_kernel_time")
+    return ms.value, n.value
+
+
+def pd_ctx_reset_timing(ctx: Ctx) -> None:
+    _check(ctx, _lib.pd_ctx_reset_timing(ctx.handle), "pd_ctx_reset_timing")
+
+
+def pd_choose_k(total_residues: int, alphabet: int = 20) -> int:
+    return int(load().pd_choose_k(int(total_residues), int(alphabet)))
+
+
+# ---------------------------------------------------------------- handles
+class _Handle:
+    _free_name = ""
+
+    def __init__(self, ctx: Ctx, h: C.c_void_p):
+        self.ctx = ctx
+        self.handle = h
+
+    def free(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            getattr(_lib, self._free_name)(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.free()
+
+
+class Profiles(_Handle):
+    _free_name = "pd_profiles_free"
+
+
+class Hits(_Handle):
+    _free_name = "pd_hits_free"
+
+
+class BbhSet(_Handle):
+    _free_name = "pd_bbh_free"
+
+
+def pd_build_profiles(ctx: Ctx, residues, gene_ptr, genome_ptr, k: int) -> Profiles:
+    """residues uint8[N], gene_ptr int64[G+1], genome_ptr int32[n+1]: host or device."""
+    n_res = int(residues.shape[0])
+    n_genes = int(gene_ptr.shape[0]) - 1
+    n_genomes = int(genome_ptr.shape[0]) - 1
+    h = C.c_void_p()
+    st = _lib.pd_build_profiles(ctx.handle, _ptr(residues), n_res, _ptr(gene_ptr), n_genes, _ptr(genome_ptr),
+                                n_genomes, int(k), C.byref(h))
+    _check(ctx, st, "pd_build_profiles")
+    return Profiles(ctx, h)
+
+
+def pd_profiles_get_info(prof: Profiles) -> ProfilesInfo:
+    info = ProfilesInfo()
+    _check(prof.ctx, _lib.pd_profiles_get_info(prof.handle, C.byref(info)), "pd_profiles_get_info")
+    return info
+
+
+def pd_profiles_copy_mv(ctx: Ctx, prof: Profiles):
+    """(mv_ptr int64[G+1], codes uint64[E], counts uint32[E], La uint32[G]) on the host."""
+    info = pd_profiles_get_info(prof)
+    G, E = info.n_genes, info.n_entries
+    mv_ptr = np.zeros(G + 1, np.int64)
+    codes = np.zeros(max(E, 1), np.uint64)
+    counts = np.zeros(max(E, 1), np.uint32)
+    La = np.zeros(max(G, 1), np.uint32)
+    _check(ctx, _lib.pd_profiles_copy_mv(ctx.handle, prof.handle, _ptr(mv_ptr), _ptr(codes), _ptr(counts),
+                                         _ptr(La)), "pd_profiles_copy_mv")
+    return mv_ptr, codes[:E], counts[:E], La[:G]
+
+
+def pd_profiles_copy_index(ctx: Ctx, prof: Profiles):
+    """(post_ptr int64[D+1], codes uint64[D], genes int32[E], counts uint32[E]) on the host."""
+    info = pd_profiles_get_info(prof)
+    D, E = info.n_distinct, info.n_entries
+    post_ptr = np.zeros(D + 1, np.int64)
+    codes = np.zeros(max(D, 1), np.uint64)
+    genes = np.zeros(max(E, 1), np.int32)
+    counts = np.zeros(max(E, 1), np.uint32)
+    _check(ctx, _lib.pd_profiles_copy_index(ctx.handle, prof.handle, _ptr(post_ptr), _ptr(codes), _ptr(genes),
+                                            _ptr(counts)), "pd_profiles_copy_index")
+    return post_ptr, codes[:D], genes[:E], counts[:E]
+
+
+def pd_best_hits_all(ctx: Ctx, prof: Profiles) -> Hits:
+    h = C.c_void_p()
+    _check(ctx, _lib.pd_best_hits_all(ctx.handle, prof.handle, C.byref(h)), "pd_best_hits_all")
+    return Hits(ctx, h)
+
+
+def pd_best_hits(ctx: Ctx, prof: Profiles, gi: int, gj: int) -> Hits:
+    h = C.c_void_p()
+    _check(ctx, _lib.pd_best_hits(ctx.handle, prof.handle, int(gi), int(gj), C.byref(h)), "pd_best_hits")
+    return Hits(ctx, h)
+
+
+def pd_hits_get_info(hits: Hits) -> HitsInfo:
+    info = HitsInfo()
+    _check(hits.ctx, _lib.pd_hits_get_info(hits.handle, C.byref(info)), "pd_hits_get_info")
+    return info
+
+
+def pd_hits_copy(ctx: Ctx, hits: Hits, row_ptr=None, cols=None, s=None):
+    """Copy Best Hits as CSR.  Without buffers, allocates host arrays and returns
+    (row_ptr int64[n_rows+1], cols int32[n], s uint32[n])."""
+    if row_ptr is None and cols is None and s is None:
+        info = pd_hits_get_info(hits)
+        row_ptr = np.zeros(info.n_rows + 1, np.int64)
+        cols = np.zeros(max(info.n_hits, 1), np.int32)
+        s = np.zeros(max(info.n_hits, 1), np.uint32)
+        n = C.c_uint64(0)
+        _check(ctx, _lib.pd_hits_copy(ctx.handle, hits.handle, _ptr(row_ptr), _ptr(cols), _ptr(s), C.byref(n)),
+               "pd_hits_copy")
+        return row_ptr, cols[:n.value], s[:n.value]
+    n = C.c_uint64(0)
+    _check(ctx, _lib.pd_hits_copy(ctx.handle, hits.handle, _ptr(row_ptr), _ptr(cols), _ptr(s), C.byref(n)),
+           "pd_hits_copy")
+    return int(n.value)
+
+
+def pd_bbh_all(ctx: Ctx, prof: Profiles, hits: Hits) -> BbhSet:
+    h = C.c_void_p()
+    _check(ctx, _lib.pd_bbh_all(ctx.handle, prof.handle, hits.handle, C.byref(h)), "pd_bbh_all")
+    return BbhSet(ctx, h)
+
+
+def pd_bbh(ctx: Ctx, prof: Profiles, gi: int, gj: int) -> BbhSet:
+    h = C.c_void_p()
+    _check(ctx, _lib.pd_bbh(ctx.handle, prof.handle, int(gi), int(gj), C.byref(h)), "pd_bbh")
+    return BbhSet(ctx, h)
+
+
+def pd_bbh_count(bbh: BbhSet) -> int:
+    return int(_lib.pd_bbh_count(bbh.handle))
+
+
+def pd_bbh_copy(ctx: Ctx, bbh: BbhSet, a=None, b=None):
+    """Copy pairs.  Without buffers returns a host int32 array [n, 2]."""
+    if a is None and b is None:
+        n = pd_bbh_count(bbh)
+        a = np.zeros(max(n, 1), np.int32)
+        b = np.zeros(max(n, 1), np.int32)
+        _check(ctx, _lib.pd_bbh_copy(ctx.handle, bbh.handle, _ptr(a), _ptr(b), None), "pd_bbh_copy")
+        return np.stack([a[:n], b[:n]], axis=1)
+    n = C.c_uint64(0)
+    _check(ctx, _lib.pd_bbh_copy(ctx.handle, bbh.handle, _ptr(a), _ptr(b), C.byref(n)), "pd_bbh_copy")
+    return int(n.value)
+
+
+def pd_summin_pairs(ctx: Ctx, prof: Profiles, gi: int, gj: int):
+    """All (a, b, s) with s >= 1 between genomes gi and gj (local ids), host arrays."""
+    n = C.c_uint64(0)
+    _check(ctx, _lib.pd_summin_pairs(ctx.handle, prof.handle, int(gi), int(gj), None, None, None, C.byref(n)),
+           "pd_summin_pairs")
+    cnt = n.value
+    a = np.zeros(max(cnt, 1), np.int32)
+    b = np.zeros(max(cnt, 1), np.int32)
+    s = np.zeros(max(cnt, 1), np.uint32)
+    _check(ctx, _lib.pd_summin_pairs(ctx.handle, prof.handle, int(gi), int(gj), _ptr(a), _ptr(b), _ptr(s),
+                                     C.byref(n)), "pd_summin_pairs")
+    return a[:cnt], b[:cnt], s[:cnt]

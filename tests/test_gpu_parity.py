@@ -1,0 +1,239 @@
+"""GPU path (through the C ABI) against the CPU oracle: bit-exact.
+
+Every sum-min, every Best Hit index and every Bidirectional Best Hit pair must
+equal the oracle's; the multiplicity vectors and the inverted index must equal
+the oracle's k-mer counts.  Sizes span several thread-block tiles with ragged
+tails (genes of 80..600 residues, 250 genes per genome) plus the edge cases:
+k = 1, genes shorter than k, empty genes, ties, rows without candidates,
+inputs that overflow the shared-memory accumulator, saturated posting counts.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_23679_gb300 import pd, synth
+from tests import _golden
+from tests._gpu import GpuRun, all_pairs_row_slice, csr_lists, oracle_nonzero, oracle_pairs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    torch.cuda.init()
+    c = pd.pd_ctx_create(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def pan4(ctx):
+    ds = synth.workload("pan4x250")
+    k = oracle.choose_k(ds.n_residues)
+    assert k == 5
+    run = GpuRun(ctx, ds, k)
+    pairs = list(itertools.permutations(range(ds.n_genomes), 2))
+    return run, oracle_pairs(ds, k, pairs, n_threads=4)
+
+
+# ------------------------------------------------------------------ hand-worked examples
+@pytest.mark.parametrize("fname", _golden.all_fixtures())
+def test_golden_on_gpu(ctx, fname):
+    g = _golden.load(fname)
+    ds = synth.from_strings([g.rows, g.cols])
+    run = GpuRun(ctx, ds, g.k)
+    want = {(a, b): s for a, row in enumerate(g.S) for b, (s, _) in enumerate(row) if s > 0}
+    assert run.summin(0, 1) == want
+    rows, _ = run.best_hits(0, 1)
+    assert rows == g.row_bh
+    cols, _ = run.best_hits(1, 0)
+    assert cols == g.col_bh
+    assert run.bbh(0, 1) == g.bbh
+    rp, cbh, s, bbh, _ = run.all_pairs()
+    nr = len(g.rows)
+    assert [all_pairs_row_slice(ds, rp, cbh, a, 1) for a in range(nr)] == g.row_bh
+    assert [tuple(x) for x in bbh.tolist()] == [(a, nr + b) for a, b in g.bbh]
+
+
+# ------------------------------------------------------------------ profiles
+def test_multiplicity_vectors(pan4, ctx):
+    run, _ = pan4
+    ds = run.ds
+    prof = oracle.Profiles(ds.residues, ds.gene_ptr, run.k)
+    mv, La = run.mv()
+    for g in range(ds.n_genes):
+        kmers, cnt = prof.mv(g)
+        assert mv[g][0] == kmers and mv[g][1] == cnt.tolist(), f"gene {g}"
+        assert La[g] == prof.La(g)
+    assert run.info.n_windows == sum(prof.La(g) for g in range(ds.n_genes))
+
+
+def test_inverted_index(pan4, ctx):
+    run, _ = pan4
+    ds = run.ds
+    prof = oracle.Profiles(ds.residues, ds.gene_ptr, run.k)
+    expect = {}
+    for g in range(ds.n_genes):
+        kmers, cnt = prof.mv(g)
+        for km, c in zip(kmers, cnt):
+            expect.setdefault(km, []).append((g, int(c)))
+    post_ptr, codes, genes, counts = pd.pd_profiles_copy_index(ctx, run.prof)
+    got = {}
+    from tests._gpu import decode_code
+    for w in range(len(codes)):
+        km = decode_code(int(codes[w]), run.k)
+        got[km] = list(zip(genes[post_ptr[w]:post_ptr[w + 1]].tolist(), counts[post_ptr[w]:post_ptr[w + 1]].tolist()))
+    assert got == expect
+    assert list(codes) == sorted(codes)
+    assert run.info.n_distinct == len(expect)
+
+
+# ------------------------------------------------------------------ sum-min, BH, BBH per genome pair
+def test_summin_every_pair(pan4):
+    run, ref = pan4
+    for (gi, gj), R in ref.items():
+        assert run.summin(gi, gj) == oracle_nonzero(R), f"pair {gi},{gj}"
+
+
+def test_best_hits_every_pair(pan4):
+    run, ref = pan4
+    for (gi, gj), R in ref.items():
+        rows, svals = run.best_hits(gi, gj)
+        assert rows == csr_lists(R.row_ptr, R.row_col), f"pair {gi},{gj}"
+        for a, (cols, ss) in enumerate(zip(rows, svals)):
+            assert ss == [int(R.S[a, b]) for b in cols]
+
+
+def test_bbh_every_pair(pan4):
+    run, ref = pan4
+    for (gi, gj), R in ref.items():
+        assert run.bbh(gi, gj) == [tuple(x) for x in R.bbh.tolist()], f"pair {gi},{gj}"
+
+
+def test_all_pairs_equals_oracle(pan4):
+    run, ref = pan4
+    ds = run.ds
+    rp, cols, s, bbh, info = run.all_pairs()
+    gp = ds.genome_ptr
+    for (gi, gj), R in ref.items():
+        got = [all_pairs_row_slice(ds, rp, cols, int(gp[gi]) + a, gj) for a in range(R.S.shape[0])]
+        assert got == csr_lists(R.row_ptr, R.row_col), f"pair {gi},{gj}"
+    want = []
+    for gi, gj in itertools.combinations(range(ds.n_genomes), 2):
+        want += [(int(gp[gi]) + a, int(gp[gj]) + b) for a, b in ref[(gi, gj)].bbh.tolist()]
+    assert [tuple(x) for x in bbh.tolist()] == sorted(want)
+    assert info.n_deferred == 0
+
+
+def test_all_pairs_is_deterministic(pan4):
+    run, _ = pan4
+    r1 = run.all_pairs()
+    r2 = run.all_pairs()
+    for x, y in zip(r1[:4], r2[:4]):
+        assert np.array_equal(x, y)
+
+
+def test_device_inputs_match_host_inputs(pan4, ctx):
+    run, _ = pan4
+    dev = GpuRun(ctx, run.ds, run.k, device_inputs=True)
+    for x, y in zip(run.all_pairs()[:4], dev.all_pairs()[:4]):
+        assert np.array_equal(x, y)
+
+
+# ------------------------------------------------------------------ edge cases
+@pytest.mark.parametrize("seed", range(8))
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_tiny_random_against_oracle(ctx, seed, k):
+    letters = [b"AC", b"ACD", b"ACDEFGHIKL", synth.ALPHABET][seed % 4]
+    ds = synth.random_tiny(1000 + seed * 3 + k, n_genomes=3, max_genes=7, max_len=40, letters=letters)
+    run = GpuRun(ctx, ds, k)
+    pairs = list(itertools.permutations(range(ds.n_genomes), 2))
+    ref = oracle_pairs(ds, k, pairs)
+    for (gi, gj), R in ref.items():
+        assert run.summin(gi, gj) == oracle_nonzero(R)
+        assert run.best_hits(gi, gj)[0] == csr_lists(R.row_ptr, R.row_col)
+        assert run.bbh(gi, gj) == [tuple(x) for x in R.bbh.tolist()]
+    rp, cols, s, bbh, _ = run.all_pairs()
+    gp = ds.genome_ptr
+    for (gi, gj), R in ref.items():
+        got = [all_pairs_row_slice(ds, rp, cols, int(gp[gi]) + a, gj) for a in range(R.S.shape[0])]
+        assert got == csr_lists(R.row_ptr, R.row_col)
+
+
+def test_empty_genes_and_genomes(ctx):
+    ds = synth.from_strings([[b"", b"ACDEF", b"A"], [], [b"ACDEG", b""], [b"CDEF"]])
+    run = GpuRun(ctx, ds, 3)
+    ref = oracle_pairs(ds, 3, [(0, 2), (2, 0), (0, 3), (2, 3)])
+    for (gi, gj), R in ref.items():
+        assert run.summin(gi, gj) == oracle_nonzero(R)
+        assert run.bbh(gi, gj) == [tuple(x) for x in R.bbh.tolist()]
+    rp, cols, s, bbh, _ = run.all_pairs()
+    assert len(rp) == ds.n_genes + 1
+    assert run.best_hits(0, 1)[0] == [[], [], []]  # empty target genome
+
+
+def test_k_equal_to_gene_length(ctx):
+    ds = synth.from_strings([[b"ACDEFGHIKL", b"ACDEFGHIKM"], [b"ACDEFGHIKL", b"ACDEFGHIK"]])
+    run = GpuRun(ctx, ds, 8)
+    ref = oracle_pairs(ds, 8, [(0, 1)])[(0, 1)]
+    assert run.summin(0, 1) == oracle_nonzero(ref)
+    assert run.bbh(0, 1) == [tuple(x) for x in ref.bbh.tolist()]
+
+
+def test_errors_are_reported(ctx):
+    bad = synth.from_strings([[b"ACDX"], [b"ACD"]])
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_build_profiles(ctx, bad.residues, bad.gene_ptr, bad.genome_ptr, 2)
+    assert e.value.status == 2
+    ok = synth.from_strings([[b"ACD"], [b"ACD"]])
+    for k in (0, pd.PD_MAX_K + 1):
+        with pytest.raises(pd.PdError) as e:
+            pd.pd_build_profiles(ctx, ok.residues, ok.gene_ptr, ok.genome_ptr, k)
+        assert e.value.status == 4
+    long = synth.from_strings([[b"A" * (pd.PD_MAX_WINDOWS + 2)], [b"A"]])
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_build_profiles(ctx, long.residues, long.gene_ptr, long.genome_ptr, 1)
+    assert e.value.status == 3
+    run = GpuRun(ctx, ok, 2)
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_best_hits(ctx, run.prof, 0, 0)
+    assert e.value.status == 1
+    # the context stays usable after errors
+    assert run.bbh(0, 1) == [(0, 0)]
+
+
+def test_accumulator_overflow_takes_the_large_path(ctx):
+    # one query shares a k-mer with 5000 distinct targets (> 3/4 of the shared
+    # table) and ties with all of them (> the shared Best Hit list)
+    rng = np.random.default_rng(7)
+    targets = [b"AC" + bytes(rng.choice(list(b"FGHIKLMNPQRSTVWY"), size=6)) for _ in range(5000)]
+    ds = synth.from_strings([[b"ACDE", b"GGGG"], targets])
+    run = GpuRun(ctx, ds, 2)
+    R = oracle_pairs(ds, 2, [(0, 1)])[(0, 1)]
+    assert run.summin(0, 1) == oracle_nonzero(R)
+    rows, _ = run.best_hits(0, 1)
+    assert rows == csr_lists(R.row_ptr, R.row_col)
+    assert run.bbh(0, 1) == [tuple(x) for x in R.bbh.tolist()]
+    rp, cols, s, bbh, info = run.all_pairs()
+    assert info.n_deferred >= 1
+    assert [all_pairs_row_slice(ds, rp, cols, a, 1) for a in range(2)] == csr_lists(R.row_ptr, R.row_col)
+
+
+def test_saturated_posting_counts_and_long_genes(ctx):
+    # > 2^17 genes leave 14 count bits in a packed posting (cap 16383); two
+    # long one-letter genes exceed it, so the exact count is looked up.
+    n_empty = 70000
+    ds = synth.from_strings([[b"A" * 20000] + [b""] * n_empty, [b"A" * 17000 + b"C"] + [b""] * n_empty])
+    run = GpuRun(ctx, ds, 1)
+    assert run.info.count_bits == 14
+    pair = synth.from_strings([[b"A" * 20000], [b"A" * 17000 + b"C"]])
+    prof = oracle.Profiles(pair.residues, pair.gene_ptr, 1)
+    s, d = prof.summin(0, 1)
+    assert (s, d) == (17000, 20001)
+    assert run.summin(0, 1) == {(0, 0): s}
+    assert run.bbh(0, 1) == [(0, 0)]
+    _, _, gen, cnt = pd.pd_profiles_copy_index(ctx, run.prof)
+    assert sorted(cnt.tolist()) == [1, 17000, 20000]
