@@ -209,7 +209,8 @@ def test_accumulator_overflow_takes_the_large_path(ctx):
     # one query shares a k-mer with 5000 distinct targets (> 3/4 of the shared
     # table) and ties with all of them (> the shared Best Hit list)
     rng = np.random.default_rng(7)
-    targets = [b"AC" + bytes(rng.choice(list(b"FGHIKLMNPQRSTVWY"), size=6)) for _ in range(5000)]
+    letters = np.frombuffer(b"FGHIKLMNPQRSTVWY", np.uint8)
+    targets = [b"AC" + rng.choice(letters, size=6).tobytes() for _ in range(5000)]
     ds = synth.from_strings([[b"ACDE", b"GGGG"], targets])
     run = GpuRun(ctx, ds, 2)
     R = oracle_pairs(ds, 2, [(0, 1)])[(0, 1)]
