@@ -2,25 +2,32 @@
 // selection ("Best Hit detection phase", Algorithm 2, Eqs. (5) and (8)).
 //
 // One thread block owns one query gene a at a time:
-//   1. stage a chunk of a's multiplicity vector (id, mult_a) in shared memory
-//      with the posting range of each id (restricted by binary search to the
-//      target gene range in the pair form) and a block prefix sum of the
-//      range lengths, so that the chunk's postings form one flat index space;
-//   2. every thread walks flat posting indices (consecutive threads read
-//      consecutive postings: coalesced), unpacks (b, mult_b) and adds
-//      min(mult_a, mult_b) to b's accumulator in a shared-memory open-
-//      addressing hash table: after all chunks, acc[b] = s(a, b) =
-//      sum over shared k-mers of min(mult) (Eq. (5) numerator), exactly;
-//   3. Best Hits: per target genome, the maximum of s / (La + Lb - s) is kept
-//      as a (s, den) pair updated by compare-and-swap with a 64-bit
+//   1. stage a chunk of a's multiplicity vector in shared memory: for each
+//      k-mer its multiplicity and posting range (stored with the vector, so
+//      this read is coalesced; in the pair form the range is narrowed by
+//      binary search to the target genome), and a block prefix sum of the
+//      range lengths: the chunk's postings form one flat index space;
+//   2. merge-path walk: thread t takes the flat range [t*P, (t+1)*P), finds
+//      its first k-mer by one binary search and then advances sequentially;
+//      postings are loaded in batches of four before any is used; each
+//      posting (b, mult_b) adds min(mult_a, mult_b) to b's accumulator in an
+//      open-addressing hash.  After all chunks acc[b] = s(a, b), the Eq. (5)
+//      numerator, exactly;
+//   3. Best Hits: per target genome the maximum ratio s / (La + Lb - s) is
+//      kept as an (s, den) pair updated by compare-and-swap under a 64-bit
 //      cross-multiplication order; every accumulator whose ratio equals its
 //      genome's maximum (again by cross-multiplication) is a Best Hit (Eq. (8),
-//      ties kept); the block sorts them by gene and appends them to the output.
+//      ties kept).  The second pass also clears the slots it reads, so the
+//      table is clean for the next query.  Each hit is written at its rank
+//      among the query's hits (ascending gene): rows come out sorted without a
+//      sorting network.
 // The similarity matrix S_ij is never materialised: only pairs sharing a
-// k-mer are touched.  A query whose accumulator would pass 3/4 of the shared
-// table, or whose Best Hit list does not fit, is deferred to the second tier,
-// which runs the same code with the table in global memory sized for every
-// possible target, so results are exact for any input.
+// k-mer are touched.  A query whose insertions probe too far (a nearly full
+// table), or whose Best Hit list does not fit, is deferred to the next tier:
+// 4096 slots
+// in shared memory (256 threads) -> 16384 slots in shared memory (1024
+// threads, one block per SM) -> a global-memory table sized for every
+// possible target.  Results are exact and independent of the tier.
 #include <algorithm>
 
 #include "pd_internal.cuh"
@@ -28,19 +35,11 @@
 namespace pdg {
 namespace {
 
-constexpr int kThreads = 256;
-constexpr uint32_t kCap = 4096;     // shared hash slots (power of two)
-constexpr uint32_t kChunk = 1024;   // query k-mers staged per round
-constexpr uint32_t kItems = kChunk / kThreads;
-constexpr uint32_t kOutCap = 1024;  // Best Hit entries per query in the shared tier
-constexpr uint32_t kMinCap = 64;
-
 struct Scalars {
-  uint32_t n_used;
   uint32_t n_out;
   uint32_t overflow;
   uint32_t base_lo, base_hi;
-  uint32_t warp_tmp[kThreads / 32 + 1];
+  uint32_t warp_tmp[33];
 };
 
 __device__ __forceinline__ uint32_t hash_gene(uint32_t b) {
@@ -48,24 +47,25 @@ __device__ __forceinline__ uint32_t hash_gene(uint32_t b) {
   return h ^ (h >> 15);
 }
 
-// Add m to the accumulator of gene b.  Returns false when the table is over
-// its load limit or full (the caller defers the query).
-__device__ __forceinline__ bool acc_add(uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t b, uint32_t m,
-                                        uint32_t* n_used, uint32_t limit) {
+// Probes allowed before a query counts as overflowing its table.  With the
+// load limited this way (and a mixing hash) long chains mean a nearly full
+// table; the query then moves to a larger tier, so the bound never changes a
+// result, only where it is computed.
+constexpr uint32_t kMaxProbe = 64;
+
+// Add m to the accumulator of gene b.  Returns false after kMaxProbe probes
+// without finding b or a free slot (the query is deferred).
+__device__ __forceinline__ bool acc_add(uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t b, uint32_t m) {
   uint32_t h = hash_gene(b) & mask;
-  for (uint32_t probe = 0; probe <= mask; ++probe) {
-    uint32_t k = *((volatile uint32_t*)&keys[h]);
+  for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
+    const uint32_t k = *((volatile uint32_t*)&keys[h]);
     if (k == b) {
       atomicAdd(&vals[h], m);
       return true;
     }
     if (k == kEmpty) {
-      uint32_t prev = atomicCAS(&keys[h], kEmpty, b);
-      if (prev == kEmpty) {
-        atomicAdd(&vals[h], m);
-        return atomicAdd(n_used, 1u) < limit;
-      }
-      if (prev == b) {
+      const uint32_t prev = atomicCAS(&keys[h], kEmpty, b);
+      if (prev == kEmpty || prev == b) {
         atomicAdd(&vals[h], m);
         return true;
       }
@@ -78,16 +78,18 @@ __device__ __forceinline__ bool acc_add(uint32_t* keys, uint32_t* vals, uint32_t
 __device__ __forceinline__ uint32_t lower_bound_post(const uint32_t* __restrict__ post, uint32_t lo, uint32_t hi,
                                                      unsigned long long key) {
   while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
+    const uint32_t mid = (lo + hi) >> 1;
     if ((unsigned long long)post[mid] < key) lo = mid + 1; else hi = mid;
   }
   return lo;
 }
 
 __device__ __forceinline__ uint32_t mv_count_of(const ProfilesView& P, uint32_t g, uint32_t id) {
-  uint32_t lo = P.win_off[g], end = lo + P.mv_len[g], hi = end;
+  uint32_t lo = P.win_off[g];
+  const uint32_t end = lo + P.mv_n[g];
+  uint32_t hi = end;
   while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
+    const uint32_t mid = (lo + hi) >> 1;
     if (P.mv_id[mid] < id) lo = mid + 1; else hi = mid;
   }
   return (lo < end && P.mv_id[lo] == id) ? P.mv_cnt[lo] : 0u;
@@ -106,43 +108,64 @@ __device__ __forceinline__ void best_update(unsigned long long* slot, uint32_t s
   }
 }
 
-template <bool kBig, bool kEmitAll>
+template <int kThreads>
+struct Chunk {
+  static constexpr uint32_t kSize = 2 * kThreads;  // query k-mers staged per round
+  static constexpr uint32_t kItems = 2;
+  static constexpr size_t kBytes = (((size_t)kSize * 4 + (size_t)(kSize + 1) * 4 + (size_t)kSize * 2) + 15) & ~(size_t)15;
+};
+
+// Table geometry of one call (shared or global memory).
+struct Table {
+  uint32_t* keys;
+  uint32_t* vals;
+  unsigned long long* out;
+  uint32_t cap;      // power of two, a multiple of the block size
+  uint32_t out_cap;  // hits (or emitted pairs) that fit in `out`
+};
+
+template <int kThreads, bool kEmitAll, uint32_t kSlots>
 __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P, const QuerySet& Q,
-                                              const HitsOut& O, DevErr* err, uint32_t* keys, uint32_t* vals,
-                                              uint32_t cap_max, unsigned long long* out, uint32_t out_cap,
-                                              uint32_t* c_lo, uint32_t* c_off, uint16_t* c_cnt,
+                                              const HitsOut& O, const TierIO& T, DevErr* err, const Table& tb,
+                                              uint32_t* c_post, uint32_t* c_off, uint16_t* c_cnt,
                                               unsigned long long* best, Scalars* sh) {
-  // ---- query gene and its targets
-  uint32_t a, tlo, thi, own0 = 0, own1 = 0;
+  constexpr uint32_t kChunk = Chunk<kThreads>::kSize, kItems = Chunk<kThreads>::kItems;
+  uint32_t* keys = tb.keys;
+  uint32_t* vals = tb.vals;
+  unsigned long long* out = tb.out;
+  const uint32_t mask = tb.cap - 1u;
+  // ---- query gene, its output row and its targets
+  uint32_t a, row, own0 = 0, own1 = 0;
+  unsigned long long key_lo = 0, key_hi = 0;
   if (Q.all_pairs) {
-    a = Q.q0 + qi;
+    a = Q.order ? Q.order[qi] : Q.q0 + qi;
+    row = a;
     const uint32_t gg = P.gene_genome[a];
     own0 = (uint32_t)P.genome_ptr[gg];
     own1 = (uint32_t)P.genome_ptr[gg + 1];
-    tlo = 0;
-    thi = P.n_genes;
-  } else if (qi < Q.nA) {
-    a = Q.qa0 + qi;
-    tlo = Q.ta0;
-    thi = Q.ta1;
   } else {
-    a = Q.qb0 + (qi - Q.nA);
-    tlo = Q.tb0;
-    thi = Q.tb1;
+    uint32_t tlo, thi;
+    if (qi < Q.nA) {
+      a = Q.qa0 + qi;
+      tlo = Q.ta0;
+      thi = Q.ta1;
+    } else {
+      a = Q.qb0 + (qi - Q.nA);
+      tlo = Q.tb0;
+      thi = Q.tb1;
+    }
+    row = qi;
+    key_lo = (unsigned long long)tlo << P.cnt_bits;
+    key_hi = (unsigned long long)thi << P.cnt_bits;
   }
-  const uint32_t m0 = P.win_off[a], E = P.mv_len[a], La_a = P.La[a];
+  const uint32_t m0 = P.win_off[a], E = P.mv_n[a], La_a = P.La[a];
   const uint32_t cnt_mask = (1u << P.cnt_bits) - 1u;
-  const unsigned long long key_lo = (unsigned long long)tlo << P.cnt_bits;
-  const unsigned long long key_hi = (unsigned long long)thi << P.cnt_bits;
   const uint32_t tid = threadIdx.x;
-
   if (tid == 0) {
-    sh->n_used = 0;
     sh->n_out = 0;
     sh->overflow = 0;
   }
   __syncthreads();
-  uint32_t cap = cap_max;
   unsigned long long walked = 0;
   for (uint32_t c0 = 0; c0 < E; c0 += kChunk) {
     const uint32_t n_c = min(kChunk, E - c0);
@@ -154,13 +177,13 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
       const uint32_t e = tid * kItems + r;
       uint32_t len = 0;
       if (e < n_c) {
-        const uint32_t id = P.mv_id[m0 + c0 + e];
-        uint32_t lo = P.post_ptr[id], hi = P.post_ptr[id + 1];
+        uint32_t lo = P.mv_post[m0 + c0 + e];
+        uint32_t hi = lo + P.mv_plen[m0 + c0 + e];
         if (!Q.all_pairs) {
           lo = lower_bound_post(P.post, lo, hi, key_lo);
           hi = lower_bound_post(P.post, lo, hi, key_hi);
         }
-        c_lo[e] = lo;
+        c_post[e] = lo;
         c_cnt[e] = P.mv_cnt[m0 + c0 + e];
         len = hi - lo;
       }
@@ -176,215 +199,293 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
       run += len_loc[r];
     }
     if (tid == 0) c_off[n_c] = J_c;
-    // ---- size and clear the accumulator before the first chunk
-    if (c0 == 0) {
-      if (E <= kChunk && J_c < (cap_max >> 1)) cap = max(kMinCap, next_pow2(2u * J_c));
-      for (uint32_t h = tid; h < cap; h += kThreads) {
-        keys[h] = kEmpty;
-        vals[h] = 0;
-      }
-    }
     __syncthreads();
     walked += J_c;
-    const uint32_t mask = cap - 1u;
-    const uint32_t limit = (cap >> 2) * 3u;
-    // ---- walk the chunk's postings
-    for (uint32_t t = tid; t < J_c; t += kThreads) {
+    // ---- merge-path walk of the chunk's postings
+    const uint32_t per = (J_c + kThreads - 1) / kThreads;
+    uint32_t x = min(J_c, tid * per);
+    const uint32_t x_end = min(J_c, x + per);
+    if (x < x_end) {
       uint32_t lo = 0, hi = n_c;
       while (hi - lo > 1) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (c_off[mid] <= t) lo = mid; else hi = mid;
+        if (c_off[mid] <= x) lo = mid; else hi = mid;
       }
-      const uint32_t p = P.post[c_lo[lo] + (t - c_off[lo])];
-      const uint32_t b = p >> P.cnt_bits;
-      if (Q.all_pairs && b >= own0 && b < own1) continue;
-      const uint32_t ca = c_cnt[lo];
-      uint32_t cb = p & cnt_mask;
-      if (cb == P.cnt_cap && ca > cb) cb = mv_count_of(P, b, P.mv_id[m0 + c0 + lo]);
-      if (!acc_add(keys, vals, mask, b, min(ca, cb), &sh->n_used, limit)) sh->overflow = 1;
+      uint32_t e = lo, e_end = c_off[lo + 1], base = c_post[lo] - c_off[lo], ca = c_cnt[lo];
+      while (x < x_end) {
+        uint32_t pv[4], cav[4], ev[4];
+        uint32_t nb = 0;
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+          if (x < x_end) {
+            while (x >= e_end) {
+              ++e;
+              e_end = c_off[e + 1];
+              base = c_post[e] - c_off[e];
+              ca = c_cnt[e];
+            }
+            pv[j] = P.post[base + x];
+            cav[j] = ca;
+            ev[j] = e;
+            ++x;
+            nb = j + 1;
+          }
+        }
+#pragma unroll
+        for (uint32_t j = 0; j < 4; ++j) {
+          if (j < nb) {
+            const uint32_t p = pv[j];
+            const uint32_t b = p >> P.cnt_bits;
+            if (Q.all_pairs && b >= own0 && b < own1) continue;
+            uint32_t cb = p & cnt_mask;
+            if (cb == P.cnt_cap && cav[j] > cb) cb = mv_count_of(P, b, P.mv_id[m0 + c0 + ev[j]]);
+            if (!acc_add(keys, vals, mask, b, min(cav[j], cb))) sh->overflow = 1;
+          }
+        }
+      }
     }
     __syncthreads();
     if (sh->overflow) break;
   }
 
-  bool defer = sh->overflow != 0;
-  uint32_t n_out = 0;
-  if (!defer && E > 0) {
+  // Slots are visited interleaved (slot = i * kThreads + tid: conflict-free);
+  // an occupancy mask in registers lets the second pass skip empty slots.
+  // kSlots = 0 means the table size is only known at run time (global tier).
+  const bool overflow = sh->overflow != 0;
+  const uint32_t slots = kSlots ? kSlots : tb.cap / kThreads;
+  if (!overflow) {
     if (kEmitAll) {
-      // every accumulator is an output (the sum-min test hook)
-      for (uint32_t h = tid; h < cap; h += kThreads) {
+      for (uint32_t i = 0; i < slots; ++i) {
+        const uint32_t h = i * kThreads + tid;
         const uint32_t b = keys[h];
         if (b == kEmpty) continue;
         const uint32_t slot = atomicAdd(&sh->n_out, 1u);
-        if (slot < out_cap) out[slot] = ((unsigned long long)b << 32) | vals[h];
+        if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | vals[h];
+        keys[h] = kEmpty;
+        vals[h] = 0;
       }
     } else {
       // ---- per target genome: the maximum ratio, then every entry at it
       const uint32_t n_best = Q.all_pairs ? P.n_genomes : 1u;
       for (uint32_t j = tid; j < n_best; j += kThreads) best[j] = 0ull;
       __syncthreads();
-      for (uint32_t h = tid; h < cap; h += kThreads) {
+      uint32_t occ = 0;  // bit i: slot i * kThreads + tid is occupied (first 32 rounds)
+      for (uint32_t i = 0; i < slots; ++i) {
+        const uint32_t h = i * kThreads + tid;
         const uint32_t b = keys[h];
         if (b == kEmpty) continue;
+        if (i < 32) occ |= 1u << i;
         const uint32_t s = vals[h];
-        const uint32_t den = La_a + P.La[b] - s;
-        best_update(&best[Q.all_pairs ? (uint32_t)P.gene_genome[b] : 0u], s, den);
+        const uint32_t gi = P.ginfo[b];
+        best_update(&best[Q.all_pairs ? (gi >> 16) : 0u], s, La_a + (gi & 0xFFFFu) - s);
       }
       __syncthreads();
-      for (uint32_t h = tid; h < cap; h += kThreads) {
+      for (uint32_t i = 0; i < slots; ++i) {
+        if (i < 32 && !(occ & (1u << i))) continue;
+        const uint32_t h = i * kThreads + tid;
         const uint32_t b = keys[h];
         if (b == kEmpty) continue;
         const uint32_t s = vals[h];
-        const uint32_t den = La_a + P.La[b] - s;
-        const unsigned long long bv = best[Q.all_pairs ? (uint32_t)P.gene_genome[b] : 0u];
-        if (ratio_equal(s, den, (uint32_t)(bv >> 32), (uint32_t)bv)) {
+        const uint32_t gi = P.ginfo[b];
+        const unsigned long long bv = best[Q.all_pairs ? (gi >> 16) : 0u];
+        if (ratio_equal(s, La_a + (gi & 0xFFFFu) - s, (uint32_t)(bv >> 32), (uint32_t)bv)) {
           const uint32_t slot = atomicAdd(&sh->n_out, 1u);
-          if (slot < out_cap) out[slot] = ((unsigned long long)b << 32) | s;
+          if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | s;
         }
+        keys[h] = kEmpty;
+        vals[h] = 0;
       }
     }
-    __syncthreads();
-    n_out = sh->n_out;
-    if (n_out > out_cap) defer = true;
-  }
-
-  if (defer) {
-    if (kBig) {  // cannot happen: the large tier is sized for every target
-      if (tid == 0) raise_error(err, PD_ERR_INTERNAL, qi);
-    } else if (tid == 0) {
-      O.deferred[atomicAdd(O.n_deferred, 1u)] = qi;
+  } else {
+    for (uint32_t i = 0; i < slots; ++i) {
+      keys[i * kThreads + tid] = kEmpty;
+      vals[i * kThreads + tid] = 0;
     }
+  }
+  __syncthreads();
+  const uint32_t n_out = sh->n_out;
+  if (overflow || n_out > tb.out_cap) {
     if (tid == 0) {
-      O.row_off[qi] = 0;
-      O.row_len[qi] = 0;
+      if (T.def_list) {
+        T.def_list[atomicAdd(T.def_count, 1u)] = qi;
+      } else {
+        raise_error(err, PD_ERR_INTERNAL, qi);  // the last tier holds every target
+      }
+      O.row_off[row] = 0;
+      O.row_len[row] = 0;
     }
     __syncthreads();
     return;
   }
-
-  // ---- sort the hits by gene and append them
-  if (n_out > 1) {
-    const uint32_t n2 = next_pow2(n_out);
-    for (uint32_t x = n_out + tid; x < n2; x += kThreads) out[x] = ~0ull;
-    __syncthreads();
-    block_bitonic_sort(out, n2);
-  }
+  // ---- append: each hit goes to its rank among the query's hits
   if (tid == 0) {
     const unsigned long long base = atomicAdd(O.cursor, (unsigned long long)n_out);
     sh->base_lo = (uint32_t)base;
     sh->base_hi = (uint32_t)(base >> 32);
-    O.row_off[qi] = base;
-    O.row_len[qi] = n_out;
+    O.row_off[row] = base;
+    O.row_len[row] = n_out;
     atomicAdd(O.walked, walked);
   }
   __syncthreads();
   const unsigned long long base = ((unsigned long long)sh->base_hi << 32) | sh->base_lo;
   if (base + n_out <= O.out_cap) {
-    for (uint32_t x = tid; x < n_out; x += kThreads) {
-      O.out_b[base + x] = (uint32_t)(out[x] >> 32);
-      O.out_s[base + x] = (uint32_t)out[x];
+    for (uint32_t t = tid; t < n_out; t += kThreads) {
+      const unsigned long long v = out[t];
+      uint32_t rank = 0;
+      for (uint32_t u = 0; u < n_out; ++u) rank += (out[u] < v) ? 1u : 0u;
+      O.out_b[base + rank] = (uint32_t)(v >> 32);
+      O.out_s[base + rank] = (uint32_t)v;
     }
   }
   __syncthreads();
 }
 
-template <bool kEmitAll>
-__host__ __device__ constexpr uint32_t out_cap_smem() {
-  return kEmitAll ? kCap : kOutCap;
-}
+// ---- shared-memory tiers: [keys cap][vals cap][chunk | hits][best]
+template <int kThreads, uint32_t kCap, uint32_t kOutCap>
+struct SmemTier {
+  static_assert(kCap % kThreads == 0, "table must split evenly over the block");
+  static constexpr size_t kTable = (size_t)kCap * 8;
+  static constexpr size_t kUnion =
+      Chunk<kThreads>::kBytes > (size_t)kOutCap * 8 ? Chunk<kThreads>::kBytes : (size_t)kOutCap * 8;
+  static size_t bytes(uint32_t n_best) { return kTable + kUnion + (size_t)(n_best ? n_best : 1) * 8; }
+};
 
-template <bool kEmitAll>
-__host__ __device__ constexpr size_t union_bytes() {
-  constexpr size_t chunk = (size_t)kChunk * 4 + (size_t)(kChunk + 1) * 4 + (size_t)kChunk * 2;
-  constexpr size_t outb = (size_t)out_cap_smem<kEmitAll>() * 8;
-  return ((chunk > outb ? chunk : outb) + 15) & ~(size_t)15;
-}
-
-template <bool kEmitAll>
-__global__ void __launch_bounds__(kThreads) k_summin_bh(ProfilesView P, QuerySet Q, HitsOut O, DevErr* err) {
+template <int kThreads, uint32_t kCap, uint32_t kOutCap, bool kEmitAll>
+__global__ void __launch_bounds__(kThreads) k_summin_smem(ProfilesView P, QuerySet Q, HitsOut O, TierIO T,
+                                                          DevErr* err) {
+  using S = SmemTier<kThreads, kCap, kOutCap>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Scalars sh;
-  uint32_t* keys = (uint32_t*)smem;
-  uint32_t* vals = keys + kCap;
-  unsigned char* uni = (unsigned char*)(vals + kCap);
-  unsigned long long* out = (unsigned long long*)uni;
-  uint32_t* c_lo = (uint32_t*)uni;
-  uint32_t* c_off = c_lo + kChunk;
-  uint16_t* c_cnt = (uint16_t*)(c_off + kChunk + 1);
-  unsigned long long* best = (unsigned long long*)(uni + union_bytes<kEmitAll>());
-  for (uint32_t qi = blockIdx.x; qi < Q.n_queries; qi += gridDim.x)
-    process_query<false, kEmitAll>(qi, P, Q, O, err, keys, vals, kCap, out, out_cap_smem<kEmitAll>(), c_lo, c_off,
-                                   c_cnt, best, &sh);
+  Table tb;
+  tb.keys = (uint32_t*)smem;
+  tb.vals = tb.keys + kCap;
+  tb.cap = kCap;
+  tb.out_cap = kOutCap;
+  unsigned char* uni = smem + S::kTable;
+  tb.out = (unsigned long long*)uni;
+  uint32_t* c_post = (uint32_t*)uni;
+  uint32_t* c_off = c_post + Chunk<kThreads>::kSize;
+  uint16_t* c_cnt = (uint16_t*)(c_off + Chunk<kThreads>::kSize + 1);
+  unsigned long long* best = (unsigned long long*)(uni + S::kUnion);
+  for (uint32_t h = threadIdx.x; h < kCap; h += kThreads) {
+    tb.keys[h] = kEmpty;
+    tb.vals[h] = 0;
+  }
+  __syncthreads();
+  const uint32_t n = T.in_list ? *T.in_count : Q.n_queries;
+  for (uint32_t x = blockIdx.x; x < n; x += gridDim.x)
+    process_query<kThreads, kEmitAll, kCap / kThreads>(T.in_list ? T.in_list[x] : x, P, Q, O, T, err, tb, c_post,
+                                                       c_off, c_cnt, best, &sh);
 }
 
+// ---- global-memory tier: table and hit list of each block in scratch
 template <bool kEmitAll>
-__global__ void __launch_bounds__(kThreads) k_summin_bh_big(ProfilesView P, QuerySet Q, HitsOut O, BigScratch B,
-                                                            DevErr* err) {
+__global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet Q, HitsOut O, TierIO T,
+                                                       BigScratch B, DevErr* err) {
+  constexpr int kThreads = 256;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Scalars sh;
-  uint32_t* c_lo = (uint32_t*)smem;
-  uint32_t* c_off = c_lo + kChunk;
-  uint16_t* c_cnt = (uint16_t*)(c_off + kChunk + 1);
-  unsigned long long* best = (unsigned long long*)(smem + union_bytes<false>());
-  uint32_t* keys = B.keys + (size_t)blockIdx.x * B.cap;
-  uint32_t* vals = B.vals + (size_t)blockIdx.x * B.cap;
-  unsigned long long* out = B.out + (size_t)blockIdx.x * B.out_cap;
-  const uint32_t n_def = *O.n_deferred;
-  for (uint32_t x = blockIdx.x; x < n_def; x += gridDim.x)
-    process_query<true, kEmitAll>(O.deferred[x], P, Q, O, err, keys, vals, B.cap, out, B.out_cap, c_lo, c_off, c_cnt,
-                                  best, &sh);
+  Table tb;
+  tb.keys = B.keys + (size_t)blockIdx.x * B.cap;
+  tb.vals = B.vals + (size_t)blockIdx.x * B.cap;
+  tb.out = B.out + (size_t)blockIdx.x * B.out_cap;
+  tb.cap = B.cap;
+  tb.out_cap = B.out_cap;
+  uint32_t* c_post = (uint32_t*)smem;
+  uint32_t* c_off = c_post + Chunk<kThreads>::kSize;
+  uint16_t* c_cnt = (uint16_t*)(c_off + Chunk<kThreads>::kSize + 1);
+  unsigned long long* best = (unsigned long long*)(smem + Chunk<kThreads>::kBytes);
+  for (uint32_t h = threadIdx.x; h < B.cap; h += kThreads) {
+    tb.keys[h] = kEmpty;
+    tb.vals[h] = 0;
+  }
+  __syncthreads();
+  const uint32_t n = *T.in_count;
+  for (uint32_t x = blockIdx.x; x < n; x += gridDim.x)
+    process_query<kThreads, kEmitAll, 0>(T.in_list[x], P, Q, O, T, err, tb, c_post, c_off, c_cnt, best, &sh);
+}
+
+// Tier 1 and tier 2 geometries.
+constexpr int kT1Threads = 256;
+constexpr uint32_t kT1Cap = 4096, kT1Out = 512, kT1OutEmit = 3072;
+constexpr int kT2Threads = 1024;
+constexpr uint32_t kT2Cap = 16384, kT2Out = 4096, kT2OutEmit = 8192;  // keeps tier 2 under 227 KB
+
+static_assert(SmemTier<kT1Threads, kT1Cap, kT1Out>::kTable + SmemTier<kT1Threads, kT1Cap, kT1Out>::kUnion +
+                  PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 1 shared memory");
+static_assert(SmemTier<kT2Threads, kT2Cap, kT2Out>::kTable + SmemTier<kT2Threads, kT2Cap, kT2Out>::kUnion +
+                  PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 2 shared memory");
+static_assert(SmemTier<kT2Threads, kT2Cap, kT2OutEmit>::kTable + SmemTier<kT2Threads, kT2Cap, kT2OutEmit>::kUnion +
+                  8 <= 227 * 1024, "tier 2 (emit-all, one target genome) shared memory");
+
+template <typename K>
+cudaError_t launch_smem(K kernel, Launcher* L, const char* name, int threads, size_t smem, uint32_t max_grid,
+                        const ProfilesView& P, const QuerySet& Q, const HitsOut& O, const TierIO& T, DevErr* err,
+                        cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 1, dev = 0, n_sm = 152;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  const uint32_t grid = std::max<uint32_t>(1, std::min<uint32_t>(max_grid, (uint32_t)n_sm * std::max(per_sm, 1)));
+  if ((e = launch_begin(L, name)) != cudaSuccess) return e;
+  kernel<<<grid, threads, smem, s>>>(P, Q, O, T, err);
+  return launch_end(L, name);
 }
 
 }  // namespace
 
 size_t summin_smem_bytes(uint32_t n_genomes, bool emit_all) {
-  const size_t best = (size_t)(n_genomes ? n_genomes : 1) * 8;
-  return (size_t)kCap * 8 + (emit_all ? union_bytes<true>() : union_bytes<false>()) + best;
+  return emit_all ? SmemTier<kT1Threads, kT1Cap, kT1OutEmit>::bytes(n_genomes)
+                  : SmemTier<kT1Threads, kT1Cap, kT1Out>::bytes(n_genomes);
 }
 
-cudaError_t run_summin_bh(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O, DevErr* err,
-                          bool emit_all, cudaStream_t s) {
+cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O, DevErr* err,
+                             bool emit_all, cudaStream_t s) {
   if (Q.n_queries == 0) return cudaSuccess;
-  const size_t smem = summin_smem_bytes(P.n_genomes, emit_all);
-  const char* name = emit_all ? "summin_pairs" : "summin_bh";
+  const uint32_t n_best = Q.all_pairs ? P.n_genomes : 1u;
+  TierIO t1{nullptr, nullptr, O.def1, O.n_def1};
+  TierIO t2{O.def1, O.n_def1, O.def2, O.n_def2};
   cudaError_t e;
+  // tier 1: several resident blocks per SM, each looping over queries
   if (emit_all)
-    e = cudaFuncSetAttribute(k_summin_bh<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = launch_smem(k_summin_smem<kT1Threads, kT1Cap, kT1OutEmit, true>, L, "summin_pairs", kT1Threads,
+                    SmemTier<kT1Threads, kT1Cap, kT1OutEmit>::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   else
-    e = cudaFuncSetAttribute(k_summin_bh<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = launch_smem(k_summin_smem<kT1Threads, kT1Cap, kT1Out, false>, L, "summin_bh", kT1Threads,
+                    SmemTier<kT1Threads, kT1Cap, kT1Out>::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   if (e != cudaSuccess) return e;
-  int per_sm = 1;
+  // tier 2: one 1024-thread block per SM over the deferred queries (exits at once if none)
   if (emit_all)
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_summin_bh<true>, kThreads, smem);
+    e = launch_smem(k_summin_smem<kT2Threads, kT2Cap, kT2OutEmit, true>, L, "summin_pairs_t2", kT2Threads,
+                    SmemTier<kT2Threads, kT2Cap, kT2OutEmit>::bytes(n_best), Q.n_queries, P, Q, O, t2, err, s);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_summin_bh<false>, kThreads, smem);
-  int dev = 0, n_sm = 152;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  const unsigned grid = (unsigned)std::min<uint64_t>(Q.n_queries, (uint64_t)n_sm * (per_sm > 0 ? per_sm : 1) * 8);
-  if ((e = launch_begin(L, name)) != cudaSuccess) return e;
-  if (emit_all)
-    k_summin_bh<true><<<grid, kThreads, smem, s>>>(P, Q, O, err);
-  else
-    k_summin_bh<false><<<grid, kThreads, smem, s>>>(P, Q, O, err);
-  return launch_end(L, name);
+    e = launch_smem(k_summin_smem<kT2Threads, kT2Cap, kT2Out, false>, L, "summin_bh_t2", kT2Threads,
+                    SmemTier<kT2Threads, kT2Cap, kT2Out>::bytes(n_best), Q.n_queries, P, Q, O, t2, err, s);
+  return e;
 }
 
-cudaError_t run_summin_bh_big(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O,
+size_t summin_global_smem_bytes(uint32_t n_genomes) {
+  return Chunk<256>::kBytes + (size_t)(n_genomes ? n_genomes : 1) * 8;
+}
+
+cudaError_t run_summin_global(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O,
                               const BigScratch& B, uint32_t n_ctas, DevErr* err, bool emit_all, cudaStream_t s) {
-  const size_t smem = union_bytes<false>() + (size_t)(P.n_genomes ? P.n_genomes : 1) * 8;
-  const char* name = emit_all ? "summin_pairs_big" : "summin_bh_big";
+  const size_t smem = summin_global_smem_bytes(Q.all_pairs ? P.n_genomes : 1u);
+  TierIO t3{O.def2, O.n_def2, nullptr, nullptr};
+  const char* name = emit_all ? "summin_pairs_t3" : "summin_bh_t3";
   cudaError_t e;
   if (emit_all)
-    e = cudaFuncSetAttribute(k_summin_bh_big<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_summin_global<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   else
-    e = cudaFuncSetAttribute(k_summin_bh_big<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = cudaFuncSetAttribute(k_summin_global<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if ((e = launch_begin(L, name)) != cudaSuccess) return e;
   if (emit_all)
-    k_summin_bh_big<true><<<n_ctas, kThreads, smem, s>>>(P, Q, O, B, err);
+    k_summin_global<true><<<n_ctas, 256, smem, s>>>(P, Q, O, t3, B, err);
   else
-    k_summin_bh_big<false><<<n_ctas, kThreads, smem, s>>>(P, Q, O, B, err);
+    k_summin_global<false><<<n_ctas, 256, smem, s>>>(P, Q, O, t3, B, err);
   return launch_end(L, name);
 }
 

@@ -210,7 +210,8 @@ struct pd_profiles {
   pd_ctx* ctx = nullptr;
   pdg::ProfilesView view{};
   pd_profiles_info info{};
-  Buf genome_ptr, La, win_off, mv_len, mv_id, mv_cnt, gene_genome, bitmap, word_rank, post_ptr, post;
+  Buf genome_ptr, La, win_off, mv_n, mv_id, mv_cnt, mv_post, mv_plen, gene_genome, ginfo, bitmap, word_rank, post_ptr,
+      post, order;
   std::vector<int32_t> h_genome_ptr;
 };
 
@@ -347,6 +348,12 @@ PD_API int pd_choose_k(uint64_t total, int alphabet) {
 }
 
 // ------------------------------------------------------------------ profiles
+static uint32_t ceil_log2_u64(uint64_t x) {
+  uint32_t b = 0;
+  while (b < 64 && ((uint64_t)1 << b) < x) ++b;
+  return b;
+}
+
 static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                                      uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
                                      pd_profiles** out) {
@@ -374,7 +381,7 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   uint64_t W = 0;
   std::vector<uint32_t> long_genes, long_off;
   uint64_t long_total = 0;
-  const uint32_t kMaxSmemSort = 8192;
+  const uint32_t kMaxSmemSort = 4096;
   for (uint32_t g = 0; g < n_genes; ++g) {
     const int64_t len = hg[g + 1] - hg[g];
     if (len < 0) return fail(c, PD_ERR_ARG, "gene_ptr is decreasing at " + std::to_string(g));
@@ -400,9 +407,11 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   std::unique_ptr<pd_profiles> guard(P);
   const uint64_t n_codes = pow_u64(20, k);
   const uint64_t n_words = (n_codes + 63) / 64;
+  const size_t G1 = std::max<uint32_t>(n_genes, 1), W1 = std::max<uint64_t>(W, 1);
+  pdg::Launcher* L = &c->L;
 
   // ---- inputs on the device
-  Buf d_res, d_gene_ptr, d_long, d_long_off, d_long_scratch, tmp;
+  Buf d_res, d_gene_ptr, d_long, d_long_off, d_long_scratch, tmp, d_counts, minhash;
   const uint8_t* res_dev = residues;
   const int64_t* gp_devp = gene_ptr;
   if (n_res > 0 && !is_device_ptr(residues)) {
@@ -417,18 +426,17 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
     gp_devp = d_gene_ptr.as<int64_t>();
   }
   ALLOC(P->genome_ptr, sizeof(int32_t) * (n_genomes + 1));
-  ALLOC(P->La, sizeof(uint32_t) * std::max<uint32_t>(n_genes, 1));
+  ALLOC(P->La, sizeof(uint32_t) * G1);
   ALLOC(P->win_off, sizeof(uint32_t) * (n_genes + 1));
-  ALLOC(P->gene_genome, sizeof(uint16_t) * std::max<uint32_t>(n_genes, 1));
+  ALLOC(P->gene_genome, sizeof(uint16_t) * G1);
+  ALLOC(P->ginfo, sizeof(uint32_t) * G1);
   CK(cudaMemcpyAsync(P->genome_ptr.p, hgn.data(), sizeof(int32_t) * (n_genomes + 1), cudaMemcpyHostToDevice,
                      c->stream));
   if (n_genes) CK(cudaMemcpyAsync(P->La.p, La.data(), sizeof(uint32_t) * n_genes, cudaMemcpyHostToDevice, c->stream));
   CK(cudaMemcpyAsync(P->win_off.p, win_off.data(), sizeof(uint32_t) * (n_genes + 1), cudaMemcpyHostToDevice,
                      c->stream));
-  // host vectors must outlive the async copies: synchronize before they go
-  pdg::Launcher* L = &c->L;
-  if (n_genomes) CK(pdg::run_gene_genome(L, P->genome_ptr.as<int32_t>(), n_genomes, P->gene_genome.as<uint16_t>(),
-                                          c->stream));
+  CK(pdg::run_gene_info(L, P->genome_ptr.as<int32_t>(), n_genomes, P->La.as<uint32_t>(),
+                        P->gene_genome.as<uint16_t>(), P->ginfo.as<uint32_t>(), c->stream));
 
   // ---- dictionary: bitmap of present codes and word ranks
   ALLOC(P->bitmap, sizeof(unsigned long long) * n_words);
@@ -437,9 +445,10 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   if (n_genes)
     CK(pdg::run_encode_mark(L, res_dev, gp_devp, n_genes, k, P->bitmap.as<unsigned long long>(), c->d_err,
                             c->stream));
-  ALLOC(tmp, pdg::scan_temp_bytes(std::max<uint64_t>(n_words, W + 1)) + 64);
-  Buf d_counts;  // [0] = D, [1] = max posting
-  ALLOC(d_counts, 4 * sizeof(uint32_t));
+  const uint32_t kOrderShift = 16;  // 65536 min-hash buckets
+  const uint64_t n_order_b = (uint64_t)1 << (32 - kOrderShift);
+  ALLOC(tmp, pdg::scan_temp_bytes(std::max<uint64_t>(std::max<uint64_t>(n_words, n_order_b), 24577)) + 64);
+  ALLOC(d_counts, 4 * sizeof(uint32_t));  // [0] = D, [1] = max posting
   CK(cudaMemsetAsync(d_counts.p, 0, 4 * sizeof(uint32_t), c->stream));
   CK(pdg::scan_popc_words(L, P->bitmap.as<unsigned long long>(), n_words, P->word_rank.as<uint32_t>(),
                           d_counts.as<uint32_t>(), tmp.p, c->stream));
@@ -449,13 +458,11 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   if (st != PD_OK) return st;
   const uint64_t D = h_counts[0];
 
-  // ---- multiplicity vectors and posting counts per id
-  Buf hist;
-  ALLOC(hist, sizeof(uint32_t) * (D + 1));
-  CK(cudaMemsetAsync(hist.p, 0, sizeof(uint32_t) * (D + 1), c->stream));
-  ALLOC(P->mv_id, sizeof(uint32_t) * std::max<uint64_t>(W, 1));
-  ALLOC(P->mv_cnt, sizeof(uint16_t) * std::max<uint64_t>(W, 1));
-  ALLOC(P->mv_len, sizeof(uint32_t) * std::max<uint32_t>(n_genes, 1));
+  // ---- multiplicity vectors
+  ALLOC(P->mv_id, sizeof(uint32_t) * W1);
+  ALLOC(P->mv_cnt, sizeof(uint16_t) * W1);
+  ALLOC(P->mv_n, sizeof(uint32_t) * G1);
+  ALLOC(minhash, sizeof(uint32_t) * G1);
   if (!long_genes.empty()) {
     ALLOC(d_long, sizeof(uint32_t) * long_genes.size());
     ALLOC(d_long_off, sizeof(uint32_t) * long_off.size());
@@ -468,40 +475,66 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   if (n_genes)
     CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
                          P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), P->mv_id.as<uint32_t>(),
-                         P->mv_cnt.as<uint16_t>(), P->mv_len.as<uint32_t>(), hist.as<uint32_t>(),
+                         P->mv_cnt.as<uint16_t>(), P->mv_n.as<uint32_t>(), minhash.as<uint32_t>(),
                          d_long.as<uint32_t>(), (uint32_t)long_genes.size(), d_long_scratch.as<uint32_t>(),
                          d_long_off.as<uint32_t>(), kMaxSmemSort, c->stream));
-  ALLOC(P->post_ptr, sizeof(uint32_t) * (D + 1));
-  CK(pdg::scan_u32(L, hist.as<uint32_t>(), D, P->post_ptr.as<uint32_t>(), tmp.p, c->stream));
-  if (D) CK(pdg::run_max_u32(L, hist.as<uint32_t>(), D, d_counts.as<uint32_t>() + 1, c->stream));
-  uint32_t E32 = 0;
-  CK(cudaMemcpyAsync(&E32, P->post_ptr.as<uint32_t>() + D, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(h_counts, d_counts.p, sizeof(h_counts), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  const uint64_t E = E32;
-  const uint32_t max_posting = h_counts[1];
 
-  // ---- inverted index
+  // ---- inverted index: bucketed transpose of the multiplicity vectors
   const uint32_t gene_bits = bits_for(n_genes > 0 ? n_genes - 1 : 0);
   const uint32_t cnt_bits = 32 - gene_bits;
   const uint32_t cnt_cap = std::min<uint32_t>((1u << cnt_bits) - 1u, 65535u);
-  ALLOC(P->post, sizeof(uint32_t) * std::max<uint64_t>(E, 1));
-  if (n_genes)
-    CK(pdg::run_post_fill(L, P->win_off.as<uint32_t>(), P->mv_len.as<uint32_t>(), P->mv_id.as<uint32_t>(),
-                          P->mv_cnt.as<uint16_t>(), n_genes, P->post_ptr.as<uint32_t>(), hist.as<uint32_t>(),
-                          P->post.as<uint32_t>(), cnt_bits, cnt_cap, c->stream));
-  if (D) {
-    Buf queue, qlen, lscr;
-    ALLOC(queue, sizeof(uint32_t) * (E / 33 + 1));
-    ALLOC(qlen, sizeof(uint32_t));
-    CK(cudaMemsetAsync(qlen.p, 0, sizeof(uint32_t), c->stream));
-    if (pdg::next_pow2(max_posting) > 8192) ALLOC(lscr, sizeof(uint32_t) * pdg::next_pow2(max_posting));
-    CK(pdg::run_post_sort(L, P->post_ptr.as<uint32_t>(), D, P->post.as<uint32_t>(), queue.as<uint32_t>(),
-                          qlen.as<uint32_t>(), max_posting, lscr.as<uint32_t>(), c->stream));
-    CK(cudaStreamSynchronize(c->stream));  // scratch lifetime
+  uint32_t shift = ceil_log2_u64(std::max<uint64_t>(D, 1));
+  shift = shift > 13 ? shift - 13 : 0;
+  if (shift > 14) shift = 14;
+  const uint64_t NB64 = (D + ((uint64_t)1 << shift) - 1) >> shift;
+  if (NB64 > 24576) return fail(c, PD_ERR_ARG, "more than 402M distinct k-mers in one dataset");
+  const uint32_t NB = (uint32_t)std::max<uint64_t>(NB64, 1);
+  Buf bcount, bstart, bcursor, recs;
+  ALLOC(bcount, sizeof(uint32_t) * NB);
+  ALLOC(bstart, sizeof(uint32_t) * (NB + 1));
+  ALLOC(bcursor, sizeof(uint32_t) * NB);
+  ALLOC(recs, sizeof(unsigned long long) * W1);
+  ALLOC(P->post_ptr, sizeof(uint32_t) * (D + 1));
+  ALLOC(P->post, sizeof(uint32_t) * W1);
+  CK(cudaMemsetAsync(bcount.p, 0, sizeof(uint32_t) * NB, c->stream));
+  if (n_genes && D) {
+    CK(pdg::run_bucket_count(L, P->win_off.as<uint32_t>(), P->mv_n.as<uint32_t>(), P->mv_id.as<uint32_t>(), n_genes,
+                             shift, NB, bcount.as<uint32_t>(), c->stream));
   }
-  st = check_dev_err(c);
+  CK(pdg::scan_u32(L, bcount.as<uint32_t>(), NB, bstart.as<uint32_t>(), tmp.p, c->stream));
+  CK(cudaMemcpyAsync(bcursor.p, bstart.p, sizeof(uint32_t) * NB, cudaMemcpyDeviceToDevice, c->stream));
+  if (n_genes && D) {
+    CK(pdg::run_bucket_scatter(L, P->win_off.as<uint32_t>(), P->mv_n.as<uint32_t>(), P->mv_id.as<uint32_t>(),
+                               P->mv_cnt.as<uint16_t>(), n_genes, shift, NB, bcursor.as<uint32_t>(), cnt_bits,
+                               cnt_cap, recs.as<unsigned long long>(), c->stream));
+    CK(pdg::run_bucket_fine(L, bstart.as<uint32_t>(), NB, shift, D, recs.as<unsigned long long>(),
+                            P->post_ptr.as<uint32_t>(), P->post.as<uint32_t>(), d_counts.as<uint32_t>() + 1,
+                            c->stream));
+  }
+  CK(cudaMemcpyAsync(P->post_ptr.as<uint32_t>() + D, bstart.as<uint32_t>() + NB, sizeof(uint32_t),
+                     cudaMemcpyDeviceToDevice, c->stream));
+  ALLOC(P->mv_post, sizeof(uint32_t) * W1);
+  ALLOC(P->mv_plen, sizeof(uint32_t) * W1);
+  if (n_genes && D)
+    CK(pdg::run_mv_post(L, P->win_off.as<uint32_t>(), P->mv_n.as<uint32_t>(), P->mv_id.as<uint32_t>(), n_genes,
+                        P->post_ptr.as<uint32_t>(), P->mv_post.as<uint32_t>(), P->mv_plen.as<uint32_t>(), c->stream));
+
+  // ---- all-pairs query order: min-hash buckets
+  Buf ocount;
+  ALLOC(P->order, sizeof(uint32_t) * G1);
+  ALLOC(ocount, sizeof(uint32_t) * (2 * n_order_b + 1));
+  CK(cudaMemsetAsync(ocount.p, 0, sizeof(uint32_t) * n_order_b, c->stream));
+  if (n_genes)
+    CK(pdg::run_order(L, minhash.as<uint32_t>(), n_genes, kOrderShift, ocount.as<uint32_t>(),
+                      P->order.as<uint32_t>(), tmp.p, c->stream));
+
+  uint32_t E32 = 0;
+  CK(cudaMemcpyAsync(&E32, bstart.as<uint32_t>() + NB, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(h_counts, d_counts.p, sizeof(h_counts), cudaMemcpyDeviceToHost, c->stream));
+  st = check_dev_err(c);  // synchronizes; temporaries are released after this
   if (st != PD_OK) return st;
+  const uint64_t E = E32;
+  const uint32_t max_posting = h_counts[1];
 
   pdg::ProfilesView& v = P->view;
   v.k = k;
@@ -514,17 +547,21 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   v.cnt_cap = cnt_cap;
   v.max_posting = max_posting;
   v.win_off = P->win_off.as<uint32_t>();
-  v.mv_len = P->mv_len.as<uint32_t>();
+  v.mv_n = P->mv_n.as<uint32_t>();
   v.mv_id = P->mv_id.as<uint32_t>();
   v.mv_cnt = P->mv_cnt.as<uint16_t>();
+  v.mv_post = P->mv_post.as<uint32_t>();
+  v.mv_plen = P->mv_plen.as<uint32_t>();
   v.La = P->La.as<uint32_t>();
   v.gene_genome = P->gene_genome.as<uint16_t>();
+  v.ginfo = P->ginfo.as<uint32_t>();
   v.genome_ptr = P->genome_ptr.as<int32_t>();
   v.bitmap = P->bitmap.as<unsigned long long>();
   v.word_rank = P->word_rank.as<uint32_t>();
   v.n_words = n_words;
   v.post_ptr = P->post_ptr.as<uint32_t>();
   v.post = P->post.as<uint32_t>();
+  v.order = P->order.as<uint32_t>();
   pd_profiles_info& in = P->info;
   in.k = k;
   in.n_genes = n_genes;
@@ -534,8 +571,9 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   in.n_entries = E;
   in.max_posting = max_posting;
   in.count_bits = cnt_bits;
-  in.device_bytes = P->genome_ptr.n + P->La.n + P->win_off.n + P->mv_len.n + P->mv_id.n + P->mv_cnt.n +
-                    P->gene_genome.n + P->bitmap.n + P->word_rank.n + P->post_ptr.n + P->post.n;
+  in.device_bytes = P->genome_ptr.n + P->La.n + P->win_off.n + P->mv_n.n + P->mv_id.n + P->mv_cnt.n +
+                    P->mv_post.n + P->mv_plen.n + P->gene_genome.n + P->ginfo.n + P->bitmap.n + P->word_rank.n +
+                    P->post_ptr.n + P->post.n + P->order.n;
   *out = guard.release();
   return PD_OK;
 }
@@ -590,7 +628,7 @@ PD_API pd_status pd_profiles_copy_mv(pd_ctx* c, const pd_profiles* P, int64_t* m
     Buf ptr, tmp, code_of_id, d_codes, d_counts;
     ALLOC(ptr, sizeof(unsigned long long) * (v.n_genes + 1));
     ALLOC(tmp, pdg::scan_temp_bytes(v.n_genes + 1) + 64);
-    CK(pdg::scan_u32_to_u64(L, v.mv_len, v.n_genes, ptr.as<unsigned long long>(), tmp.p, c->stream));
+    CK(pdg::scan_u32_to_u64(L, v.mv_n, v.n_genes, ptr.as<unsigned long long>(), tmp.p, c->stream));
     if (codes) {
       ALLOC(code_of_id, sizeof(unsigned long long) * std::max<uint64_t>(v.n_distinct, 1));
       CK(pdg::run_select_codes(L, v.bitmap, v.word_rank, v.n_words, code_of_id.as<unsigned long long>(), c->stream));
@@ -648,28 +686,30 @@ PD_API pd_status pd_profiles_copy_index(pd_ctx* c, const pd_profiles* P, int64_t
 }
 
 // ------------------------------------------------------------------ sum-min + Best Hits
-// Runs the shared tier, then (if needed) the global tier for deferred queries,
-// growing the output until every row fits.  The result rows live in H.
+// Runs the shared-memory tiers, then (only if needed) the global-memory tier
+// for the queries they deferred, growing the output until every row fits.
 static pd_status run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& Q, bool emit_all, pd_hits* H) {
   const pdg::ProfilesView& v = P->view;
   pdg::Launcher* L = &c->L;
   const uint32_t nq = Q.n_queries;
+  const uint32_t n_rows = Q.all_pairs ? v.n_genes : nq;
   uint64_t cap;
   if (Q.all_pairs)
     cap = (uint64_t)nq * std::max<uint32_t>(v.n_genomes - 1, 1) * 3 / 2 + 4096;
   else
     cap = (uint64_t)nq * 4 + 4096;
   if (emit_all) cap = (uint64_t)nq * 64 + 4096;
-  Buf counters, deferred;
+  Buf counters, def1, def2;
   ALLOC(counters, 4 * sizeof(unsigned long long));
-  ALLOC(H->row_off, sizeof(unsigned long long) * std::max<uint32_t>(nq, 1));
-  ALLOC(H->row_len, sizeof(uint32_t) * std::max<uint32_t>(nq, 1));
-  ALLOC(deferred, sizeof(uint32_t) * std::max<uint32_t>(nq, 1));
+  ALLOC(H->row_off, sizeof(unsigned long long) * std::max<uint32_t>(n_rows, 1));
+  ALLOC(H->row_len, sizeof(uint32_t) * std::max<uint32_t>(n_rows, 1));
+  ALLOC(def1, sizeof(uint32_t) * std::max<uint32_t>(nq, 1));
+  ALLOC(def2, sizeof(uint32_t) * std::max<uint32_t>(nq, 1));
   for (int attempt = 0; attempt < 3; ++attempt) {
     ALLOC(H->out_b, sizeof(uint32_t) * cap);
     ALLOC(H->out_s, sizeof(uint32_t) * cap);
     CK(cudaMemsetAsync(counters.p, 0, 4 * sizeof(unsigned long long), c->stream));
-    CK(cudaMemsetAsync(H->row_len.p, 0, sizeof(uint32_t) * std::max<uint32_t>(nq, 1), c->stream));
+    CK(cudaMemsetAsync(H->row_len.p, 0, sizeof(uint32_t) * std::max<uint32_t>(n_rows, 1), c->stream));
     unsigned long long* cnt = counters.as<unsigned long long>();
     pdg::HitsOut O;
     O.out_b = H->out_b.as<uint32_t>();
@@ -677,22 +717,24 @@ static pd_status run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& 
     O.out_cap = cap;
     O.cursor = cnt + 0;
     O.walked = cnt + 1;
-    O.n_deferred = (uint32_t*)(cnt + 2);
+    O.n_def1 = (uint32_t*)(cnt + 2);
+    O.n_def2 = (uint32_t*)(cnt + 3);
     O.row_off = H->row_off.as<unsigned long long>();
     O.row_len = H->row_len.as<uint32_t>();
-    O.deferred = deferred.as<uint32_t>();
-    CK(pdg::run_summin_bh(L, v, Q, O, c->d_err, emit_all, c->stream));
+    O.def1 = def1.as<uint32_t>();
+    O.def2 = def2.as<uint32_t>();
+    CK(pdg::run_summin_tiers(L, v, Q, O, c->d_err, emit_all, c->stream));
     unsigned long long h[4];
     CK(cudaMemcpyAsync(h, counters.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     pd_status st = check_dev_err(c);
     if (st != PD_OK) return st;
-    const uint32_t n_def = (uint32_t)h[2];
-    if (n_def > 0) {
+    const uint32_t n_def1 = (uint32_t)h[2], n_def2 = (uint32_t)h[3];
+    if (n_def2 > 0) {
       pdg::BigScratch B;
       const uint32_t targets = std::max<uint32_t>(v.n_genes, 2);
-      B.cap = pdg::next_pow2(2 * targets);
+      B.cap = std::max<uint32_t>(pdg::next_pow2(4 * targets), 256);  // load <= 1/4: short probe chains
       B.out_cap = pdg::next_pow2(targets);
-      const uint32_t n_ctas = std::min<uint32_t>(n_def, 64);
+      const uint32_t n_ctas = std::min<uint32_t>(n_def2, 64);
       Buf bk, bv, bo;
       ALLOC(bk, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
       ALLOC(bv, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
@@ -700,7 +742,7 @@ static pd_status run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& 
       B.keys = bk.as<uint32_t>();
       B.vals = bv.as<uint32_t>();
       B.out = bo.as<unsigned long long>();
-      CK(pdg::run_summin_bh_big(L, v, Q, O, B, n_ctas, c->d_err, emit_all, c->stream));
+      CK(pdg::run_summin_global(L, v, Q, O, B, n_ctas, c->d_err, emit_all, c->stream));
       CK(cudaMemcpyAsync(h, counters.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
       st = check_dev_err(c);  // synchronizes (scratch lifetime)
       if (st != PD_OK) return st;
@@ -708,8 +750,8 @@ static pd_status run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& 
     if (h[0] <= cap) {
       H->n_hits = h[0];
       H->walked = h[1];
-      H->n_deferred = n_def;
-      H->n_rows = nq;
+      H->n_deferred = n_def1;
+      H->n_rows = n_rows;
       return PD_OK;
     }
     cap = h[0] + 4096;  // output did not fit: rerun with the exact size
@@ -752,6 +794,7 @@ PD_API pd_status pd_best_hits_all(pd_ctx* c, const pd_profiles* P, pd_hits** out
     H->all_pairs = 1;
     pdg::QuerySet Q{};
     Q.all_pairs = 1;
+    Q.order = P->view.order;
     Q.q0 = 0;
     Q.n_queries = P->view.n_genes;
     pd_status st = run_hits(c, P, Q, false, H.get());

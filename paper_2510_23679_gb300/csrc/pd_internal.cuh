@@ -5,12 +5,14 @@
 //
 //   gene g (global id, 0..G-1) has La[g] = max(0, |g|-k+1) k-mer windows.
 //   win_off[G+1]   uint32  exclusive prefix of La: window range of each gene.
-//   mv_len[G]      uint32  distinct k-mers of the gene (E_g <= La[g]).
-//   mv_id[W]       uint32  dense k-mer id, gene g at win_off[g] .. +mv_len[g],
+//   mv_n[G]        uint32  distinct k-mers of the gene (E_g <= La[g]).
+//   mv_id[W]       uint32  dense k-mer id, gene g at win_off[g] .. +mv_n[g],
 //                          ascending (the multiplicity vector of Algorithm 1,
 //                          stored in the gene's window range: "padded CSR").
 //   mv_cnt[W]      uint16  multiplicity of that k-mer in the gene.
-//   gene_genome[G] uint16  genome of each gene.
+//   mv_post[W],    uint32  posting range of that k-mer (copied from post_ptr so
+//   mv_plen[W]             a query reads its list bounds with its own vector).
+//   gene_genome[G] uint16  genome of each gene; ginfo[G] = La | genome << 16.
 //   bitmap[20^k/64] uint64 one bit per possible k-mer code: set if it occurs.
 //   word_rank[...]  uint32 number of set bits before each bitmap word, so the
 //                          dense id of code c is word_rank[c>>6] +
@@ -22,6 +24,9 @@
 //                          cnt_cap) with cnt_bits = 32 - bits(G-1).  A count
 //                          equal to cnt_cap is saturated; the exact value is
 //                          in the gene's multiplicity vector.
+//   order[G]       uint32  all-pairs query order: genes grouped by the top bits
+//                          of their min-hash (minimum of a hash of their k-mer
+//                          ids), so likely homologs run together.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -149,28 +154,34 @@ struct ProfilesView {
   uint32_t n_genes, n_genomes;
   uint64_t n_windows, n_distinct, n_entries;
   uint32_t cnt_bits, cnt_cap, max_posting;
-  const uint32_t* win_off;
-  const uint32_t* mv_len;
-  const uint32_t* mv_id;
-  const uint16_t* mv_cnt;
-  const uint32_t* La;
-  const uint16_t* gene_genome;
-  const int32_t* genome_ptr;  // device copy, n_genomes+1
+  const uint32_t* win_off;      // [G+1] window range of each gene
+  const uint32_t* mv_n;         // [G]   distinct k-mers of each gene
+  const uint32_t* mv_id;        // [W]   multiplicity vectors: dense ids
+  const uint16_t* mv_cnt;       // [W]   multiplicities
+  const uint32_t* mv_post;      // [W]   posting-list start of each entry's id
+  const uint32_t* mv_plen;      // [W]   posting-list length of each entry's id
+  const uint32_t* La;           // [G]   windows per gene
+  const uint16_t* gene_genome;  // [G]   genome of each gene
+  const uint32_t* ginfo;        // [G]   La | genome << 16
+  const int32_t* genome_ptr;    // [n+1] device copy
   const unsigned long long* bitmap;
   const uint32_t* word_rank;
   uint64_t n_words;
-  const uint32_t* post_ptr;
-  const uint32_t* post;
+  const uint32_t* post_ptr;     // [D+1]
+  const uint32_t* post;         // [E]   packed postings
+  const uint32_t* order;        // [G]   all-pairs query order (min-hash buckets)
 };
 
 // Target selection of one sum-min launch.
-//   all_pairs = 1: queries are genes q0..q0+n_queries-1 and each query targets
-//                  every genome except its own.
+//   all_pairs = 1: query index x is gene order[x] (or q0 + x without an order)
+//                  and each query targets every genome except its own; its
+//                  output row is its gene id.
 //   all_pairs = 0: query index x < nA is gene qa0 + x targeting genes
 //                  [ta0, ta1); index x >= nA is gene qb0 + (x - nA) targeting
-//                  [tb0, tb1).
+//                  [tb0, tb1); the output row is x.
 struct QuerySet {
   int all_pairs;
+  const uint32_t* order;
   uint32_t q0, n_queries;
   uint32_t qa0, nA, ta0, ta1;
   uint32_t qb0, tb0, tb1;
@@ -181,20 +192,31 @@ struct HitsOut {
   uint32_t* out_s;                   // sum-min
   unsigned long long out_cap;        // capacity of out_b / out_s
   unsigned long long* cursor;        // append cursor (keeps counting past cap)
-  unsigned long long* row_off;       // per query index
-  uint32_t* row_len;                 // per query index
-  uint32_t* deferred;                // query indices for the large path
-  uint32_t* n_deferred;
+  unsigned long long* row_off;       // per output row
+  uint32_t* row_len;                 // per output row
+  uint32_t* def1;                    // queries deferred by tier 1 ...
+  uint32_t* n_def1;
+  uint32_t* def2;                    // ... and by tier 2
+  uint32_t* n_def2;
   unsigned long long* walked;        // postings visited
 };
 
-// Large-accumulator (global memory) scratch of the second tier.
+// Global-memory scratch of the last tier (per block: table and hits).
 struct BigScratch {
   uint32_t* keys;        // n_ctas * cap
   uint32_t* vals;        // n_ctas * cap
   unsigned long long* out;  // n_ctas * out_cap
   uint32_t cap;          // power of two
-  uint32_t out_cap;      // power of two
+  uint32_t out_cap;
+};
+
+// Queries of one sum-min launch: the range 0..n_queries-1 (first tier) or a
+// list of query indices with its count in device memory (later tiers).
+struct TierIO {
+  const uint32_t* in_list;
+  const uint32_t* in_count;
+  uint32_t* def_list;   // deferred queries (nullptr in the last tier)
+  uint32_t* def_count;
 };
 
 // ---------------------------------------------------------------- launchers
@@ -217,18 +239,27 @@ cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene
                             unsigned long long* bitmap, DevErr* err, cudaStream_t s);
 cudaError_t run_mv_build(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, const uint32_t* win_off,
                          uint32_t n_genes, int k, const unsigned long long* bitmap, const uint32_t* word_rank,
-                         uint32_t* mv_id, uint16_t* mv_cnt, uint32_t* mv_len, uint32_t* hist,
+                         uint32_t* mv_id, uint16_t* mv_cnt, uint32_t* mv_n, uint32_t* minhash,
                          const uint32_t* long_genes, uint32_t n_long, uint32_t* long_scratch,
                          const uint32_t* long_scratch_off, uint32_t max_smem_sort, cudaStream_t s);
-cudaError_t run_post_fill(Launcher* L, const uint32_t* win_off, const uint32_t* mv_len, const uint32_t* mv_id,
-                          const uint16_t* mv_cnt, uint32_t n_genes, const uint32_t* post_ptr, uint32_t* fill,
-                          uint32_t* post, uint32_t cnt_bits, uint32_t cnt_cap, cudaStream_t s);
-cudaError_t run_post_sort(Launcher* L, const uint32_t* post_ptr, uint64_t n_lists, uint32_t* post,
-                          uint32_t* queue, uint32_t* queue_len, uint32_t max_posting, uint32_t* long_scratch,
-                          cudaStream_t s);
-cudaError_t run_max_u32(Launcher* L, const uint32_t* a, uint64_t n, uint32_t* out, cudaStream_t s);
-cudaError_t run_gene_genome(Launcher* L, const int32_t* genome_ptr, uint32_t n_genomes, uint16_t* gene_genome,
-                            cudaStream_t s);
+cudaError_t run_bucket_count(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
+                             uint32_t n_genes, uint32_t shift, uint32_t n_buckets, uint32_t* bucket_count,
+                             cudaStream_t s);
+cudaError_t run_bucket_scatter(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
+                               const uint16_t* mv_cnt, uint32_t n_genes, uint32_t shift, uint32_t n_buckets,
+                               uint32_t* bucket_cursor, uint32_t cnt_bits, uint32_t cnt_cap,
+                               unsigned long long* recs, cudaStream_t s);
+cudaError_t run_bucket_fine(Launcher* L, const uint32_t* bucket_start, uint32_t n_buckets, uint32_t shift,
+                            uint64_t n_ids, unsigned long long* recs, uint32_t* post_ptr, uint32_t* post,
+                            uint32_t* max_posting, cudaStream_t s);
+cudaError_t run_mv_post(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
+                        uint32_t n_genes, const uint32_t* post_ptr, uint32_t* mv_post, uint32_t* mv_plen,
+                        cudaStream_t s);
+// count must hold 2 * 2^(32-shift) + 1 words (counts, then their prefix sum).
+cudaError_t run_order(Launcher* L, const uint32_t* minhash, uint32_t n_genes, uint32_t shift, uint32_t* count,
+                      uint32_t* order, void* scan_tmp, cudaStream_t s);
+cudaError_t run_gene_info(Launcher* L, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* La,
+                          uint16_t* gene_genome, uint32_t* ginfo, cudaStream_t s);
 cudaError_t run_select_codes(Launcher* L, const unsigned long long* bitmap, const uint32_t* word_rank,
                              uint64_t n_words, unsigned long long* code_of_id, cudaStream_t s);
 cudaError_t run_export_mv(Launcher* L, const ProfilesView& P, const unsigned long long* mv_ptr,
@@ -237,13 +268,15 @@ cudaError_t run_export_mv(Launcher* L, const ProfilesView& P, const unsigned lon
 cudaError_t run_export_index(Launcher* L, const ProfilesView& P, int32_t* genes, uint32_t* counts,
                              cudaStream_t s);
 
-// sum-min and Best Hits (k_summin.cu)
+// sum-min and Best Hits (k_summin.cu): shared-memory tiers 1 and 2 in one
+// call (tier 2 reads tier 1's deferred list on the device), then, only if
+// tier 2 deferred queries, the global-memory tier.
 size_t summin_smem_bytes(uint32_t n_genomes, bool emit_all);
-cudaError_t run_summin_bh(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O, DevErr* err,
-                          bool emit_all, cudaStream_t s);
-cudaError_t run_summin_bh_big(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O,
-                              const BigScratch& B, uint32_t n_ctas, DevErr* err, bool emit_all,
-                              cudaStream_t s);
+cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O, DevErr* err,
+                             bool emit_all, cudaStream_t s);
+size_t summin_global_smem_bytes(uint32_t n_genomes);
+cudaError_t run_summin_global(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O,
+                              const BigScratch& B, uint32_t n_ctas, DevErr* err, bool emit_all, cudaStream_t s);
 
 // BBH and result gathering (k_bbh.cu)
 cudaError_t run_gather_rows(Launcher* L, uint32_t n_rows, const unsigned long long* row_off,
