@@ -47,33 +47,73 @@ __device__ __forceinline__ uint32_t hash_gene(uint32_t b) {
   return h ^ (h >> 15);
 }
 
-// Probes allowed before a query counts as overflowing its table.  With the
-// load limited this way (and a mixing hash) long chains mean a nearly full
-// table; the query then moves to a larger tier, so the bound never changes a
-// result, only where it is computed.
+// Probes allowed before a query counts as overflowing its table.  Long chains
+// mean a nearly full table; the query then moves to a larger tier, so the
+// bound never changes a result, only where it is computed.
 constexpr uint32_t kMaxProbe = 64;
 
-// Add m to the accumulator of gene b.  Returns false after kMaxProbe probes
-// without finding b or a free slot (the query is deferred).
-__device__ __forceinline__ bool acc_add(uint32_t* keys, uint32_t* vals, uint32_t mask, uint32_t b, uint32_t m) {
-  uint32_t h = hash_gene(b) & mask;
-  for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
-    const uint32_t k = *((volatile uint32_t*)&keys[h]);
-    if (k == b) {
-      atomicAdd(&vals[h], m);
-      return true;
-    }
-    if (k == kEmpty) {
-      const uint32_t prev = atomicCAS(&keys[h], kEmpty, b);
-      if (prev == kEmpty || prev == b) {
-        atomicAdd(&vals[h], m);
-        return true;
+// Two table layouts share the code below.
+//   packed (tier 1): one word per slot, (b << cnt_bits) | s.  Valid while
+//     s < 2^cnt_bits - 1, which holds for every query with La < 2^cnt_bits - 1
+//     since s <= La; other queries go to tier 2.  The empty word 0xFFFFFFFF
+//     can never be a real slot because s stays below the all-ones count.
+//   split (tiers 2 and 3): keys[] = b, vals[] = s.
+template <bool kPacked>
+struct Acc {
+  uint32_t* keys;  // packed: slot words
+  uint32_t* vals;  // split only
+  uint32_t cnt_bits;
+
+  __device__ __forceinline__ bool add(uint32_t mask, uint32_t b, uint32_t m) const {
+    uint32_t h = hash_gene(b) & mask;
+    for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
+      const uint32_t k = *((volatile uint32_t*)&keys[h]);
+      if (kPacked) {
+        if (k != kEmpty && (k >> cnt_bits) == b) {
+          atomicAdd(&keys[h], m);
+          return true;
+        }
+        if (k == kEmpty) {
+          const uint32_t prev = atomicCAS(&keys[h], kEmpty, (b << cnt_bits) | m);
+          if (prev == kEmpty) return true;
+          if ((prev >> cnt_bits) == b) {
+            atomicAdd(&keys[h], m);
+            return true;
+          }
+        }
+      } else {
+        if (k == b) {
+          atomicAdd(&vals[h], m);
+          return true;
+        }
+        if (k == kEmpty) {
+          const uint32_t prev = atomicCAS(&keys[h], kEmpty, b);
+          if (prev == kEmpty || prev == b) {
+            atomicAdd(&vals[h], m);
+            return true;
+          }
+        }
       }
+      h = (h + 1) & mask;
     }
-    h = (h + 1) & mask;
+    return false;
   }
-  return false;
-}
+  __device__ __forceinline__ bool occupied(uint32_t h) const { return keys[h] != kEmpty; }
+  __device__ __forceinline__ void get(uint32_t h, uint32_t* b, uint32_t* s) const {
+    const uint32_t k = keys[h];
+    if (kPacked) {
+      *b = k >> cnt_bits;
+      *s = k & ((1u << cnt_bits) - 1u);
+    } else {
+      *b = k;
+      *s = vals[h];
+    }
+  }
+  __device__ __forceinline__ void clear(uint32_t h) const {
+    keys[h] = kEmpty;
+    if (!kPacked) vals[h] = 0;
+  }
+};
 
 __device__ __forceinline__ uint32_t lower_bound_post(const uint32_t* __restrict__ post, uint32_t lo, uint32_t hi,
                                                      unsigned long long key) {
@@ -115,23 +155,25 @@ struct Chunk {
   static constexpr size_t kBytes = (((size_t)kSize * 4 + (size_t)(kSize + 1) * 4 + (size_t)kSize * 2) + 15) & ~(size_t)15;
 };
 
-// Table geometry of one call (shared or global memory).
+// Memory of one call: table, the list of occupied slots (filled after the
+// walk) and the hit list.
+template <typename TIdx>
 struct Table {
   uint32_t* keys;
-  uint32_t* vals;
-  unsigned long long* out;
-  uint32_t cap;      // power of two, a multiple of the block size
-  uint32_t out_cap;  // hits (or emitted pairs) that fit in `out`
+  uint32_t* vals;          // split layout only
+  TIdx* used;              // capacity cap
+  unsigned long long* out; // capacity out_cap
+  uint32_t cap;            // power of two, a multiple of the block size
+  uint32_t out_cap;
 };
 
-template <int kThreads, bool kEmitAll, uint32_t kSlots>
+template <int kThreads, bool kEmitAll, bool kPacked, typename TIdx>
 __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P, const QuerySet& Q,
-                                              const HitsOut& O, const TierIO& T, DevErr* err, const Table& tb,
-                                              uint32_t* c_post, uint32_t* c_off, uint16_t* c_cnt,
-                                              unsigned long long* best, Scalars* sh) {
+                                              const HitsOut& O, const TierIO& T, DevErr* err,
+                                              const Table<TIdx>& tb, uint32_t* c_post, uint32_t* c_off,
+                                              uint16_t* c_cnt, unsigned long long* best, Scalars* sh) {
   constexpr uint32_t kChunk = Chunk<kThreads>::kSize, kItems = Chunk<kThreads>::kItems;
-  uint32_t* keys = tb.keys;
-  uint32_t* vals = tb.vals;
+  const Acc<kPacked> acc{tb.keys, tb.vals, P.cnt_bits};
   unsigned long long* out = tb.out;
   const uint32_t mask = tb.cap - 1u;
   // ---- query gene, its output row and its targets
@@ -163,11 +205,12 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
   const uint32_t tid = threadIdx.x;
   if (tid == 0) {
     sh->n_out = 0;
-    sh->overflow = 0;
+    // a packed slot holds s <= La_a: queries beyond the field go to tier 2
+    sh->overflow = (kPacked && La_a >= cnt_mask) ? 1u : 0u;
   }
   __syncthreads();
   unsigned long long walked = 0;
-  for (uint32_t c0 = 0; c0 < E; c0 += kChunk) {
+  for (uint32_t c0 = 0; c0 < E && !sh->overflow; c0 += kChunk) {
     const uint32_t n_c = min(kChunk, E - c0);
     // ---- stage the chunk: posting ranges and their prefix sum
     uint32_t len_loc[kItems];
@@ -239,68 +282,65 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
             if (Q.all_pairs && b >= own0 && b < own1) continue;
             uint32_t cb = p & cnt_mask;
             if (cb == P.cnt_cap && cav[j] > cb) cb = mv_count_of(P, b, P.mv_id[m0 + c0 + ev[j]]);
-            if (!acc_add(keys, vals, mask, b, min(cav[j], cb))) sh->overflow = 1;
+            if (!acc.add(mask, b, min(cav[j], cb))) sh->overflow = 1;
           }
         }
       }
     }
     __syncthreads();
-    if (sh->overflow) break;
   }
 
-  // Slots are visited interleaved (slot = i * kThreads + tid: conflict-free);
-  // an occupancy mask in registers lets the second pass skip empty slots.
-  // kSlots = 0 means the table size is only known at run time (global tier).
   const bool overflow = sh->overflow != 0;
-  const uint32_t slots = kSlots ? kSlots : tb.cap / kThreads;
+  // Slots are visited interleaved (slot = i * kThreads + tid: conflict-free).
+  const uint32_t slots = tb.cap / kThreads;
   if (!overflow) {
+    // ---- list the occupied slots (block prefix sum over per-thread counts)
+    uint32_t n_mine = 0;
+    for (uint32_t i = 0; i < slots; ++i) n_mine += acc.occupied(i * kThreads + tid) ? 1u : 0u;
+    uint32_t n_occ;
+    uint32_t pos = block_exclusive_scan(n_mine, sh->warp_tmp, &n_occ);
+    for (uint32_t i = 0; i < slots; ++i) {
+      const uint32_t h = i * kThreads + tid;
+      if (acc.occupied(h)) tb.used[pos++] = (TIdx)h;
+    }
+    __syncthreads();
     if (kEmitAll) {
-      for (uint32_t i = 0; i < slots; ++i) {
-        const uint32_t h = i * kThreads + tid;
-        const uint32_t b = keys[h];
-        if (b == kEmpty) continue;
+      for (uint32_t u = tid; u < n_occ; u += kThreads) {
+        const uint32_t h = tb.used[u];
+        uint32_t b, s;
+        acc.get(h, &b, &s);
         const uint32_t slot = atomicAdd(&sh->n_out, 1u);
-        if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | vals[h];
-        keys[h] = kEmpty;
-        vals[h] = 0;
+        if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | s;
+        acc.clear(h);
       }
     } else {
       // ---- per target genome: the maximum ratio, then every entry at it
       const uint32_t n_best = Q.all_pairs ? P.n_genomes : 1u;
       for (uint32_t j = tid; j < n_best; j += kThreads) best[j] = 0ull;
       __syncthreads();
-      uint32_t occ = 0;  // bit i: slot i * kThreads + tid is occupied (first 32 rounds)
-      for (uint32_t i = 0; i < slots; ++i) {
-        const uint32_t h = i * kThreads + tid;
-        const uint32_t b = keys[h];
-        if (b == kEmpty) continue;
-        if (i < 32) occ |= 1u << i;
-        const uint32_t s = vals[h];
+      for (uint32_t u = tid; u < n_occ; u += kThreads) {
+        uint32_t b, s;
+        acc.get(tb.used[u], &b, &s);
         const uint32_t gi = P.ginfo[b];
         best_update(&best[Q.all_pairs ? (gi >> 16) : 0u], s, La_a + (gi & 0xFFFFu) - s);
       }
       __syncthreads();
-      for (uint32_t i = 0; i < slots; ++i) {
-        if (i < 32 && !(occ & (1u << i))) continue;
-        const uint32_t h = i * kThreads + tid;
-        const uint32_t b = keys[h];
-        if (b == kEmpty) continue;
-        const uint32_t s = vals[h];
+      for (uint32_t u = tid; u < n_occ; u += kThreads) {
+        const uint32_t h = tb.used[u];
+        uint32_t b, s;
+        acc.get(h, &b, &s);
         const uint32_t gi = P.ginfo[b];
         const unsigned long long bv = best[Q.all_pairs ? (gi >> 16) : 0u];
         if (ratio_equal(s, La_a + (gi & 0xFFFFu) - s, (uint32_t)(bv >> 32), (uint32_t)bv)) {
           const uint32_t slot = atomicAdd(&sh->n_out, 1u);
           if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | s;
         }
-        keys[h] = kEmpty;
-        vals[h] = 0;
+        acc.clear(h);
       }
     }
   } else {
-    for (uint32_t i = 0; i < slots; ++i) {
-      keys[i * kThreads + tid] = kEmpty;
-      vals[i * kThreads + tid] = 0;
-    }
+    // the walk stopped early: clear every slot
+    for (uint32_t i = 0; i < slots; ++i) acc.clear(i * kThreads + tid);
   }
   __syncthreads();
   const uint32_t n_out = sh->n_out;
@@ -340,54 +380,58 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
   __syncthreads();
 }
 
-// ---- shared-memory tiers: [keys cap][vals cap][chunk | hits][best]
-template <int kThreads, uint32_t kCap, uint32_t kOutCap>
+// ---- shared-memory tiers: [table][chunk | (used list, hits)][best]
+template <int kThreads, uint32_t kCap, uint32_t kOutCap, bool kPacked>
 struct SmemTier {
   static_assert(kCap % kThreads == 0, "table must split evenly over the block");
-  static constexpr size_t kTable = (size_t)kCap * 8;
-  static constexpr size_t kUnion =
-      Chunk<kThreads>::kBytes > (size_t)kOutCap * 8 ? Chunk<kThreads>::kBytes : (size_t)kOutCap * 8;
+  static_assert(kCap <= 65536, "slot indices are 16-bit");
+  static constexpr size_t kTable = (size_t)kCap * (kPacked ? 4 : 8);
+  static constexpr size_t kUsed = (size_t)kCap * 2;
+  static constexpr size_t kAfterWalk = kUsed + (size_t)kOutCap * 8;
+  static constexpr size_t kUnion = Chunk<kThreads>::kBytes > kAfterWalk ? Chunk<kThreads>::kBytes : kAfterWalk;
   static size_t bytes(uint32_t n_best) { return kTable + kUnion + (size_t)(n_best ? n_best : 1) * 8; }
 };
 
-template <int kThreads, uint32_t kCap, uint32_t kOutCap, bool kEmitAll>
-__global__ void __launch_bounds__(kThreads) k_summin_smem(ProfilesView P, QuerySet Q, HitsOut O, TierIO T,
-                                                          DevErr* err) {
-  using S = SmemTier<kThreads, kCap, kOutCap>;
+template <int kThreads, int kMinBlocks, uint32_t kCap, uint32_t kOutCap, bool kPacked, bool kEmitAll>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) k_summin_smem(ProfilesView P, QuerySet Q, HitsOut O,
+                                                                      TierIO T, DevErr* err) {
+  using S = SmemTier<kThreads, kCap, kOutCap, kPacked>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Scalars sh;
-  Table tb;
+  Table<uint16_t> tb;
   tb.keys = (uint32_t*)smem;
-  tb.vals = tb.keys + kCap;
+  tb.vals = kPacked ? nullptr : tb.keys + kCap;
   tb.cap = kCap;
   tb.out_cap = kOutCap;
   unsigned char* uni = smem + S::kTable;
-  tb.out = (unsigned long long*)uni;
+  tb.used = (uint16_t*)uni;
+  tb.out = (unsigned long long*)(uni + S::kUsed);
   uint32_t* c_post = (uint32_t*)uni;
   uint32_t* c_off = c_post + Chunk<kThreads>::kSize;
   uint16_t* c_cnt = (uint16_t*)(c_off + Chunk<kThreads>::kSize + 1);
   unsigned long long* best = (unsigned long long*)(uni + S::kUnion);
   for (uint32_t h = threadIdx.x; h < kCap; h += kThreads) {
     tb.keys[h] = kEmpty;
-    tb.vals[h] = 0;
+    if (!kPacked) tb.vals[h] = 0;
   }
   __syncthreads();
   const uint32_t n = T.in_list ? *T.in_count : Q.n_queries;
   for (uint32_t x = blockIdx.x; x < n; x += gridDim.x)
-    process_query<kThreads, kEmitAll, kCap / kThreads>(T.in_list ? T.in_list[x] : x, P, Q, O, T, err, tb, c_post,
-                                                       c_off, c_cnt, best, &sh);
+    process_query<kThreads, kEmitAll, kPacked, uint16_t>(T.in_list ? T.in_list[x] : x, P, Q, O, T, err, tb, c_post,
+                                                         c_off, c_cnt, best, &sh);
 }
 
-// ---- global-memory tier: table and hit list of each block in scratch
+// ---- global-memory tier: table, used list and hit list of each block in scratch
 template <bool kEmitAll>
 __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet Q, HitsOut O, TierIO T,
                                                        BigScratch B, DevErr* err) {
   constexpr int kThreads = 256;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Scalars sh;
-  Table tb;
+  Table<uint32_t> tb;
   tb.keys = B.keys + (size_t)blockIdx.x * B.cap;
   tb.vals = B.vals + (size_t)blockIdx.x * B.cap;
+  tb.used = B.used + (size_t)blockIdx.x * B.cap;
   tb.out = B.out + (size_t)blockIdx.x * B.out_cap;
   tb.cap = B.cap;
   tb.out_cap = B.out_cap;
@@ -402,21 +446,23 @@ __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet 
   __syncthreads();
   const uint32_t n = *T.in_count;
   for (uint32_t x = blockIdx.x; x < n; x += gridDim.x)
-    process_query<kThreads, kEmitAll, 0>(T.in_list[x], P, Q, O, T, err, tb, c_post, c_off, c_cnt, best, &sh);
+    process_query<kThreads, kEmitAll, false, uint32_t>(T.in_list[x], P, Q, O, T, err, tb, c_post, c_off, c_cnt, best,
+                                                       &sh);
 }
 
-// Tier 1 and tier 2 geometries.
-constexpr int kT1Threads = 256;
+// Tier 1 (packed 4096-slot table, several blocks per SM) and tier 2 (split
+// 16384-slot table, one 1024-thread block per SM) geometries.
+constexpr int kT1Threads = 256, kT1MinBlocks = 6;
 constexpr uint32_t kT1Cap = 4096, kT1Out = 512, kT1OutEmit = 3072;
 constexpr int kT2Threads = 1024;
-constexpr uint32_t kT2Cap = 16384, kT2Out = 4096, kT2OutEmit = 8192;  // keeps tier 2 under 227 KB
-
-static_assert(SmemTier<kT1Threads, kT1Cap, kT1Out>::kTable + SmemTier<kT1Threads, kT1Cap, kT1Out>::kUnion +
-                  PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 1 shared memory");
-static_assert(SmemTier<kT2Threads, kT2Cap, kT2Out>::kTable + SmemTier<kT2Threads, kT2Cap, kT2Out>::kUnion +
-                  PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 2 shared memory");
-static_assert(SmemTier<kT2Threads, kT2Cap, kT2OutEmit>::kTable + SmemTier<kT2Threads, kT2Cap, kT2OutEmit>::kUnion +
-                  8 <= 227 * 1024, "tier 2 (emit-all, one target genome) shared memory");
+constexpr uint32_t kT2Cap = 16384, kT2Out = 2048, kT2OutEmit = 4096;
+using T1 = SmemTier<kT1Threads, kT1Cap, kT1Out, true>;
+using T1E = SmemTier<kT1Threads, kT1Cap, kT1OutEmit, true>;
+using T2 = SmemTier<kT2Threads, kT2Cap, kT2Out, false>;
+using T2E = SmemTier<kT2Threads, kT2Cap, kT2OutEmit, false>;
+static_assert(T1::kTable + T1::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 1 shared memory");
+static_assert(T2::kTable + T2::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 2 shared memory");
+static_assert(T2E::kTable + T2E::kUnion + 8 <= 227 * 1024, "tier 2 (emit-all, one target genome) shared memory");
 
 template <typename K>
 cudaError_t launch_smem(K kernel, Launcher* L, const char* name, int threads, size_t smem, uint32_t max_grid,
@@ -437,8 +483,7 @@ cudaError_t launch_smem(K kernel, Launcher* L, const char* name, int threads, si
 }  // namespace
 
 size_t summin_smem_bytes(uint32_t n_genomes, bool emit_all) {
-  return emit_all ? SmemTier<kT1Threads, kT1Cap, kT1OutEmit>::bytes(n_genomes)
-                  : SmemTier<kT1Threads, kT1Cap, kT1Out>::bytes(n_genomes);
+  return emit_all ? T1E::bytes(n_genomes) : T1::bytes(n_genomes);
 }
 
 cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O, DevErr* err,
@@ -450,19 +495,19 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
   cudaError_t e;
   // tier 1: several resident blocks per SM, each looping over queries
   if (emit_all)
-    e = launch_smem(k_summin_smem<kT1Threads, kT1Cap, kT1OutEmit, true>, L, "summin_pairs", kT1Threads,
-                    SmemTier<kT1Threads, kT1Cap, kT1OutEmit>::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
+    e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutEmit, true, true>, L, "summin_pairs",
+                    kT1Threads, T1E::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   else
-    e = launch_smem(k_summin_smem<kT1Threads, kT1Cap, kT1Out, false>, L, "summin_bh", kT1Threads,
-                    SmemTier<kT1Threads, kT1Cap, kT1Out>::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
+    e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false>, L, "summin_bh",
+                    kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   if (e != cudaSuccess) return e;
   // tier 2: one 1024-thread block per SM over the deferred queries (exits at once if none)
   if (emit_all)
-    e = launch_smem(k_summin_smem<kT2Threads, kT2Cap, kT2OutEmit, true>, L, "summin_pairs_t2", kT2Threads,
-                    SmemTier<kT2Threads, kT2Cap, kT2OutEmit>::bytes(n_best), Q.n_queries, P, Q, O, t2, err, s);
+    e = launch_smem(k_summin_smem<kT2Threads, 1, kT2Cap, kT2OutEmit, false, true>, L, "summin_pairs_t2", kT2Threads,
+                    T2E::bytes(n_best), Q.n_queries, P, Q, O, t2, err, s);
   else
-    e = launch_smem(k_summin_smem<kT2Threads, kT2Cap, kT2Out, false>, L, "summin_bh_t2", kT2Threads,
-                    SmemTier<kT2Threads, kT2Cap, kT2Out>::bytes(n_best), Q.n_queries, P, Q, O, t2, err, s);
+    e = launch_smem(k_summin_smem<kT2Threads, 1, kT2Cap, kT2Out, false, false>, L, "summin_bh_t2", kT2Threads,
+                    T2::bytes(n_best), Q.n_queries, P, Q, O, t2, err, s);
   return e;
 }
 

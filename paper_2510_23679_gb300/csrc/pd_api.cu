@@ -735,12 +735,14 @@ static pd_status run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& 
       B.cap = std::max<uint32_t>(pdg::next_pow2(4 * targets), 256);  // load <= 1/4: short probe chains
       B.out_cap = pdg::next_pow2(targets);
       const uint32_t n_ctas = std::min<uint32_t>(n_def2, 64);
-      Buf bk, bv, bo;
+      Buf bk, bv, bu, bo;
       ALLOC(bk, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
       ALLOC(bv, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
+      ALLOC(bu, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
       ALLOC(bo, sizeof(unsigned long long) * (size_t)B.out_cap * n_ctas);
       B.keys = bk.as<uint32_t>();
       B.vals = bv.as<uint32_t>();
+      B.used = bu.as<uint32_t>();
       B.out = bo.as<unsigned long long>();
       CK(pdg::run_summin_global(L, v, Q, O, B, n_ctas, c->d_err, emit_all, c->stream));
       CK(cudaMemcpyAsync(h, counters.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));

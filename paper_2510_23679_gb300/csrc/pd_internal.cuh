@@ -201,10 +201,12 @@ struct HitsOut {
   unsigned long long* walked;        // postings visited
 };
 
-// Global-memory scratch of the last tier (per block: table and hits).
+// Global-memory scratch of the last tier (per block: table, occupied-slot
+// list and hits).
 struct BigScratch {
   uint32_t* keys;        // n_ctas * cap
   uint32_t* vals;        // n_ctas * cap
+  uint32_t* used;        // n_ctas * cap
   unsigned long long* out;  // n_ctas * out_cap
   uint32_t cap;          // power of two
   uint32_t out_cap;
