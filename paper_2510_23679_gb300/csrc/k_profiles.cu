@@ -9,16 +9,13 @@
 //   (scan)         popcount prefix of the bitmap words: the dense id of a code
 //                  is its rank among the codes present (an injective f that is
 //                  ascending with the code, "Multiplicity vector building").
-//   mv_build       per gene: ids of its windows, sorted in shared memory,
-//                  run-length encoded into (id, multiplicity) pairs (Eqs.
-//                  (2)-(3)); also a min-hash of the gene's ids.
-//   bucket_count   the inverted index is the transpose of the multiplicity
-//   (scan)         vectors.  It is built in two levels: ids are grouped into
-//   bucket_scatter at most 24576 buckets of 2^s consecutive ids; every (id,
-//   bucket_fine    gene, count) record is scattered into its bucket (per-block
-//                  histograms in shared memory reserve contiguous runs), then
-//                  one block per bucket counts the records per id, writes the
-//                  id offsets, places the postings and sorts each list by gene.
+//   mv_build       per gene: ids of its windows counted in a shared-memory
+//                  hash table, compacted into (id, multiplicity) pairs (Eqs.
+//                  (2)-(3)), one index record per pair; also a min-hash.
+//   (radix sort)   the inverted index is the transpose of the multiplicity
+//                  vectors: the index records are sorted by k-mer id with a
+//                  stable radix sort (k_radix.cu), which keeps each posting
+//                  list in gene order.
 //   mv_post        each multiplicity-vector entry gets its posting range, so
 //                  the sum-min kernel reads list bounds from its own
 //                  (coalesced) vector instead of the id offset table.
@@ -33,8 +30,8 @@ namespace {
 constexpr int kEncThreads = 256;
 constexpr int kMvThreads = 256;
 constexpr int kMvLongThreads = 1024;
-constexpr int kBucketThreads = 512;
-constexpr int kFineThreads = 256;
+constexpr uint32_t kMvSmallCap = 2048;  // table slots of the shared-memory multiplicity-vector build
+constexpr uint32_t kMvMidCap = 16384;   // ... of its 1024-thread variant (one block per SM)
 
 __device__ __forceinline__ uint32_t mix32(uint32_t x) {
   x ^= x >> 16;
@@ -81,53 +78,72 @@ __device__ __forceinline__ uint32_t code_rank(unsigned long long code, const uns
   return word_rank[code >> 6] + (uint32_t)__popcll(w & below);
 }
 
-// Multiplicity vector of gene g, with `keys` (shared or global) holding at
-// least next_pow2(La) words.  Called by every thread of the block.
-__device__ __forceinline__ void mv_build_one(uint32_t g, uint32_t* keys, const uint8_t* __restrict__ lut,
-                                             uint32_t* warp_tmp, const uint8_t* __restrict__ res,
-                                             const int64_t* __restrict__ gene_ptr,
+// Multiplicity vector of gene g (Eqs. (2)-(3)): the dense ids of its windows
+// are counted in an open-addressing table of 64-bit slots (id << 32 | count)
+// of `cap` slots (a power of two, at least 1.5 x La), then the occupied slots
+// are compacted into the gene's window range.  The entries of one vector are
+// in table order: nothing downstream depends on their order (sums commute,
+// posting lists are sorted by gene later, and the export hook sorts by code).
+// Besides (id, count) the gene emits one 64-bit record per entry for the
+// index build, (id << 32) | packed posting, and marks the unused tail of its
+// window range with all-ones records.  Called by every thread of the block.
+__device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* table, uint32_t cap,
+                                             const uint8_t* __restrict__ lut, uint32_t* warp_tmp,
+                                             const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr,
                                              const uint32_t* __restrict__ win_off, int k,
                                              const unsigned long long* __restrict__ bitmap,
-                                             const uint32_t* __restrict__ word_rank, uint32_t* __restrict__ mv_id,
-                                             uint16_t* __restrict__ mv_cnt, uint32_t* __restrict__ mv_n,
-                                             uint32_t* __restrict__ minhash) {
+                                             const uint32_t* __restrict__ word_rank, const MvOut& M) {
+  constexpr unsigned long long kFree = ~0ull;
   const uint32_t off = win_off[g];
   const uint32_t La = win_off[g + 1] - off;
   const uint8_t* s = res + gene_ptr[g];
-  const uint32_t n2 = next_pow2(La);
-  for (uint32_t p = threadIdx.x; p < n2; p += blockDim.x) {
-    uint32_t key = kEmpty;
-    if (p < La) {
-      unsigned long long code = 0;
-      for (int t = 0; t < k; ++t) {
-        uint32_t c = lut[s[p + t]];
-        code = code * (unsigned long long)kAlphabetSize + (c < (uint32_t)kAlphabetSize ? c : 0u);
-      }
-      key = code_rank(code, bitmap, word_rank);
+  for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) table[h] = kFree;
+  __syncthreads();
+  for (uint32_t p = threadIdx.x; p < La; p += blockDim.x) {
+    unsigned long long code = 0;
+    for (int t = 0; t < k; ++t) {
+      const uint32_t c = lut[s[p + t]];
+      code = code * (unsigned long long)kAlphabetSize + (c < (uint32_t)kAlphabetSize ? c : 0u);
     }
-    keys[p] = key;
+    const uint32_t id = code_rank(code, bitmap, word_rank);
+    uint32_t h = mix32(id) & (cap - 1u);
+    uint32_t probe = 0;
+    for (; probe < cap; ++probe) {  // a free slot always exists: cap > La >= distinct ids
+      const unsigned long long cur = *((volatile unsigned long long*)&table[h]);
+      if (cur != kFree && (uint32_t)(cur >> 32) == id) {
+        atomicAdd(&table[h], 1ull);
+        break;
+      }
+      if (cur == kFree) {
+        const unsigned long long prev = atomicCAS(&table[h], kFree, ((unsigned long long)id << 32) | 1ull);
+        if (prev == kFree) break;
+        if ((uint32_t)(prev >> 32) == id) {
+          atomicAdd(&table[h], 1ull);
+          break;
+        }
+      }
+      h = (h + 1u) & (cap - 1u);
+    }
+    if (probe == cap) raise_error(M.err, PD_ERR_INTERNAL, g);  // unreachable by the bound above
   }
   __syncthreads();
-  if (n2 > 1) block_bitonic_sort(keys, n2);
-  // run-length encoding: each thread owns a contiguous segment of positions
-  const uint32_t seg = (La + blockDim.x - 1) / blockDim.x;
-  const uint32_t p0 = min(La, threadIdx.x * seg), p1 = min(La, p0 + seg);
-  uint32_t heads = 0;
-  for (uint32_t p = p0; p < p1; ++p) heads += (p == 0 || keys[p] != keys[p - 1]) ? 1u : 0u;
-  uint32_t total;
-  uint32_t idx = block_exclusive_scan(heads, warp_tmp, &total);
+  // compaction of the occupied slots (interleaved: slot = i * blockDim + tid)
+  uint32_t mine = 0;
+  for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) mine += table[h] != kFree ? 1u : 0u;
+  uint32_t E;
+  uint32_t pos = block_exclusive_scan(mine, warp_tmp, &E);
   uint32_t mh = kEmpty;
-  for (uint32_t p = p0; p < p1; ++p) {
-    if (p == 0 || keys[p] != keys[p - 1]) {
-      const uint32_t id = keys[p];
-      uint32_t q = p + 1;
-      while (q < La && keys[q] == id) ++q;
-      mv_id[off + idx] = id;
-      mv_cnt[off + idx] = (uint16_t)(q - p);
-      mh = min(mh, mix32(id));
-      ++idx;
-    }
+  for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) {
+    const unsigned long long v = table[h];
+    if (v == kFree) continue;
+    const uint32_t id = (uint32_t)(v >> 32), c = (uint32_t)v;
+    M.mv_id[off + pos] = id;
+    M.mv_cnt[off + pos] = (uint16_t)c;
+    M.rec[off + pos] = ((unsigned long long)id << 32) | (g << M.cnt_bits) | (c < M.cnt_cap ? c : M.cnt_cap);
+    mh = min(mh, mix32(id));
+    ++pos;
   }
+  for (uint32_t p = E + threadIdx.x; p < La; p += blockDim.x) M.rec[off + p] = kFree;
   // block minimum of the hashed ids (warp_tmp is free again after the scan)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mh = min(mh, __shfl_xor_sync(0xffffffffu, mh, o));
@@ -136,212 +152,76 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, uint32_t* keys, const u
   if ((threadIdx.x & 31u) == 0) atomicMin(&warp_tmp[0], mh);
   __syncthreads();
   if (threadIdx.x == 0) {
-    mv_n[g] = total;
-    minhash[g] = warp_tmp[0];
+    M.mv_n[g] = E;
+    M.minhash[g] = warp_tmp[0];
   }
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kMvThreads)
+__host__ __device__ __forceinline__ uint32_t mv_table_cap(uint32_t La) {
+  const uint32_t c = next_pow2(La + La / 2 + 1);
+  return c < 64 ? 64 : c;
+}
+
+// Genes whose table fits `max_cap` slots of shared memory: all genes with a
+// table of at most max_cap slots (list == nullptr), or the listed genes.
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads)
     k_mv_build_smem(const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr,
                     const uint32_t* __restrict__ win_off, uint32_t n_genes, int k,
-                    const unsigned long long* __restrict__ bitmap, const uint32_t* __restrict__ word_rank,
-                    uint32_t* __restrict__ mv_id, uint16_t* __restrict__ mv_cnt, uint32_t* __restrict__ mv_n,
-                    uint32_t* __restrict__ minhash, uint32_t max_sort) {
-  extern __shared__ uint32_t keys[];
+                    const unsigned long long* __restrict__ bitmap, const uint32_t* __restrict__ word_rank, MvOut M,
+                    uint32_t max_cap, const uint32_t* __restrict__ list, uint32_t n_list) {
+  extern __shared__ unsigned long long table[];
   __shared__ uint8_t lut[256];
-  __shared__ uint32_t warp_tmp[kMvThreads / 32 + 1];
+  __shared__ uint32_t warp_tmp[kThreads / 32 + 1];
   init_letter_table(lut);
-  for (uint32_t g = blockIdx.x; g < n_genes; g += gridDim.x) {
-    const uint32_t La = win_off[g + 1] - win_off[g];
-    if (next_pow2(La) > max_sort) continue;  // long gene: other kernel
-    mv_build_one(g, keys, lut, warp_tmp, res, gene_ptr, win_off, k, bitmap, word_rank, mv_id, mv_cnt, mv_n,
-                 minhash);
+  const uint32_t n = list ? n_list : n_genes;
+  for (uint32_t x = blockIdx.x; x < n; x += gridDim.x) {
+    const uint32_t g = list ? list[x] : x;
+    const uint32_t cap = mv_table_cap(win_off[g + 1] - win_off[g]);
+    if (cap > max_cap) continue;  // uniform over the block: built by a later launch
+    mv_build_one(g, table, cap, lut, warp_tmp, res, gene_ptr, win_off, k, bitmap, word_rank, M);
   }
 }
 
+// Genes too long for shared memory: tables in global scratch (one per gene).
 __global__ void __launch_bounds__(kMvLongThreads)
     k_mv_build_long(const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr,
                     const uint32_t* __restrict__ win_off, int k, const unsigned long long* __restrict__ bitmap,
-                    const uint32_t* __restrict__ word_rank, uint32_t* __restrict__ mv_id,
-                    uint16_t* __restrict__ mv_cnt, uint32_t* __restrict__ mv_n, uint32_t* __restrict__ minhash,
-                    const uint32_t* __restrict__ long_genes, uint32_t n_long, uint32_t* scratch,
-                    const uint32_t* __restrict__ scratch_off) {
+                    const uint32_t* __restrict__ word_rank, MvOut M, const uint32_t* __restrict__ long_genes,
+                    uint32_t n_long, unsigned long long* scratch, const unsigned long long* __restrict__ scratch_off) {
   __shared__ uint8_t lut[256];
   __shared__ uint32_t warp_tmp[kMvLongThreads / 32 + 1];
   init_letter_table(lut);
   for (uint32_t x = blockIdx.x; x < n_long; x += gridDim.x) {
-    mv_build_one(long_genes[x], scratch + scratch_off[x], lut, warp_tmp, res, gene_ptr, win_off, k, bitmap,
-                 word_rank, mv_id, mv_cnt, mv_n, minhash);
+    const uint32_t g = long_genes[x];
+    mv_build_one(g, scratch + scratch_off[x], mv_table_cap(win_off[g + 1] - win_off[g]), lut, warp_tmp, res,
+                 gene_ptr, win_off, k, bitmap, word_rank, M);
   }
 }
 
-// ------------------------------------------------------------ bucketed transpose
-// Genes [g0, g1) of block b: a contiguous share of all genes.
-__device__ __forceinline__ void block_gene_range(uint32_t n_genes, uint32_t* g0, uint32_t* g1) {
-  const uint64_t per = ((uint64_t)n_genes + gridDim.x - 1) / gridDim.x;
-  *g0 = (uint32_t)(per * blockIdx.x < n_genes ? per * blockIdx.x : n_genes);
-  *g1 = (uint32_t)(per * (blockIdx.x + 1) < n_genes ? per * (blockIdx.x + 1) : n_genes);
-}
-
-__global__ void __launch_bounds__(kBucketThreads)
-    k_bucket_count(const uint32_t* __restrict__ win_off, const uint32_t* __restrict__ mv_n,
-                   const uint32_t* __restrict__ mv_id, uint32_t n_genes, uint32_t shift, uint32_t n_buckets,
-                   uint32_t* __restrict__ bucket_count) {
-  extern __shared__ uint32_t hist[];
-  for (uint32_t b = threadIdx.x; b < n_buckets; b += blockDim.x) hist[b] = 0;
-  __syncthreads();
-  uint32_t g0, g1;
-  block_gene_range(n_genes, &g0, &g1);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-  for (uint32_t g = g0 + warp; g < g1; g += n_warps) {
-    const uint32_t off = win_off[g], n = mv_n[g];
-    for (uint32_t e = lane; e < n; e += 32) atomicAdd(&hist[mv_id[off + e] >> shift], 1u);
-  }
-  __syncthreads();
-  for (uint32_t b = threadIdx.x; b < n_buckets; b += blockDim.x)
-    if (hist[b]) atomicAdd(&bucket_count[b], hist[b]);
-}
-
-__global__ void __launch_bounds__(kBucketThreads)
-    k_bucket_scatter(const uint32_t* __restrict__ win_off, const uint32_t* __restrict__ mv_n,
-                     const uint32_t* __restrict__ mv_id, const uint16_t* __restrict__ mv_cnt, uint32_t n_genes,
-                     uint32_t shift, uint32_t n_buckets, uint32_t* __restrict__ bucket_cursor, uint32_t cnt_bits,
-                     uint32_t cnt_cap, unsigned long long* __restrict__ recs) {
-  extern __shared__ uint32_t hist[];  // n_buckets counts, then n_buckets bases
-  uint32_t* base = hist + n_buckets;
-  for (uint32_t b = threadIdx.x; b < n_buckets; b += blockDim.x) hist[b] = 0;
-  __syncthreads();
-  uint32_t g0, g1;
-  block_gene_range(n_genes, &g0, &g1);
-  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
-  for (uint32_t g = g0 + warp; g < g1; g += n_warps) {
-    const uint32_t off = win_off[g], n = mv_n[g];
-    for (uint32_t e = lane; e < n; e += 32) atomicAdd(&hist[mv_id[off + e] >> shift], 1u);
-  }
-  __syncthreads();
-  for (uint32_t b = threadIdx.x; b < n_buckets; b += blockDim.x)
-    base[b] = hist[b] ? atomicAdd(&bucket_cursor[b], hist[b]) : 0u;
-  __syncthreads();
-  for (uint32_t g = g0 + warp; g < g1; g += n_warps) {
-    const uint32_t off = win_off[g], n = mv_n[g];
-    for (uint32_t e = lane; e < n; e += 32) {
-      const uint32_t id = mv_id[off + e];
-      const uint32_t c = mv_cnt[off + e];
-      const uint32_t pos = atomicAdd(&base[id >> shift], 1u);
-      recs[pos] = ((unsigned long long)id << 32) | (g << cnt_bits) | (c < cnt_cap ? c : cnt_cap);
-    }
-  }
-}
-
-// One block per bucket: counting sort of the bucket's records by id, then
-// each id's postings sorted by gene (gene ids are unique within a list).
-__global__ void __launch_bounds__(kFineThreads)
-    k_bucket_fine(const uint32_t* __restrict__ bucket_start, uint32_t n_buckets, uint32_t shift, uint64_t n_ids_total,
-                  unsigned long long* __restrict__ recs, uint32_t* __restrict__ post_ptr, uint32_t* __restrict__ post,
-                  uint32_t* __restrict__ max_posting) {
-  extern __shared__ uint32_t cnt[];  // 2^shift counters, then the long-list queue
-  __shared__ uint32_t warp_tmp[kFineThreads / 32 + 1];
-  __shared__ uint32_t n_long;
-  const uint32_t ids_per = 1u << shift;
-  uint32_t* longq = cnt + ids_per;
-  const uint32_t items = (ids_per + kFineThreads - 1) / kFineThreads;
-  uint32_t my_max = 0;
-  for (uint32_t bk = blockIdx.x; bk < n_buckets; bk += gridDim.x) {
-    const uint64_t id0 = (uint64_t)bk << shift;
-    const uint32_t n_ids = (uint32_t)(n_ids_total - id0 < ids_per ? n_ids_total - id0 : ids_per);
-    const uint32_t r0 = bucket_start[bk], R = bucket_start[bk + 1] - r0;
-    for (uint32_t i = threadIdx.x; i < ids_per; i += kFineThreads) cnt[i] = 0;
-    if (threadIdx.x == 0) n_long = 0;
-    __syncthreads();
-    for (uint32_t r = threadIdx.x; r < R; r += kFineThreads)
-      atomicAdd(&cnt[(uint32_t)(recs[r0 + r] >> 32) - (uint32_t)id0], 1u);
-    __syncthreads();
-    // exclusive scan of the per-id counts (each thread owns `items` consecutive ids)
-    uint32_t sum = 0;
-    for (uint32_t t = 0; t < items; ++t) {
-      const uint32_t i = threadIdx.x * items + t;
-      if (i < ids_per) sum += cnt[i];
-    }
-    uint32_t tot;
-    uint32_t run = block_exclusive_scan(sum, warp_tmp, &tot);
-    for (uint32_t t = 0; t < items; ++t) {
-      const uint32_t i = threadIdx.x * items + t;
-      if (i < ids_per) {
-        const uint32_t c = cnt[i];
-        cnt[i] = run;  // becomes the placement cursor
-        if (i < n_ids) post_ptr[id0 + i] = r0 + run;
-        my_max = max(my_max, c);
-        run += c;
-      }
-    }
-    __syncthreads();
-    for (uint32_t r = threadIdx.x; r < R; r += kFineThreads) {
-      const unsigned long long v = recs[r0 + r];
-      const uint32_t pos = atomicAdd(&cnt[(uint32_t)(v >> 32) - (uint32_t)id0], 1u);
-      post[r0 + pos] = (uint32_t)v;
-    }
-    __syncthreads();
-    // cnt[i] now holds the end of list i; list i starts at cnt[i-1] (or 0).
-    for (uint32_t i = threadIdx.x; i < n_ids; i += kFineThreads) {
-      const uint32_t lo = i ? cnt[i - 1] : 0u, hi = cnt[i], len = hi - lo;
-      if (len <= 1) continue;
-      if (len > 24) {
-        longq[atomicAdd(&n_long, 1u)] = i;
-        continue;
-      }
-      uint32_t* L = post + r0 + lo;  // insertion sort in place (L1-resident)
-      for (uint32_t x = 1; x < len; ++x) {
-        const uint32_t v = L[x];
-        uint32_t y = x;
-        while (y > 0 && L[y - 1] > v) {
-          L[y] = L[y - 1];
-          --y;
-        }
-        L[y] = v;
-      }
-    }
-    __syncthreads();
-    // longer lists: one warp each, rank placement through the dead record area
-    const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
-    for (uint32_t q = warp; q < n_long; q += kFineThreads / 32) {
-      const uint32_t i = longq[q];
-      const uint32_t lo = i ? cnt[i - 1] : 0u, len = cnt[i] - lo;
-      uint32_t* L = post + r0 + lo;
-      uint32_t* tmp = (uint32_t*)(recs + r0) + lo;  // disjoint per list
-      for (uint32_t x = lane; x < len; x += 32) {
-        const uint32_t v = L[x];
-        uint32_t rank = 0;
-        for (uint32_t y = 0; y < len; ++y) rank += (L[y] < v) ? 1u : 0u;
-        tmp[rank] = v;
-      }
-      __syncwarp();
-      for (uint32_t x = lane; x < len; x += 32) L[x] = tmp[x];
-      __syncwarp();
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) my_max = max(my_max, __shfl_xor_sync(0xffffffffu, my_max, o));
-  if ((threadIdx.x & 31u) == 0) atomicMax(max_posting, my_max);
-}
-
-// Every multiplicity-vector entry gets its posting range [mv_post, +mv_plen).
+// Every multiplicity-vector entry gets its posting range [mv_post, +mv_plen);
+// the longest list length goes to *max_posting.
 __global__ void __launch_bounds__(256)
     k_mv_post(const uint32_t* __restrict__ win_off, const uint32_t* __restrict__ mv_n,
               const uint32_t* __restrict__ mv_id, uint32_t n_genes, const uint32_t* __restrict__ post_ptr,
-              uint32_t* __restrict__ mv_post, uint32_t* __restrict__ mv_plen) {
+              uint32_t* __restrict__ mv_post, uint32_t* __restrict__ mv_plen, uint32_t* __restrict__ max_posting) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  uint32_t m = 0;
   for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_genes; g += warps) {
     const uint32_t off = win_off[g], n = mv_n[g];
     for (uint32_t e = lane; e < n; e += 32) {
       const uint32_t id = mv_id[off + e];
-      const uint32_t lo = post_ptr[id];
+      const uint32_t lo = post_ptr[id], len = post_ptr[id + 1] - lo;
       mv_post[off + e] = lo;
-      mv_plen[off + e] = post_ptr[id + 1] - lo;
+      mv_plen[off + e] = len;
+      m = max(m, len);
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if (lane == 0 && m) atomicMax(max_posting, m);
 }
 
 // ------------------------------------------------------------ query order
@@ -382,29 +262,48 @@ __global__ void k_select_codes(const unsigned long long* __restrict__ bitmap, co
   }
 }
 
+// Export of the multiplicity vectors in ascending code order (inspection
+// hook): each gene's (code << 16 | count) keys go to a power-of-two padded
+// scratch region, one block sorts each region, then the keys are unpacked.
+__global__ void k_export_mv_keys(ProfilesView P, const unsigned long long* __restrict__ pad_off,
+                                 const unsigned long long* __restrict__ code_of_id, unsigned long long* __restrict__ pad) {
+  for (uint32_t g = blockIdx.x; g < P.n_genes; g += gridDim.x) {
+    const uint32_t off = P.win_off[g], n = P.mv_n[g];
+    const unsigned long long o = pad_off[g], n2 = pad_off[g + 1] - o;
+    for (uint32_t e = threadIdx.x; e < n2; e += blockDim.x)
+      pad[o + e] = e < n ? (code_of_id[P.mv_id[off + e]] << 16) | P.mv_cnt[off + e] : ~0ull;
+  }
+}
+
+__global__ void __launch_bounds__(512) k_export_mv_sort(uint32_t n_genes, const unsigned long long* __restrict__ pad_off,
+                                                        unsigned long long* pad) {
+  for (uint32_t g = blockIdx.x; g < n_genes; g += gridDim.x) {
+    const unsigned long long o = pad_off[g];
+    const uint32_t n2 = (uint32_t)(pad_off[g + 1] - o);
+    if (n2 > 1) block_bitonic_sort(pad + o, n2);
+    __syncthreads();
+  }
+}
+
 __global__ void k_export_mv(ProfilesView P, const unsigned long long* __restrict__ mv_ptr,
-                            const unsigned long long* __restrict__ code_of_id, unsigned long long* __restrict__ codes,
-                            uint32_t* __restrict__ counts) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < P.n_genes; g += warps) {
-    const uint32_t off = P.win_off[g];
-    const unsigned long long dst = mv_ptr[g];
-    for (uint32_t e = lane; e < P.mv_n[g]; e += 32) {
-      if (codes) codes[dst + e] = code_of_id[P.mv_id[off + e]];
-      if (counts) counts[dst + e] = P.mv_cnt[off + e];
+                            const unsigned long long* __restrict__ pad_off, const unsigned long long* __restrict__ pad,
+                            unsigned long long* __restrict__ codes, uint32_t* __restrict__ counts) {
+  for (uint32_t g = blockIdx.x; g < P.n_genes; g += gridDim.x) {
+    const unsigned long long o = pad_off[g], dst = mv_ptr[g];
+    for (uint32_t e = threadIdx.x; e < P.mv_n[g]; e += blockDim.x) {
+      const unsigned long long v = pad[o + e];
+      if (codes) codes[dst + e] = v >> 16;
+      if (counts) counts[dst + e] = (uint32_t)(v & 0xFFFFu);
     }
   }
 }
 
-// Exact count of k-mer id in gene g (binary search in its multiplicity vector).
+// Exact count of k-mer id in gene g (its multiplicity vector is unordered).
 __device__ __forceinline__ uint32_t mv_count_of(const ProfilesView& P, uint32_t g, uint32_t id) {
-  uint32_t lo = P.win_off[g], end = lo + P.mv_n[g], hi = end;
-  while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
-    if (P.mv_id[mid] < id) lo = mid + 1; else hi = mid;
-  }
-  return (lo < end && P.mv_id[lo] == id) ? P.mv_cnt[lo] : 0u;
+  const uint32_t off = P.win_off[g], n = P.mv_n[g];
+  for (uint32_t e = 0; e < n; ++e)
+    if (P.mv_id[off + e] == id) return P.mv_cnt[off + e];
+  return 0u;
 }
 
 __global__ void k_export_index(ProfilesView P, int32_t* __restrict__ genes, uint32_t* __restrict__ counts) {
@@ -454,68 +353,40 @@ cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene
 
 cudaError_t run_mv_build(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, const uint32_t* win_off,
                          uint32_t n_genes, int k, const unsigned long long* bitmap, const uint32_t* word_rank,
-                         uint32_t* mv_id, uint16_t* mv_cnt, uint32_t* mv_n, uint32_t* minhash,
-                         const uint32_t* long_genes, uint32_t n_long, uint32_t* long_scratch,
-                         const uint32_t* long_scratch_off, uint32_t max_smem_sort, cudaStream_t s) {
-  const size_t smem = (size_t)max_smem_sort * sizeof(uint32_t);
-  cudaError_t ea = cudaFuncSetAttribute(k_mv_build_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                         const MvOut& M, const uint32_t* mid_genes, uint32_t n_mid, const uint32_t* long_genes,
+                         uint32_t n_long, unsigned long long* long_scratch, const unsigned long long* long_scratch_off,
+                         cudaStream_t s) {
+  const size_t smem1 = (size_t)kMvSmallCap * 8, smem2 = (size_t)kMvMidCap * 8;
+  cudaError_t ea = cudaFuncSetAttribute(k_mv_build_smem<kMvThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem1);
   if (ea != cudaSuccess) return ea;
-  const unsigned grid = grid_for(n_genes, 1, 152u * 64u);
+  ea = cudaFuncSetAttribute(k_mv_build_smem<kMvLongThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+  if (ea != cudaSuccess) return ea;
   PD_LAUNCH(L, "mv_build",
-            k_mv_build_smem<<<grid, kMvThreads, smem, s>>>(res, gene_ptr, win_off, n_genes, k, bitmap, word_rank,
-                                                            mv_id, mv_cnt, mv_n, minhash, max_smem_sort));
+            k_mv_build_smem<kMvThreads><<<grid_for(n_genes, 1, 152u * 64u), kMvThreads, smem1, s>>>(
+                res, gene_ptr, win_off, n_genes, k, bitmap, word_rank, M, kMvSmallCap, nullptr, 0u));
+  if (n_mid) {
+    PD_LAUNCH(L, "mv_build_mid",
+              k_mv_build_smem<kMvLongThreads><<<grid_for(n_mid, 1, 152u), kMvLongThreads, smem2, s>>>(
+                  res, gene_ptr, win_off, n_genes, k, bitmap, word_rank, M, kMvMidCap, mid_genes, n_mid));
+  }
   if (n_long) {
     PD_LAUNCH(L, "mv_build_long",
               k_mv_build_long<<<grid_for(n_long, 1, 152u), kMvLongThreads, 0, s>>>(
-                  res, gene_ptr, win_off, k, bitmap, word_rank, mv_id, mv_cnt, mv_n, minhash, long_genes, n_long,
-                  long_scratch, long_scratch_off));
+                  res, gene_ptr, win_off, k, bitmap, word_rank, M, long_genes, n_long, long_scratch,
+                  long_scratch_off));
   }
   return cudaSuccess;
 }
 
-cudaError_t run_bucket_count(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
-                             uint32_t n_genes, uint32_t shift, uint32_t n_buckets, uint32_t* bucket_count,
-                             cudaStream_t s) {
-  const size_t smem = (size_t)n_buckets * sizeof(uint32_t);
-  cudaError_t ea = cudaFuncSetAttribute(k_bucket_count, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (ea != cudaSuccess) return ea;
-  PD_LAUNCH(L, "bucket_count",
-            k_bucket_count<<<grid_for(n_genes, 64, 152u * 3u), kBucketThreads, smem, s>>>(
-                win_off, mv_n, mv_id, n_genes, shift, n_buckets, bucket_count));
-  return cudaSuccess;
-}
-
-cudaError_t run_bucket_scatter(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
-                               const uint16_t* mv_cnt, uint32_t n_genes, uint32_t shift, uint32_t n_buckets,
-                               uint32_t* bucket_cursor, uint32_t cnt_bits, uint32_t cnt_cap,
-                               unsigned long long* recs, cudaStream_t s) {
-  const size_t smem = 2 * (size_t)n_buckets * sizeof(uint32_t);
-  cudaError_t ea = cudaFuncSetAttribute(k_bucket_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (ea != cudaSuccess) return ea;
-  PD_LAUNCH(L, "bucket_scatter",
-            k_bucket_scatter<<<grid_for(n_genes, 64, 152u * 3u), kBucketThreads, smem, s>>>(
-                win_off, mv_n, mv_id, mv_cnt, n_genes, shift, n_buckets, bucket_cursor, cnt_bits, cnt_cap, recs));
-  return cudaSuccess;
-}
-
-cudaError_t run_bucket_fine(Launcher* L, const uint32_t* bucket_start, uint32_t n_buckets, uint32_t shift,
-                            uint64_t n_ids, unsigned long long* recs, uint32_t* post_ptr, uint32_t* post,
-                            uint32_t* max_posting, cudaStream_t s) {
-  const size_t smem = 2 * ((size_t)1 << shift) * sizeof(uint32_t);
-  cudaError_t ea = cudaFuncSetAttribute(k_bucket_fine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (ea != cudaSuccess) return ea;
-  PD_LAUNCH(L, "bucket_fine",
-            k_bucket_fine<<<grid_for(n_buckets, 1, 152u * 4u), kFineThreads, smem, s>>>(
-                bucket_start, n_buckets, shift, n_ids, recs, post_ptr, post, max_posting));
-  return cudaSuccess;
-}
+uint32_t mv_build_table_cap(uint32_t La) { return mv_table_cap(La); }
 
 cudaError_t run_mv_post(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
                         uint32_t n_genes, const uint32_t* post_ptr, uint32_t* mv_post, uint32_t* mv_plen,
-                        cudaStream_t s) {
+                        uint32_t* max_posting, cudaStream_t s) {
   PD_LAUNCH(L, "mv_post",
             k_mv_post<<<grid_for((uint64_t)n_genes * 32, 256, 152u * 16u), 256, 0, s>>>(
-                win_off, mv_n, mv_id, n_genes, post_ptr, mv_post, mv_plen));
+                win_off, mv_n, mv_id, n_genes, post_ptr, mv_post, mv_plen, max_posting));
   return cudaSuccess;
 }
 
@@ -549,11 +420,13 @@ cudaError_t run_select_codes(Launcher* L, const unsigned long long* bitmap, cons
 }
 
 cudaError_t run_export_mv(Launcher* L, const ProfilesView& P, const unsigned long long* mv_ptr,
+                          const unsigned long long* pad_off, unsigned long long* pad,
                           const unsigned long long* code_of_id, unsigned long long* codes, uint32_t* counts,
                           cudaStream_t s) {
-  PD_LAUNCH(L, "export_mv",
-            k_export_mv<<<grid_for((uint64_t)P.n_genes * 32, 256, 152u * 16u), 256, 0, s>>>(P, mv_ptr, code_of_id,
-                                                                                             codes, counts));
+  const unsigned grid = grid_for(P.n_genes, 1, 152u * 16u);
+  PD_LAUNCH(L, "export_mv_keys", k_export_mv_keys<<<grid, 256, 0, s>>>(P, pad_off, code_of_id, pad));
+  PD_LAUNCH(L, "export_mv_sort", k_export_mv_sort<<<grid, 512, 0, s>>>(P.n_genes, pad_off, pad));
+  PD_LAUNCH(L, "export_mv", k_export_mv<<<grid, 256, 0, s>>>(P, mv_ptr, pad_off, pad, codes, counts));
   return cudaSuccess;
 }
 

@@ -42,10 +42,6 @@ struct Scalars {
   uint32_t warp_tmp[33];
 };
 
-__device__ __forceinline__ uint32_t hash_gene(uint32_t b) {
-  uint32_t h = b * 0x9E3779B1u;
-  return h ^ (h >> 15);
-}
 
 // Probes allowed before a query counts as overflowing its table.  Long chains
 // mean a nearly full table; the query then moves to a larger tier, so the
@@ -53,42 +49,52 @@ __device__ __forceinline__ uint32_t hash_gene(uint32_t b) {
 constexpr uint32_t kMaxProbe = 64;
 
 // Two table layouts share the code below.
-//   packed (tier 1): one word per slot, (b << cnt_bits) | s.  Valid while
-//     s < 2^cnt_bits - 1, which holds for every query with La < 2^cnt_bits - 1
-//     since s <= La; other queries go to tier 2.  The empty word 0xFFFFFFFF
-//     can never be a real slot because s stays below the all-ones count.
+//   packed (tier 1): one word per slot, (b << cnt_bits) | s.  A posting is
+//     packed the same way, so the walk keys the table with the posting's own
+//     high bits ("bkey") and never unpacks the gene id.  Valid while s stays
+//     below the all-ones count, which holds for every query with
+//     La < 2^cnt_bits - 1 (s <= La); other queries go to tier 2.  The gene
+//     field never holds all ones (that id is reserved), so the empty word
+//     0xFFFFFFFF matches no key.
 //   split (tiers 2 and 3): keys[] = b, vals[] = s.
+// Slots are found by multiplicative hashing (top bits of key * odd constant)
+// and linear probing.
 template <bool kPacked>
 struct Acc {
   uint32_t* keys;  // packed: slot words
   uint32_t* vals;  // split only
   uint32_t cnt_bits;
+  uint32_t hash_shift;  // 32 - log2(cap)
 
-  __device__ __forceinline__ bool add(uint32_t mask, uint32_t b, uint32_t m) const {
-    uint32_t h = hash_gene(b) & mask;
+  __device__ __forceinline__ uint32_t home(uint32_t key) const { return (key * 0x9E3779B1u) >> hash_shift; }
+
+  // key: bkey (packed) or b (split).  Returns false after kMaxProbe probes.
+  __device__ __forceinline__ bool add(uint32_t mask, uint32_t key, uint32_t m) const {
+    uint32_t h = home(key);
+    const uint32_t hi = ~((1u << cnt_bits) - 1u);
     for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
       const uint32_t k = *((volatile uint32_t*)&keys[h]);
       if (kPacked) {
-        if (k != kEmpty && (k >> cnt_bits) == b) {
+        if ((k & hi) == key) {
           atomicAdd(&keys[h], m);
           return true;
         }
         if (k == kEmpty) {
-          const uint32_t prev = atomicCAS(&keys[h], kEmpty, (b << cnt_bits) | m);
+          const uint32_t prev = atomicCAS(&keys[h], kEmpty, key | m);
           if (prev == kEmpty) return true;
-          if ((prev >> cnt_bits) == b) {
+          if ((prev & hi) == key) {
             atomicAdd(&keys[h], m);
             return true;
           }
         }
       } else {
-        if (k == b) {
+        if (k == key) {
           atomicAdd(&vals[h], m);
           return true;
         }
         if (k == kEmpty) {
-          const uint32_t prev = atomicCAS(&keys[h], kEmpty, b);
-          if (prev == kEmpty || prev == b) {
+          const uint32_t prev = atomicCAS(&keys[h], kEmpty, key);
+          if (prev == kEmpty || prev == key) {
             atomicAdd(&vals[h], m);
             return true;
           }
@@ -173,7 +179,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
                                               const Table<TIdx>& tb, uint32_t* c_post, uint32_t* c_off,
                                               uint16_t* c_cnt, unsigned long long* best, Scalars* sh) {
   constexpr uint32_t kChunk = Chunk<kThreads>::kSize, kItems = Chunk<kThreads>::kItems;
-  const Acc<kPacked> acc{tb.keys, tb.vals, P.cnt_bits};
+  const Acc<kPacked> acc{tb.keys, tb.vals, P.cnt_bits, 32u - (31u - (uint32_t)__clz(tb.cap))};
   unsigned long long* out = tb.out;
   const uint32_t mask = tb.cap - 1u;
   // ---- query gene, its output row and its targets
@@ -274,15 +280,17 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
             nb = j + 1;
           }
         }
+        // Own-genome postings are accumulated too and dropped when the
+        // Best Hits are chosen (a few slots per query), which keeps this loop
+        // free of per-posting range tests.
 #pragma unroll
         for (uint32_t j = 0; j < 4; ++j) {
           if (j < nb) {
             const uint32_t p = pv[j];
-            const uint32_t b = p >> P.cnt_bits;
-            if (Q.all_pairs && b >= own0 && b < own1) continue;
             uint32_t cb = p & cnt_mask;
-            if (cb == P.cnt_cap && cav[j] > cb) cb = mv_count_of(P, b, P.mv_id[m0 + c0 + ev[j]]);
-            if (!acc.add(mask, b, min(cav[j], cb))) sh->overflow = 1;
+            if (cb == P.cnt_cap && cav[j] > cb) cb = mv_count_of(P, p >> P.cnt_bits, P.mv_id[m0 + c0 + ev[j]]);
+            const uint32_t key = kPacked ? (p & ~cnt_mask) : (p >> P.cnt_bits);
+            if (!acc.add(mask, key, min(cav[j], cb))) sh->overflow = 1;
           }
         }
       }
@@ -321,6 +329,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
       for (uint32_t u = tid; u < n_occ; u += kThreads) {
         uint32_t b, s;
         acc.get(tb.used[u], &b, &s);
+        if (Q.all_pairs && b >= own0 && b < own1) continue;  // same genome: not a target
         const uint32_t gi = P.ginfo[b];
         best_update(&best[Q.all_pairs ? (gi >> 16) : 0u], s, La_a + (gi & 0xFFFFu) - s);
       }
@@ -331,7 +340,8 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
         acc.get(h, &b, &s);
         const uint32_t gi = P.ginfo[b];
         const unsigned long long bv = best[Q.all_pairs ? (gi >> 16) : 0u];
-        if (ratio_equal(s, La_a + (gi & 0xFFFFu) - s, (uint32_t)(bv >> 32), (uint32_t)bv)) {
+        if (!(Q.all_pairs && b >= own0 && b < own1) &&
+            ratio_equal(s, La_a + (gi & 0xFFFFu) - s, (uint32_t)(bv >> 32), (uint32_t)bv)) {
           const uint32_t slot = atomicAdd(&sh->n_out, 1u);
           if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | s;
         }

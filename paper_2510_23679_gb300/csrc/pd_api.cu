@@ -379,9 +379,10 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
     if (hgn[i + 1] < hgn[i]) return fail(c, PD_ERR_ARG, "genome_ptr is decreasing at " + std::to_string(i));
   std::vector<uint32_t> La(n_genes), win_off(n_genes + 1);
   uint64_t W = 0;
-  std::vector<uint32_t> long_genes, long_off;
+  std::vector<uint32_t> long_genes;
+  std::vector<unsigned long long> long_off;
   uint64_t long_total = 0;
-  const uint32_t kMaxSmemSort = 4096;
+  std::vector<uint32_t> mid_genes;
   for (uint32_t g = 0; g < n_genes; ++g) {
     const int64_t len = hg[g + 1] - hg[g];
     if (len < 0) return fail(c, PD_ERR_ARG, "gene_ptr is decreasing at " + std::to_string(g));
@@ -393,10 +394,13 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
     win_off[g] = (uint32_t)W;
     W += w;
     if (W > 0xFFFFFFF0ull) return fail(c, PD_ERR_ARG, "more than 2^32 k-mer windows in the dataset");
-    if (pdg::next_pow2((uint32_t)w) > kMaxSmemSort) {
+    const uint32_t cap = pdg::mv_build_table_cap((uint32_t)w);
+    if (cap > 16384) {  // table beyond shared memory: global scratch
       long_genes.push_back(g);
-      long_off.push_back((uint32_t)long_total);
-      long_total += pdg::next_pow2((uint32_t)w);
+      long_off.push_back(long_total);
+      long_total += cap;
+    } else if (cap > 2048) {  // table beyond the small shared-memory build
+      mid_genes.push_back(g);
     }
   }
   win_off[n_genes] = (uint32_t)W;
@@ -411,7 +415,7 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   pdg::Launcher* L = &c->L;
 
   // ---- inputs on the device
-  Buf d_res, d_gene_ptr, d_long, d_long_off, d_long_scratch, tmp, d_counts, minhash;
+  Buf d_res, d_gene_ptr, d_mid, d_long, d_long_off, d_long_scratch, tmp, d_counts, minhash;
   const uint8_t* res_dev = residues;
   const int64_t* gp_devp = gene_ptr;
   if (n_res > 0 && !is_device_ptr(residues)) {
@@ -458,66 +462,66 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   if (st != PD_OK) return st;
   const uint64_t D = h_counts[0];
 
-  // ---- multiplicity vectors
+  // ---- multiplicity vectors (and one index record per entry)
+  // gene field wide enough to keep the all-ones id unused (see the packed
+  // accumulator slots of k_summin.cu)
+  const uint32_t gene_bits = bits_for(n_genes);
+  const uint32_t cnt_bits = 32 - gene_bits;
+  const uint32_t cnt_cap = std::min<uint32_t>((1u << cnt_bits) - 1u, 65535u);
+  Buf mvrec;
   ALLOC(P->mv_id, sizeof(uint32_t) * W1);
   ALLOC(P->mv_cnt, sizeof(uint16_t) * W1);
   ALLOC(P->mv_n, sizeof(uint32_t) * G1);
   ALLOC(minhash, sizeof(uint32_t) * G1);
+  ALLOC(mvrec, sizeof(unsigned long long) * W1);
+  if (!mid_genes.empty()) {
+    ALLOC(d_mid, sizeof(uint32_t) * mid_genes.size());
+    CK(cudaMemcpyAsync(d_mid.p, mid_genes.data(), sizeof(uint32_t) * mid_genes.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+  }
   if (!long_genes.empty()) {
     ALLOC(d_long, sizeof(uint32_t) * long_genes.size());
-    ALLOC(d_long_off, sizeof(uint32_t) * long_off.size());
-    ALLOC(d_long_scratch, sizeof(uint32_t) * long_total);
+    ALLOC(d_long_off, sizeof(unsigned long long) * long_off.size());
+    ALLOC(d_long_scratch, sizeof(unsigned long long) * long_total);
     CK(cudaMemcpyAsync(d_long.p, long_genes.data(), sizeof(uint32_t) * long_genes.size(), cudaMemcpyHostToDevice,
                        c->stream));
-    CK(cudaMemcpyAsync(d_long_off.p, long_off.data(), sizeof(uint32_t) * long_off.size(), cudaMemcpyHostToDevice,
-                       c->stream));
+    CK(cudaMemcpyAsync(d_long_off.p, long_off.data(), sizeof(unsigned long long) * long_off.size(),
+                       cudaMemcpyHostToDevice, c->stream));
   }
+  pdg::MvOut M;
+  M.mv_id = P->mv_id.as<uint32_t>();
+  M.mv_cnt = P->mv_cnt.as<uint16_t>();
+  M.mv_n = P->mv_n.as<uint32_t>();
+  M.rec = mvrec.as<unsigned long long>();
+  M.minhash = minhash.as<uint32_t>();
+  M.cnt_bits = cnt_bits;
+  M.cnt_cap = cnt_cap;
+  M.err = c->d_err;
   if (n_genes)
     CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
-                         P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), P->mv_id.as<uint32_t>(),
-                         P->mv_cnt.as<uint16_t>(), P->mv_n.as<uint32_t>(), minhash.as<uint32_t>(),
-                         d_long.as<uint32_t>(), (uint32_t)long_genes.size(), d_long_scratch.as<uint32_t>(),
-                         d_long_off.as<uint32_t>(), kMaxSmemSort, c->stream));
+                         P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), M,
+                         d_mid.as<uint32_t>(), (uint32_t)mid_genes.size(), d_long.as<uint32_t>(), (uint32_t)long_genes.size(), d_long_scratch.as<unsigned long long>(),
+                         d_long_off.as<unsigned long long>(), c->stream));
 
-  // ---- inverted index: bucketed transpose of the multiplicity vectors
-  const uint32_t gene_bits = bits_for(n_genes > 0 ? n_genes - 1 : 0);
-  const uint32_t cnt_bits = 32 - gene_bits;
-  const uint32_t cnt_cap = std::min<uint32_t>((1u << cnt_bits) - 1u, 65535u);
-  uint32_t shift = ceil_log2_u64(std::max<uint64_t>(D, 1));
-  shift = shift > 13 ? shift - 13 : 0;
-  if (shift > 14) shift = 14;
-  const uint64_t NB64 = (D + ((uint64_t)1 << shift) - 1) >> shift;
-  if (NB64 > 24576) return fail(c, PD_ERR_ARG, "more than 402M distinct k-mers in one dataset");
-  const uint32_t NB = (uint32_t)std::max<uint64_t>(NB64, 1);
-  Buf bcount, bstart, bcursor, recs;
-  ALLOC(bcount, sizeof(uint32_t) * NB);
-  ALLOC(bstart, sizeof(uint32_t) * (NB + 1));
-  ALLOC(bcursor, sizeof(uint32_t) * NB);
+  // ---- inverted index: stable radix sort of the index records by k-mer id
+  // (records arrive in gene order, so every posting list ends up gene-sorted)
+  Buf recs, rcounts, rtmp;
   ALLOC(recs, sizeof(unsigned long long) * W1);
+  ALLOC(rcounts, sizeof(uint32_t) * pdg::radix_counts_words(W));
+  ALLOC(rtmp, pdg::scan_temp_bytes(pdg::radix_counts_words(W)) + 64);
   ALLOC(P->post_ptr, sizeof(uint32_t) * (D + 1));
   ALLOC(P->post, sizeof(uint32_t) * W1);
-  CK(cudaMemsetAsync(bcount.p, 0, sizeof(uint32_t) * NB, c->stream));
-  if (n_genes && D) {
-    CK(pdg::run_bucket_count(L, P->win_off.as<uint32_t>(), P->mv_n.as<uint32_t>(), P->mv_id.as<uint32_t>(), n_genes,
-                             shift, NB, bcount.as<uint32_t>(), c->stream));
-  }
-  CK(pdg::scan_u32(L, bcount.as<uint32_t>(), NB, bstart.as<uint32_t>(), tmp.p, c->stream));
-  CK(cudaMemcpyAsync(bcursor.p, bstart.p, sizeof(uint32_t) * NB, cudaMemcpyDeviceToDevice, c->stream));
-  if (n_genes && D) {
-    CK(pdg::run_bucket_scatter(L, P->win_off.as<uint32_t>(), P->mv_n.as<uint32_t>(), P->mv_id.as<uint32_t>(),
-                               P->mv_cnt.as<uint16_t>(), n_genes, shift, NB, bcursor.as<uint32_t>(), cnt_bits,
-                               cnt_cap, recs.as<unsigned long long>(), c->stream));
-    CK(pdg::run_bucket_fine(L, bstart.as<uint32_t>(), NB, shift, D, recs.as<unsigned long long>(),
-                            P->post_ptr.as<uint32_t>(), P->post.as<uint32_t>(), d_counts.as<uint32_t>() + 1,
-                            c->stream));
-  }
-  CK(cudaMemcpyAsync(P->post_ptr.as<uint32_t>() + D, bstart.as<uint32_t>() + NB, sizeof(uint32_t),
-                     cudaMemcpyDeviceToDevice, c->stream));
+  CK(cudaMemsetAsync(P->post_ptr.p, 0, sizeof(uint32_t) * (D + 1), c->stream));
+  if (W && D)
+    CK(pdg::run_index_sort(L, mvrec.as<unsigned long long>(), recs.as<unsigned long long>(), W, bits_for((uint32_t)D),
+                           rcounts.as<uint32_t>(), rtmp.p, D, P->post.as<uint32_t>(), P->post_ptr.as<uint32_t>(),
+                           c->stream));
   ALLOC(P->mv_post, sizeof(uint32_t) * W1);
   ALLOC(P->mv_plen, sizeof(uint32_t) * W1);
   if (n_genes && D)
     CK(pdg::run_mv_post(L, P->win_off.as<uint32_t>(), P->mv_n.as<uint32_t>(), P->mv_id.as<uint32_t>(), n_genes,
-                        P->post_ptr.as<uint32_t>(), P->mv_post.as<uint32_t>(), P->mv_plen.as<uint32_t>(), c->stream));
+                        P->post_ptr.as<uint32_t>(), P->mv_post.as<uint32_t>(), P->mv_plen.as<uint32_t>(),
+                        d_counts.as<uint32_t>() + 1, c->stream));
 
   // ---- all-pairs query order: min-hash buckets
   Buf ocount;
@@ -529,7 +533,7 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
                       P->order.as<uint32_t>(), tmp.p, c->stream));
 
   uint32_t E32 = 0;
-  CK(cudaMemcpyAsync(&E32, bstart.as<uint32_t>() + NB, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&E32, P->post_ptr.as<uint32_t>() + D, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaMemcpyAsync(h_counts, d_counts.p, sizeof(h_counts), cudaMemcpyDeviceToHost, c->stream));
   st = check_dev_err(c);  // synchronizes; temporaries are released after this
   if (st != PD_OK) return st;
@@ -625,19 +629,30 @@ PD_API pd_status pd_profiles_copy_mv(pd_ctx* c, const pd_profiles* P, int64_t* m
     CK(cudaSetDevice(c->device));
     const pdg::ProfilesView& v = P->view;
     pdg::Launcher* L = &c->L;
-    Buf ptr, tmp, code_of_id, d_codes, d_counts;
+    Buf ptr, tmp, code_of_id, d_codes, d_counts, pad_off, pad;
     ALLOC(ptr, sizeof(unsigned long long) * (v.n_genes + 1));
     ALLOC(tmp, pdg::scan_temp_bytes(v.n_genes + 1) + 64);
     CK(pdg::scan_u32_to_u64(L, v.mv_n, v.n_genes, ptr.as<unsigned long long>(), tmp.p, c->stream));
-    if (codes) {
+    if ((codes || counts) && v.n_genes) {
+      // per-gene power-of-two scratch for the sort by code
+      std::vector<uint32_t> n(v.n_genes);
+      CK(cudaMemcpyAsync(n.data(), v.mv_n, sizeof(uint32_t) * v.n_genes, cudaMemcpyDeviceToHost, c->stream));
+      CK(cudaStreamSynchronize(c->stream));
+      std::vector<unsigned long long> off(v.n_genes + 1, 0);
+      for (uint32_t g = 0; g < v.n_genes; ++g) off[g + 1] = off[g] + (n[g] ? pdg::next_pow2(n[g]) : 0);
+      ALLOC(pad_off, sizeof(unsigned long long) * (v.n_genes + 1));
+      ALLOC(pad, sizeof(unsigned long long) * std::max<unsigned long long>(off[v.n_genes], 1));
+      CK(cudaMemcpyAsync(pad_off.p, off.data(), sizeof(unsigned long long) * (v.n_genes + 1), cudaMemcpyHostToDevice,
+                         c->stream));
       ALLOC(code_of_id, sizeof(unsigned long long) * std::max<uint64_t>(v.n_distinct, 1));
       CK(pdg::run_select_codes(L, v.bitmap, v.word_rank, v.n_words, code_of_id.as<unsigned long long>(), c->stream));
       ALLOC(d_codes, sizeof(unsigned long long) * std::max<uint64_t>(v.n_entries, 1));
-    }
-    if (counts) ALLOC(d_counts, sizeof(uint32_t) * std::max<uint64_t>(v.n_entries, 1));
-    if ((codes || counts) && v.n_genes)
-      CK(pdg::run_export_mv(L, v, ptr.as<unsigned long long>(), code_of_id.as<unsigned long long>(),
+      ALLOC(d_counts, sizeof(uint32_t) * std::max<uint64_t>(v.n_entries, 1));
+      CK(pdg::run_export_mv(L, v, ptr.as<unsigned long long>(), pad_off.as<unsigned long long>(),
+                            pad.as<unsigned long long>(), code_of_id.as<unsigned long long>(),
                             d_codes.as<unsigned long long>(), d_counts.as<uint32_t>(), c->stream));
+      CK(cudaStreamSynchronize(c->stream));  // host offsets must outlive the copy
+    }
     pd_status st;
     if ((st = copy_out(c, mv_ptr, ptr.p, sizeof(int64_t) * (v.n_genes + 1))) != PD_OK) return st;
     if ((st = copy_out(c, codes, d_codes.p, sizeof(uint64_t) * v.n_entries)) != PD_OK) return st;

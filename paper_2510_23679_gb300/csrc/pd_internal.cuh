@@ -6,9 +6,10 @@
 //   gene g (global id, 0..G-1) has La[g] = max(0, |g|-k+1) k-mer windows.
 //   win_off[G+1]   uint32  exclusive prefix of La: window range of each gene.
 //   mv_n[G]        uint32  distinct k-mers of the gene (E_g <= La[g]).
-//   mv_id[W]       uint32  dense k-mer id, gene g at win_off[g] .. +mv_n[g],
-//                          ascending (the multiplicity vector of Algorithm 1,
-//                          stored in the gene's window range: "padded CSR").
+//   mv_id[W]       uint32  dense k-mer id, gene g at win_off[g] .. +mv_n[g]
+//                          (the multiplicity vector of Algorithm 1, stored in
+//                          the gene's window range: "padded CSR"; the entries
+//                          of one gene are unordered).
 //   mv_cnt[W]      uint16  multiplicity of that k-mer in the gene.
 //   mv_post[W],    uint32  posting range of that k-mer (copied from post_ptr so
 //   mv_plen[W]             a query reads its list bounds with its own vector).
@@ -239,24 +240,36 @@ cudaError_t scan_u32_to_u64(Launcher* L, const uint32_t* in, uint64_t n, unsigne
 // profiles (k_profiles.cu)
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
                             unsigned long long* bitmap, DevErr* err, cudaStream_t s);
+// Outputs of the multiplicity-vector build.
+struct MvOut {
+  uint32_t* mv_id;
+  uint16_t* mv_cnt;
+  uint32_t* mv_n;
+  unsigned long long* rec;  // [W] (id << 32) | packed posting; all-ones in unused slots
+  uint32_t* minhash;
+  uint32_t cnt_bits, cnt_cap;
+  DevErr* err;
+};
+// Table slots used for a gene with La windows (genes above 16384 slots use
+// global scratch of that many 64-bit slots, listed in long_genes).
+uint32_t mv_build_table_cap(uint32_t La);
 cudaError_t run_mv_build(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, const uint32_t* win_off,
                          uint32_t n_genes, int k, const unsigned long long* bitmap, const uint32_t* word_rank,
-                         uint32_t* mv_id, uint16_t* mv_cnt, uint32_t* mv_n, uint32_t* minhash,
-                         const uint32_t* long_genes, uint32_t n_long, uint32_t* long_scratch,
-                         const uint32_t* long_scratch_off, uint32_t max_smem_sort, cudaStream_t s);
-cudaError_t run_bucket_count(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
-                             uint32_t n_genes, uint32_t shift, uint32_t n_buckets, uint32_t* bucket_count,
-                             cudaStream_t s);
-cudaError_t run_bucket_scatter(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
-                               const uint16_t* mv_cnt, uint32_t n_genes, uint32_t shift, uint32_t n_buckets,
-                               uint32_t* bucket_cursor, uint32_t cnt_bits, uint32_t cnt_cap,
-                               unsigned long long* recs, cudaStream_t s);
-cudaError_t run_bucket_fine(Launcher* L, const uint32_t* bucket_start, uint32_t n_buckets, uint32_t shift,
-                            uint64_t n_ids, unsigned long long* recs, uint32_t* post_ptr, uint32_t* post,
-                            uint32_t* max_posting, cudaStream_t s);
+                         const MvOut& M, const uint32_t* mid_genes, uint32_t n_mid, const uint32_t* long_genes,
+                         uint32_t n_long, unsigned long long* long_scratch, const unsigned long long* long_scratch_off,
+                         cudaStream_t s);
+// Stable LSD radix sort of the n index records in `a` (ping-pong with `b`) by
+// the low key_bits bits of their high word, then postings and id offsets:
+// post[0..E) and post_ptr[0..n_ids] (post_ptr[n_ids] = E).  `counts` holds
+// radix_counts_words(n) words; scan_tmp serves a scan of that many.
+size_t radix_counts_words(uint64_t n);
+cudaError_t run_index_sort(Launcher* L, unsigned long long* a, unsigned long long* b, uint64_t n, uint32_t key_bits,
+                           uint32_t* counts, void* scan_tmp, uint64_t n_ids, uint32_t* post, uint32_t* post_ptr,
+                           cudaStream_t s);
+// Posting range of every multiplicity-vector entry; also the longest list.
 cudaError_t run_mv_post(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
                         uint32_t n_genes, const uint32_t* post_ptr, uint32_t* mv_post, uint32_t* mv_plen,
-                        cudaStream_t s);
+                        uint32_t* max_posting, cudaStream_t s);
 // count must hold 2 * 2^(32-shift) + 1 words (counts, then their prefix sum).
 cudaError_t run_order(Launcher* L, const uint32_t* minhash, uint32_t n_genes, uint32_t shift, uint32_t* count,
                       uint32_t* order, void* scan_tmp, cudaStream_t s);
@@ -264,7 +277,9 @@ cudaError_t run_gene_info(Launcher* L, const int32_t* genome_ptr, uint32_t n_gen
                           uint16_t* gene_genome, uint32_t* ginfo, cudaStream_t s);
 cudaError_t run_select_codes(Launcher* L, const unsigned long long* bitmap, const uint32_t* word_rank,
                              uint64_t n_words, unsigned long long* code_of_id, cudaStream_t s);
+// pad_off: n_genes+1 offsets of power-of-two padded per-gene scratch regions in pad.
 cudaError_t run_export_mv(Launcher* L, const ProfilesView& P, const unsigned long long* mv_ptr,
+                          const unsigned long long* pad_off, unsigned long long* pad,
                           const unsigned long long* code_of_id, unsigned long long* codes, uint32_t* counts,
                           cudaStream_t s);
 cudaError_t run_export_index(Launcher* L, const ProfilesView& P, int32_t* genes, uint32_t* counts,
