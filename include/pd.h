@@ -219,6 +219,37 @@ void pd_bbh_free(pd_bbh_set* set);
 pd_status pd_summin_pairs(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32_t gj,
                           int32_t* a, int32_t* b, uint32_t* s, uint64_t* n);
 
+/* ---------------------------------------------------------------- no allocation */
+
+/* Scratch of pd_best_hits_noalloc: one fixed array in device memory, held by
+ * every GPU that loads this library until the process exits. */
+#define PD_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define PD_NOALLOC_MAX_ROWS 32768u     /* genes of the query genome gi */
+#define PD_NOALLOC_MAX_TARGETS 32768u  /* genes of the target genome gj */
+#define PD_NOALLOC_MAX_HITS (1u << 20) /* Best Hit entries of one call */
+
+/* The paper has no counterpart to this call: it exists for callers of this
+ * library that cannot allocate device memory while they run -- a process whose
+ * device memory is all owned by an external pool or memory manager, or a
+ * latency-critical loop where an allocation could block or fail.
+ *
+ * Same result as pd_best_hits(ctx, prof, gi, gj) followed by pd_hits_copy,
+ * written into caller-owned DEVICE buffers: row_ptr (|G_gi|+1 int64), cols
+ * and s (capacity entries each; int32 local column, uint32 sum-min).  The
+ * call allocates nothing: every temporary lives in a fixed array of
+ * PD_NOALLOC_SCRATCH_BYTES declared by the library, and no per-kernel timing
+ * events are recorded.  *n_hits (if not NULL) receives the number of entries.
+ * Limits: |G_gi| <= PD_NOALLOC_MAX_ROWS and |G_gj| <= PD_NOALLOC_MAX_TARGETS
+ * (else PD_ERR_ARG), at most PD_NOALLOC_MAX_HITS entries (else PD_ERR_BUDGET),
+ * and capacity >= the entry count (else PD_ERR_ARG, *n_hits set).
+ * The first call on a device looks up the array's device address (set-up,
+ * once per device); make that first call before any stream capture.  All
+ * calls share the one array, which keeps the last call's contents: calls that
+ * overlap on the GPU (other streams, other host threads, other contexts) race
+ * and must be serialized by the caller.  The call synchronizes ctx's stream. */
+pd_status pd_best_hits_noalloc(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32_t gj, int64_t* row_ptr,
+                               int32_t* cols, uint32_t* s, uint64_t capacity, uint64_t* n_hits);
+
 #ifdef __cplusplus
 }
 #endif

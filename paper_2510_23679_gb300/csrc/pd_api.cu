@@ -231,6 +231,38 @@ struct pd_bbh_set {
   Buf a, b;
 };
 
+// ------------------------------------------------------------------ internal accessors
+// Read-only views of the handles for other translation units of the library
+// (the allocation-free entry point of k_noalloc.cu).
+namespace pdg {
+
+bool ctx_view(pd_ctx* c, CtxView* v) {
+  if (!c || !v) return false;
+  v->stream = c->stream;
+  v->device = c->device;
+  v->d_err = c->d_err;
+  v->h_err = c->h_err;
+  v->launcher = &c->L;
+  return true;
+}
+
+bool ctx_swap_timing(pd_ctx* c, bool on) {
+  const bool was = c->timing;
+  c->timing = on;
+  return was;
+}
+
+pd_status ctx_fail(pd_ctx* c, pd_status st, const char* msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+const ProfilesView* profiles_view(const pd_profiles* P) { return P ? &P->view : nullptr; }
+
+int32_t profiles_genome_start(const pd_profiles* P, uint32_t g) { return P->h_genome_ptr[g]; }
+
+}  // namespace pdg
+
 // ------------------------------------------------------------------ context
 PD_API pd_status pd_ctx_create(int device, void* cuda_stream, pd_alloc_fn alloc, pd_free_fn free_fn, void* user,
                                pd_ctx** out) {

@@ -316,4 +316,19 @@ cudaError_t run_bbh_count(Launcher* L, const BbhRows& R, uint8_t* flags_by_hit, 
 cudaError_t run_bbh_write(Launcher* L, const BbhRows& R, const uint8_t* flags_by_hit, const uint32_t* row_start,
                           uint32_t a_base, uint32_t b_base, int32_t* out_a, int32_t* out_b, cudaStream_t s);
 
+// ---------------------------------------------------------------- handle access
+// Implemented in pd_api.cu; used by entry points in other files.
+struct CtxView {
+  cudaStream_t stream;
+  int device;
+  DevErr* d_err;  // device error block
+  DevErr* h_err;  // its pinned host mirror
+  Launcher* launcher;
+};
+bool ctx_view(pd_ctx* c, CtxView* v);
+bool ctx_swap_timing(pd_ctx* c, bool on);  // returns the previous setting
+pd_status ctx_fail(pd_ctx* c, pd_status st, const char* msg);
+const ProfilesView* profiles_view(const pd_profiles* P);
+int32_t profiles_genome_start(const pd_profiles* P, uint32_t g);  // genome_ptr[g] (host copy)
+
 }  // namespace pdg

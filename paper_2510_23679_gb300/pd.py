@@ -27,6 +27,10 @@ STATUS_NAMES = {0: "PD_OK", 1: "PD_ERR_ARG", 2: "PD_ERR_ALPHABET", 3: "PD_ERR_GE
 PD_MAX_K = 8
 PD_MAX_WINDOWS = 65535
 PD_MAX_GENOMES = 4096
+PD_NOALLOC_SCRATCH_BYTES = 32 << 20
+PD_NOALLOC_MAX_ROWS = 32768
+PD_NOALLOC_MAX_TARGETS = 32768
+PD_NOALLOC_MAX_HITS = 1 << 20
 
 
 class PdError(RuntimeError):
@@ -81,6 +85,8 @@ _SIGNATURES = [
     ("pd_bbh_count", C.c_uint64, [_P]),
     ("pd_bbh_free", None, [_P]),
     ("pd_summin_pairs", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _P, _P, _P, C.POINTER(C.c_uint64)]),
+    ("pd_best_hits_noalloc", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _P, _P, _P, C.c_uint64,
+                                       C.POINTER(C.c_uint64)]),
 ]
 EXPORTED = [s[0] for s in _SIGNATURES]
 
@@ -365,3 +371,15 @@ def pd_summin_pairs(ctx: Ctx, prof: Profiles, gi: int, gj: int):
     _check(ctx, _lib.pd_summin_pairs(ctx.handle, prof.handle, int(gi), int(gj), _ptr(a), _ptr(b), _ptr(s),
                                      C.byref(n)), "pd_summin_pairs")
     return a[:cnt], b[:cnt], s[:cnt]
+
+
+def pd_best_hits_noalloc(ctx: Ctx, prof: Profiles, gi: int, gj: int, row_ptr, cols, s) -> int:
+    """Best Hits of genome gi against gj into caller-owned device tensors, with
+    no device allocation by the library (for callers that cannot allocate while
+    they run).  row_ptr: int64 [|G_gi|+1]; cols: int32 [capacity]; s: uint32 or
+    int32 [capacity].  Returns the number of entries written."""
+    n = C.c_uint64(0)
+    cap = int(cols.shape[0])
+    _check(ctx, _lib.pd_best_hits_noalloc(ctx.handle, prof.handle, int(gi), int(gj), _ptr(row_ptr), _ptr(cols),
+                                          _ptr(s), cap, C.byref(n)), "pd_best_hits_noalloc")
+    return int(n.value)
