@@ -72,6 +72,23 @@ def config_of(ds, name, k, flush):
 
 
 # --------------------------------------------------------------------------- CPU oracle sample
+def captured_traffic(kernel_src, summary):
+    """DRAM bytes per launch from the committed ncu summary of the dominant
+    kernel, or None when the kernel source changed since that capture."""
+    import hashlib
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", summary)).read()
+        sha = hashlib.sha256(open(os.path.join(ROOT, kernel_src), "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m_sha = re.search(r"sha256 \(first 16 hex\): ([0-9a-f]{16})", text)
+    m_val = re.search(r"dram_bytes_per_launch: (\d+)", text)
+    if not m_sha or not m_val or m_sha.group(1) != sha:
+        return None
+    return int(m_val.group(1))
+
+
 def oracle_sample(ds, k, seconds, threads):
     """Time the oracle (as it stands) on whole genome pairs until `seconds` pass."""
     import oracle
@@ -318,7 +335,10 @@ def main():
             "genome_pairs_per_s": ds.n_genomes * (ds.n_genomes - 1) / 2 * world / (ms_per_step / 1e3),
             "step_ms": step_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "kernel": "summin_bh",
+                         "frac": achieved / peak,
+                         "traffic": captured_traffic("paper_2510_23679_gb300/csrc/k_summin.cu",
+                                                     "summin_bh_pan50x3000.md"),
+                         "kernel": "summin_bh",
                          "kernel_ms": k_avg_ms, "alg_bytes": alg_bytes, "peak_source": peak_src},
             "e2e": e2e,
             "gpu_launches": gpu_launches,
