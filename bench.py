@@ -74,7 +74,8 @@ def config_of(ds, name, k, flush):
 # --------------------------------------------------------------------------- CPU oracle sample
 def captured_traffic(kernel_src, summary):
     """DRAM bytes per launch from the committed ncu summary of the dominant
-    kernel, or None when the kernel source changed since that capture."""
+    kernel on this workload, or None when there is no capture of it or the
+    kernel source changed since."""
     import hashlib
     import re
     try:
@@ -337,7 +338,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
                          "traffic": captured_traffic("paper_2510_23679_gb300/csrc/k_summin.cu",
-                                                     "summin_bh_pan50x3000.md"),
+                                                     f"summin_bh_{args.workload}.md"),
                          "kernel": "summin_bh",
                          "kernel_ms": k_avg_ms, "alg_bytes": alg_bytes, "peak_source": peak_src},
             "e2e": e2e,

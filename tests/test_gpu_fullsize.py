@@ -1,18 +1,9 @@
-"""Parity at full size, in the launch configuration the benchmark times.
-
-The 50-genome x ~3000-gene workload is profiled and compared all-against-all
-on the GPU exactly as in bench.py (device-resident inputs, pd_build_profiles,
-pd_best_hits_all, pd_bbh_all).  The CPU oracle then recomputes sampled genome
-pairs in full (every Best Hit of both directions and every BBH pair must be
-equal), and properties that hold at any size are checked on the whole result.
-"""
-import os
-
-import numpy as np
+"""Parity at the benchmark's size (50 genomes x ~3000 genes, k=6), in the
+launch configuration bench.py times: sampled genome pairs recomputed in full
+by the oracle, and properties that hold at any size on the whole result."""
 import pytest
 
-import oracle
-from paper_2510_23679_gb300 import pd, synth
+from tests._fullsize import check_properties, check_sampled_pair, run_full
 
 pytestmark = pytest.mark.gpu
 
@@ -21,82 +12,13 @@ SAMPLED_PAIRS = [(0, 1), (17, 42), (48, 49)]
 
 @pytest.fixture(scope="module")
 def full():
-    import torch
-    ds = synth.workload("pan50x3000")
-    k = pd.pd_choose_k(ds.n_residues)
-    assert k == oracle.choose_k(ds.n_residues) == 6
-    ctx = pd.pd_ctx_create(0)
-    dev = torch.device("cuda", 0)
-    res = torch.from_numpy(ds.residues).to(dev)
-    gp = torch.from_numpy(ds.gene_ptr).to(dev)
-    gn = torch.from_numpy(ds.genome_ptr).to(dev)
-    prof = pd.pd_build_profiles(ctx, res, gp, gn, k)
-    hits = pd.pd_best_hits_all(ctx, prof)
-    bbh = pd.pd_bbh_copy(ctx, pd.pd_bbh_all(ctx, prof, hits))
-    rp, cols, s = pd.pd_hits_copy(ctx, hits)
-    _, _, _, La = pd.pd_profiles_copy_mv(ctx, prof)
-    return dict(ds=ds, k=k, ctx=ctx, prof=prof, rp=rp, cols=cols, s=s, bbh=bbh, La=La,
-                info=pd.pd_hits_get_info(hits))
-
-
-def _rows_towards(full, genome_from, genome_to):
-    ds, rp, cols, s = full["ds"], full["rp"], full["cols"], full["s"]
-    gp = ds.genome_ptr
-    t0, t1 = int(gp[genome_to]), int(gp[genome_to + 1])
-    out_c, out_s = [], []
-    for a in range(int(gp[genome_from]), int(gp[genome_from + 1])):
-        row = cols[rp[a]:rp[a + 1]]
-        sel = (row >= t0) & (row < t1)
-        out_c.append((row[sel] - t0).tolist())
-        out_s.append(s[rp[a]:rp[a + 1]][sel].tolist())
-    return out_c, out_s
+    return run_full("pan50x3000", expect_k=6)
 
 
 @pytest.mark.parametrize("gi,gj", SAMPLED_PAIRS)
 def test_sampled_pairs_against_oracle(full, gi, gj):
-    ds = full["ds"]
-    R = oracle.pair_for_dataset(ds, gi, gj, full["k"], n_threads=os.cpu_count() or 4)
-    rows, svals = _rows_towards(full, gi, gj)
-    assert rows == [R.row_bh(a).tolist() for a in range(R.S.shape[0])]
-    for a, (cs, ss) in enumerate(zip(rows, svals)):
-        assert ss == [int(R.S[a, b]) for b in cs]
-    cols_, _ = _rows_towards(full, gj, gi)
-    assert cols_ == [R.col_bh(b).tolist() for b in range(R.S.shape[1])]
-    gp = ds.genome_ptr
-    a0, b0 = int(gp[gi]), int(gp[gj])
-    got = full["bbh"]
-    sel = (got[:, 0] >= a0) & (got[:, 0] < int(gp[gi + 1])) & (got[:, 1] >= b0) & (got[:, 1] < int(gp[gj + 1]))
-    assert [tuple(x) for x in (got[sel] - [a0, b0]).tolist()] == [tuple(x) for x in R.bbh.tolist()]
-    # the one-pair-per-launch form agrees too
-    assert [tuple(x) for x in pd.pd_bbh_copy(full["ctx"], pd.pd_bbh(full["ctx"], full["prof"], gi, gj)).tolist()] == \
-        [tuple(x) for x in R.bbh.tolist()]
+    check_sampled_pair(full, gi, gj)
 
 
 def test_properties_at_full_size(full):
-    ds, rp, cols, s, bbh, La = full["ds"], full["rp"], full["cols"], full["s"], full["bbh"], full["La"]
-    gp = ds.genome_ptr.astype(np.int64)
-    genome_of = np.repeat(np.arange(ds.n_genomes), np.diff(gp))
-    row_of = np.repeat(np.arange(ds.n_genes), np.diff(rp))
-    assert len(rp) == ds.n_genes + 1 and rp[-1] == len(cols) == full["info"].n_hits
-    # no hit inside the query's own genome; 1 <= s <= min(La, Lb)
-    assert np.all(genome_of[cols] != genome_of[row_of])
-    assert np.all(s >= 1) and np.all(s <= np.minimum(La[row_of], La[cols]))
-    # rows strictly ascending
-    same_row = row_of[1:] == row_of[:-1]
-    assert np.all(cols[1:][same_row] > cols[:-1][same_row])
-    # all hits of a row towards one genome share one ratio s / (La + Lb - s)
-    den = La[row_of].astype(np.int64) + La[cols] - s
-    key = row_of.astype(np.int64) * ds.n_genomes + genome_of[cols]
-    same = key[1:] == key[:-1]
-    assert np.all((s[1:] * den[:-1])[same] == (s[:-1] * den[1:])[same])
-    # BBH: ordered, genome(a) < genome(b), and a mutual Best Hit
-    assert np.all(genome_of[bbh[:, 0]] < genome_of[bbh[:, 1]])
-    order = bbh[:, 0].astype(np.int64) * ds.n_genes + bbh[:, 1]
-    assert np.all(np.diff(order) > 0)
-    G = np.int64(ds.n_genes)
-    fwd = np.sort(row_of.astype(np.int64) * G + cols)
-    assert np.all(np.isin(bbh[:, 0].astype(np.int64) * G + bbh[:, 1], fwd))
-    assert np.all(np.isin(bbh[:, 1].astype(np.int64) * G + bbh[:, 0], fwd))
-    # every mutual pair of Best Hits is reported
-    mutual = np.isin(cols.astype(np.int64) * G + row_of, fwd) & (genome_of[row_of] < genome_of[cols])
-    assert int(mutual.sum()) == len(bbh)
+    check_properties(full)
