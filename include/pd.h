@@ -127,6 +127,21 @@ pd_status pd_build_profiles(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res
                             const int64_t* gene_ptr, uint32_t n_genes, const int32_t* genome_ptr,
                             uint32_t n_genomes, int k, pd_profiles** out);
 
+/* pd_build_profiles over several independent problems at once.  genome_seg
+ * (HOST array, n_genomes entries, each < n_genomes) assigns every genome to a
+ * segment; k-mers of different segments are different dictionary entries
+ * (the segment is part of the k-mer's identity), so genes of different
+ * segments share no k-mer, have sum-min 0 and are never candidates (reading
+ * of "minimum overlap" under Eq. (8)).  Best Hits and BBH of a segmented
+ * profile set therefore equal those of each segment profiled alone.  Codes
+ * returned by pd_profiles_copy_mv / _copy_index are segment * 20^k + code.
+ * Extra error: PD_ERR_BUDGET when (max segment + 1) * 20^k bits exceed the
+ * 4 GiB dictionary bitmap limit. */
+pd_status pd_build_profiles_segmented(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res,
+                                      const int64_t* gene_ptr, uint32_t n_genes, const int32_t* genome_ptr,
+                                      uint32_t n_genomes, const uint32_t* genome_seg, int k,
+                                      pd_profiles** out);
+
 typedef struct {
   int k;
   uint32_t n_genes, n_genomes;
@@ -218,6 +233,59 @@ void pd_bbh_free(pd_bbh_set* set);
  * and the call fills them.  Exposes the sum-min step for checking. */
 pd_status pd_summin_pairs(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32_t gj,
                           int32_t* a, int32_t* b, uint32_t* s, uint64_t* n);
+
+/* ---------------------------------------------------------------- batched jobs */
+
+typedef struct pd_batch pd_batch;
+
+/* How a batch is cut into chunks; each chunk is one segmented profile build,
+ * one Best Hit launch sequence and one BBH launch sequence over all of its
+ * jobs.  Zero fields take the defaults. */
+typedef struct {
+  uint64_t max_chunk_windows; /* k-mer windows profiled together (default 2^29) */
+  uint32_t max_chunk_jobs;    /* jobs per chunk (default: as many as the 1 GiB
+                                 chunk dictionary bitmap holds at the job's k,
+                                 at most PD_MAX_GENOMES / 2) */
+  uint32_t reserved;
+} pd_batch_tuning;
+
+typedef struct {
+  uint32_t n_jobs;
+  uint32_t n_chunks;         /* chunks the batch was cut into */
+  uint64_t n_rows;           /* sum over jobs of |A| + |B| */
+  uint64_t n_hits;           /* Best Hit entries, both directions, all jobs */
+  uint64_t n_bbh;            /* BBH pairs, all jobs */
+  uint64_t postings_walked;  /* (query k-mer, posting) matches visited */
+} pd_batch_info;
+
+/* Best Hits in both directions and Bidirectional Best Hits (Eqs. (8)-(9),
+ * Algorithms 2-3) of many independent genome-pair jobs, each at its own k.
+ *   residues, gene_ptr, genome_ptr  the genomes, as in pd_build_profiles
+ *              (residues host or device; offsets host or device)
+ *   jobs       HOST array of 2*n_jobs genome indices: job j compares genome
+ *              A = jobs[2j] with genome B = jobs[2j+1] (A != B); a genome may
+ *              appear in several jobs
+ *   job_k      HOST array of n_jobs k values, each in 1..PD_MAX_K
+ *   tuning     NULL for the defaults
+ * Jobs with the same k are profiled together in chunks (segmented profiles:
+ * one dictionary namespace per job), so one launch sequence serves a whole
+ * chunk.  Each job's result equals pd_bbh / pd_best_hits on a dataset of its
+ * two genomes alone.  Errors as pd_build_profiles, plus PD_ERR_ARG for bad job
+ * entries.  *out receives a device-resident handle. */
+pd_status pd_bbh_batch(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                       uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* jobs,
+                       const int32_t* job_k, uint32_t n_jobs, const pd_batch_tuning* tuning, pd_batch** out);
+pd_status pd_batch_get_info(const pd_batch* batch, pd_batch_info* info);
+/* Best Hits of every job as one CSR: the rows of job j are the genes of A then
+ * the genes of B (jobs in order); row_ptr n_rows+1 int64; cols int32, the
+ * column's index inside the partner genome (B for rows of A, A for rows of B);
+ * s uint32 sum-min.  Host or device pointers, NULL to skip. */
+pd_status pd_batch_copy_hits(pd_ctx* ctx, const pd_batch* batch, int64_t* row_ptr, int32_t* cols, uint32_t* s);
+/* BBH pairs of every job: job_ptr n_jobs+1 int64 offsets; pair p of job j is
+ * (a[p] local in A, b[p] local in B), ascending (a, b) inside each job.  Host
+ * or device pointers, NULL to skip. */
+pd_status pd_batch_copy_bbh(pd_ctx* ctx, const pd_batch* batch, int64_t* job_ptr, int32_t* a, int32_t* b);
+void pd_batch_free(pd_batch* batch);
 
 /* ---------------------------------------------------------------- no allocation */
 

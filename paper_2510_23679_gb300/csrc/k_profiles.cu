@@ -5,7 +5,10 @@
 //   encode_mark    residue -> 0..19, base-20 code of every window (Eq. (1):
 //                  windows of exactly k letters), one bit per code in a bitmap
 //                  over all 20^k codes; letters outside the alphabet raise
-//                  PD_ERR_ALPHABET.
+//                  PD_ERR_ALPHABET.  Segmented datasets (independent problems
+//                  profiled together) give each segment its own 20^k range of
+//                  the bitmap, code + segment * 20^k, so k-mers of different
+//                  segments get different ids and never meet in a posting list.
 //   (scan)         popcount prefix of the bitmap words: the dense id of a code
 //                  is its rank among the codes present (an injective f that is
 //                  ascending with the code, "Multiplicity vector building").
@@ -45,7 +48,8 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 // ------------------------------------------------------------ encode_mark
 __global__ void __launch_bounds__(kEncThreads)
     k_encode_mark(const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr, uint32_t n_genes, int k,
-                  unsigned long long* __restrict__ bitmap, DevErr* err) {
+                  unsigned long long* __restrict__ bitmap, const uint16_t* __restrict__ gene_genome,
+                  const unsigned long long* __restrict__ genome_code_base, DevErr* err) {
   __shared__ uint8_t lut[256];
   init_letter_table(lut);
   const uint32_t lane = threadIdx.x & 31u;
@@ -54,6 +58,7 @@ __global__ void __launch_bounds__(kEncThreads)
     const int64_t r0 = gene_ptr[g];
     const uint32_t len = (uint32_t)(gene_ptr[g + 1] - r0);
     const uint8_t* s = res + r0;
+    const unsigned long long base = genome_code_base ? genome_code_base[gene_genome[g]] : 0ull;
     for (uint32_t p = lane; p < len; p += 32) {
       if (lut[s[p]] >= kAlphabetSize) raise_error(err, PD_ERR_ALPHABET, (unsigned long long)(r0 + p));
     }
@@ -65,6 +70,7 @@ __global__ void __launch_bounds__(kEncThreads)
         ok &= c < (uint32_t)kAlphabetSize;
         code = code * (unsigned long long)kAlphabetSize + (c < (uint32_t)kAlphabetSize ? c : 0u);
       }
+      code += base;
       if (ok) atomicOr(&bitmap[code >> 6], 1ull << (code & 63u));
     }
   }
@@ -97,6 +103,7 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
   const uint32_t off = win_off[g];
   const uint32_t La = win_off[g + 1] - off;
   const uint8_t* s = res + gene_ptr[g];
+  const unsigned long long base = M.genome_code_base ? M.genome_code_base[M.gene_genome[g]] : 0ull;
   for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) table[h] = kFree;
   __syncthreads();
   for (uint32_t p = threadIdx.x; p < La; p += blockDim.x) {
@@ -105,7 +112,7 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
       const uint32_t c = lut[s[p + t]];
       code = code * (unsigned long long)kAlphabetSize + (c < (uint32_t)kAlphabetSize ? c : 0u);
     }
-    const uint32_t id = code_rank(code, bitmap, word_rank);
+    const uint32_t id = code_rank(code + base, bitmap, word_rank);
     uint32_t h = mix32(id) & (cap - 1u);
     uint32_t probe = 0;
     for (; probe < cap; ++probe) {  // a free slot always exists: cap > La >= distinct ids
@@ -345,9 +352,11 @@ unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
   } while (0)
 
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
-                            unsigned long long* bitmap, DevErr* err, cudaStream_t s) {
+                            unsigned long long* bitmap, const uint16_t* gene_genome,
+                            const unsigned long long* genome_code_base, DevErr* err, cudaStream_t s) {
   const unsigned grid = grid_for((uint64_t)n_genes * 32, kEncThreads, 152u * 16u);
-  PD_LAUNCH(L, "encode_mark", k_encode_mark<<<grid, kEncThreads, 0, s>>>(res, gene_ptr, n_genes, k, bitmap, err));
+  PD_LAUNCH(L, "encode_mark", k_encode_mark<<<grid, kEncThreads, 0, s>>>(res, gene_ptr, n_genes, k, bitmap,
+                                                                        gene_genome, genome_code_base, err));
   return cudaSuccess;
 }
 

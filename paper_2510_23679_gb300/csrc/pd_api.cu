@@ -16,41 +16,10 @@
 #include <vector>
 
 #include "pd.h"
+#include "pd_host.cuh"
 #include "pd_internal.cuh"
 
-#define PD_API extern "C" __attribute__((visibility("default")))
-
-struct pd_ctx;
-
-namespace pdg {
-
-struct Launcher {
-  pd_ctx* ctx;
-};
-
-}  // namespace pdg
-
-struct PendingTiming {
-  std::string name;
-  cudaEvent_t start, stop;
-};
-
-struct pd_ctx {
-  int device = 0;
-  cudaStream_t stream = nullptr;
-  pd_alloc_fn alloc = nullptr;
-  pd_free_fn free_fn = nullptr;
-  void* user = nullptr;
-  std::string err;
-  uint64_t launches = 0;
-  bool timing = false;
-  std::vector<PendingTiming> pending;
-  std::vector<cudaEvent_t> event_pool;
-  std::map<std::string, std::pair<double, uint64_t>> kernel_ms;
-  pdg::Launcher L{nullptr};
-  pdg::DevErr* d_err = nullptr;  // device error block
-  pdg::DevErr* h_err = nullptr;  // pinned host mirror
-};
+using namespace pdh;
 
 // ------------------------------------------------------------------ launches
 namespace pdg {
@@ -89,147 +58,6 @@ cudaError_t launch_end(Launcher* L, const char* name) {
 }
 
 }  // namespace pdg
-
-// ------------------------------------------------------------------ helpers
-namespace {
-
-using pdg::DevErr;
-
-pd_status fail(pd_ctx* c, pd_status st, const std::string& msg) {
-  if (c) c->err = msg;
-  return st;
-}
-
-pd_status fail_cuda(pd_ctx* c, cudaError_t e, const char* what) {
-  std::string m = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
-  cudaGetLastError();
-  return fail(c, PD_ERR_CUDA, m);
-}
-
-#define CK(expr)                                      \
-  do {                                                \
-    cudaError_t e_ = (expr);                          \
-    if (e_ != cudaSuccess) return fail_cuda(c, e_, #expr); \
-  } while (0)
-
-// Device buffer owned through the context's allocator.
-struct Buf {
-  pd_ctx* c = nullptr;
-  void* p = nullptr;
-  size_t n = 0;
-  Buf() = default;
-  Buf(const Buf&) = delete;
-  Buf& operator=(const Buf&) = delete;
-  Buf(Buf&& o) noexcept : c(o.c), p(o.p), n(o.n) { o.p = nullptr; }
-  Buf& operator=(Buf&& o) noexcept {
-    if (this != &o) {
-      release();
-      c = o.c;
-      p = o.p;
-      n = o.n;
-      o.p = nullptr;
-    }
-    return *this;
-  }
-  ~Buf() { release(); }
-  bool alloc(pd_ctx* ctx, size_t bytes) {
-    release();
-    c = ctx;
-    n = (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
-    if (c->alloc) {
-      p = c->alloc(n, (void*)c->stream, c->user);
-    } else if (cudaMallocAsync(&p, n, c->stream) != cudaSuccess) {
-      cudaGetLastError();
-      p = nullptr;
-    }
-    return p != nullptr;
-  }
-  void release() {
-    if (p && c) {
-      if (c->free_fn) c->free_fn(p, n, (void*)c->stream, c->user);
-      else cudaFreeAsync(p, c->stream);
-    }
-    p = nullptr;
-  }
-  template <typename T>
-  T* as() const {
-    return (T*)p;
-  }
-};
-
-#define ALLOC(buf, bytes)                                                                        \
-  do {                                                                                           \
-    if (!(buf).alloc(c, (bytes))) return fail(c, PD_ERR_OOM, "device allocation of " +           \
-                                                             std::to_string((size_t)(bytes)) +   \
-                                                             " bytes failed (" #buf ")");        \
-  } while (0)
-
-bool is_device_ptr(const void* p) {
-  if (!p) return false;
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
-uint32_t bits_for(uint32_t max_value) {
-  uint32_t b = 1;
-  while (b < 32 && (max_value >> b) != 0) ++b;
-  return b;
-}
-
-uint64_t pow_u64(uint64_t b, int e) {
-  uint64_t r = 1;
-  for (int i = 0; i < e; ++i) r *= b;
-  return r;
-}
-
-// Reads the device error block; returns PD_OK or the recorded error.
-pd_status check_dev_err(pd_ctx* c) {
-  CK(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(DevErr), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  if (c->h_err->code != 0) {
-    const int code = c->h_err->code;
-    const unsigned long long det = c->h_err->detail;
-    CK(cudaMemsetAsync(c->d_err, 0, sizeof(DevErr), c->stream));
-    if (code == PD_ERR_ALPHABET)
-      return fail(c, PD_ERR_ALPHABET, "residue at offset " + std::to_string(det) +
-                                          " is not one of ACDEFGHIKLMNPQRSTVWY");
-    return fail(c, (pd_status)code, "device reported error " + std::to_string(code) + " (detail " +
-                                        std::to_string(det) + ")");
-  }
-  return PD_OK;
-}
-
-}  // namespace
-
-// ------------------------------------------------------------------ handles
-struct pd_profiles {
-  pd_ctx* ctx = nullptr;
-  pdg::ProfilesView view{};
-  pd_profiles_info info{};
-  Buf genome_ptr, La, win_off, mv_n, mv_id, mv_cnt, mv_post, mv_plen, gene_genome, ginfo, bitmap, word_rank, post_ptr,
-      post, order;
-  std::vector<int32_t> h_genome_ptr;
-};
-
-struct pd_hits {
-  pd_ctx* ctx = nullptr;
-  int all_pairs = 0;
-  uint32_t n_rows = 0, row_base = 0, col_base = 0;
-  uint32_t nA = 0, qa0 = 0, qb0 = 0;  // pair form with both directions (internal)
-  uint64_t n_hits = 0, walked = 0;
-  uint32_t n_deferred = 0;
-  Buf row_off, row_len, out_b, out_s;
-};
-
-struct pd_bbh_set {
-  pd_ctx* ctx = nullptr;
-  uint64_t n = 0;
-  Buf a, b;
-};
 
 // ------------------------------------------------------------------ internal accessors
 // Read-only views of the handles for other translation units of the library
@@ -386,9 +214,12 @@ static uint32_t ceil_log2_u64(uint64_t x) {
   return b;
 }
 
-static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+// Maximum bitmap size of a segmented dataset (one bit per segment x 20^k code).
+static constexpr uint64_t kMaxBitmapBytes = (uint64_t)4 << 30;
+
+pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                                      uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
-                                     pd_profiles** out) {
+                                     const uint32_t* genome_seg, pd_profiles** out) {
   if (k < 1 || k > PD_MAX_K) return fail(c, PD_ERR_K_RANGE, "k must be in [1, " + std::to_string(PD_MAX_K) + "]");
   if (!gene_ptr || !genome_ptr || (n_res > 0 && !residues))
     return fail(c, PD_ERR_ARG, "null residues, gene_ptr or genome_ptr");
@@ -442,12 +273,25 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   P->h_genome_ptr = hgn;
   std::unique_ptr<pd_profiles> guard(P);
   const uint64_t n_codes = pow_u64(20, k);
-  const uint64_t n_words = (n_codes + 63) / 64;
+  uint64_t n_seg = 1;
+  std::vector<unsigned long long> code_base;
+  if (genome_seg) {
+    code_base.resize(n_genomes);
+    for (uint32_t i = 0; i < n_genomes; ++i) {
+      if (genome_seg[i] >= n_genomes) return fail(c, PD_ERR_ARG, "genome_seg values must be < n_genomes");
+      n_seg = std::max<uint64_t>(n_seg, (uint64_t)genome_seg[i] + 1);
+      code_base[i] = (unsigned long long)genome_seg[i] * n_codes;
+    }
+    if (n_seg * n_codes / 8 > kMaxBitmapBytes)
+      return fail(c, PD_ERR_BUDGET, "segments x 20^k exceed the dictionary bitmap limit (" +
+                                        std::to_string(kMaxBitmapBytes >> 30) + " GiB)");
+  }
+  const uint64_t n_words = (n_seg * n_codes + 63) / 64;
   const size_t G1 = std::max<uint32_t>(n_genes, 1), W1 = std::max<uint64_t>(W, 1);
   pdg::Launcher* L = &c->L;
 
   // ---- inputs on the device
-  Buf d_res, d_gene_ptr, d_mid, d_long, d_long_off, d_long_scratch, tmp, d_counts, minhash;
+  Buf d_res, d_gene_ptr, d_mid, d_long, d_long_off, d_long_scratch, tmp, d_counts, minhash, d_code_base;
   const uint8_t* res_dev = residues;
   const int64_t* gp_devp = gene_ptr;
   if (n_res > 0 && !is_device_ptr(residues)) {
@@ -474,12 +318,19 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   CK(pdg::run_gene_info(L, P->genome_ptr.as<int32_t>(), n_genomes, P->La.as<uint32_t>(),
                         P->gene_genome.as<uint16_t>(), P->ginfo.as<uint32_t>(), c->stream));
 
+  if (genome_seg) {
+    ALLOC(d_code_base, sizeof(unsigned long long) * n_genomes);
+    CK(cudaMemcpyAsync(d_code_base.p, code_base.data(), sizeof(unsigned long long) * n_genomes,
+                       cudaMemcpyHostToDevice, c->stream));
+  }
+
   // ---- dictionary: bitmap of present codes and word ranks
   ALLOC(P->bitmap, sizeof(unsigned long long) * n_words);
   ALLOC(P->word_rank, sizeof(uint32_t) * n_words);
   CK(cudaMemsetAsync(P->bitmap.p, 0, sizeof(unsigned long long) * n_words, c->stream));
   if (n_genes)
-    CK(pdg::run_encode_mark(L, res_dev, gp_devp, n_genes, k, P->bitmap.as<unsigned long long>(), c->d_err,
+    CK(pdg::run_encode_mark(L, res_dev, gp_devp, n_genes, k, P->bitmap.as<unsigned long long>(),
+                            P->gene_genome.as<uint16_t>(), d_code_base.as<unsigned long long>(), c->d_err,
                             c->stream));
   const uint32_t kOrderShift = 16;  // 65536 min-hash buckets
   const uint64_t n_order_b = (uint64_t)1 << (32 - kOrderShift);
@@ -529,6 +380,8 @@ static pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_
   M.cnt_bits = cnt_bits;
   M.cnt_cap = cnt_cap;
   M.err = c->d_err;
+  M.gene_genome = P->gene_genome.as<uint16_t>();
+  M.genome_code_base = d_code_base.as<unsigned long long>();
   if (n_genes)
     CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
                          P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), M,
@@ -620,11 +473,28 @@ PD_API pd_status pd_build_profiles(pd_ctx* c, const uint8_t* residues, uint64_t 
   if (!c || !out) return PD_ERR_ARG;
   *out = nullptr;
   try {
-    return build_profiles_impl(c, residues, n_res, gene_ptr, n_genes, genome_ptr, n_genomes, k, out);
+    return build_profiles_impl(c, residues, n_res, gene_ptr, n_genes, genome_ptr, n_genomes, k, nullptr, out);
   } catch (const std::bad_alloc&) {
     return fail(c, PD_ERR_OOM, "host allocation failed");
   } catch (...) {
     return fail(c, PD_ERR_INTERNAL, "exception in pd_build_profiles");
+  }
+}
+
+PD_API pd_status pd_build_profiles_segmented(pd_ctx* c, const uint8_t* residues, uint64_t n_res,
+                                             const int64_t* gene_ptr, uint32_t n_genes, const int32_t* genome_ptr,
+                                             uint32_t n_genomes, const uint32_t* genome_seg, int k,
+                                             pd_profiles** out) {
+  if (!c || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  if (!genome_seg) return fail(c, PD_ERR_ARG, "null genome_seg");
+  if (is_device_ptr(genome_seg)) return fail(c, PD_ERR_ARG, "genome_seg must be a host array");
+  try {
+    return build_profiles_impl(c, residues, n_res, gene_ptr, n_genes, genome_ptr, n_genomes, k, genome_seg, out);
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_build_profiles_segmented");
   }
 }
 
@@ -636,12 +506,6 @@ PD_API pd_status pd_profiles_get_info(const pd_profiles* P, pd_profiles_info* in
 
 PD_API void pd_profiles_free(pd_profiles* P) { delete P; }
 
-// Copy `bytes` from a device buffer to a caller pointer (host or device).
-static pd_status copy_out(pd_ctx* c, void* dst, const void* src, size_t bytes) {
-  if (!dst || bytes == 0) return PD_OK;
-  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream));
-  return PD_OK;
-}
 
 namespace {
 __global__ void k_u32_to_i64(const uint32_t* __restrict__ a, uint64_t n, int64_t* __restrict__ out) {
@@ -735,14 +599,16 @@ PD_API pd_status pd_profiles_copy_index(pd_ctx* c, const pd_profiles* P, int64_t
 // ------------------------------------------------------------------ sum-min + Best Hits
 // Runs the shared-memory tiers, then (only if needed) the global-memory tier
 // for the queries they deferred, growing the output until every row fits.
-static pd_status run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& Q, bool emit_all, pd_hits* H) {
+pd_status pdh::run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& Q, bool emit_all, pd_hits* H,
+                        uint32_t genomes_per_query) {
   const pdg::ProfilesView& v = P->view;
   pdg::Launcher* L = &c->L;
   const uint32_t nq = Q.n_queries;
   const uint32_t n_rows = Q.all_pairs ? v.n_genes : nq;
   uint64_t cap;
   if (Q.all_pairs)
-    cap = (uint64_t)nq * std::max<uint32_t>(v.n_genomes - 1, 1) * 3 / 2 + 4096;
+    cap = (uint64_t)nq * std::max<uint32_t>(genomes_per_query ? genomes_per_query : v.n_genomes - 1, 1) * 3 / 2 +
+          4096;
   else
     cap = (uint64_t)nq * 4 + 4096;
   if (emit_all) cap = (uint64_t)nq * 64 + 4096;
@@ -931,7 +797,7 @@ PD_API pd_status pd_hits_copy(pd_ctx* c, const pd_hits* H, int64_t* row_ptr, int
 PD_API void pd_hits_free(pd_hits* H) { delete H; }
 
 // ------------------------------------------------------------------ BBH
-static pd_status bbh_impl(pd_ctx* c, const pdg::BbhRows& R, uint64_t n_hit_slots, uint32_t a_base, uint32_t b_base,
+pd_status pdh::bbh_impl(pd_ctx* c, const pdg::BbhRows& R, uint64_t n_hit_slots, uint32_t a_base, uint32_t b_base,
                           pd_bbh_set* S) {
   pdg::Launcher* L = &c->L;
   Buf flags, row_cnt, row_start, tmp;

@@ -1,0 +1,427 @@
+// pd_batch.cu -- batched genome-pair jobs (pd_bbh_batch in pd.h).
+//
+// Many independent jobs "compare genome A with genome B at k" (Algorithms
+// 2-3 per job) are served by few launch sequences instead of one per job:
+//
+//   1. jobs are grouped by k and cut into chunks (bounded windows, bounded
+//      dictionary bitmap);
+//   2. a chunk is ONE segmented profile build (each job its own k-mer
+//      namespace, so postings of one job never reach another job's genes),
+//      ONE all-pairs Best Hit pass (every gene of every job queried in the
+//      same persistent sum-min launch; own-genome targets are skipped and
+//      other jobs' genes can never be candidates), and ONE BBH pass;
+//   3. the chunk results are scattered into job order: per-row Best Hit
+//      lengths, one scan over all rows of the batch, then the rows themselves
+//      with columns made local to the partner genome; BBH pairs likewise with
+//      one scan over the jobs.
+//
+// A chunk's genomes are read in place when they are consecutive in the input;
+// otherwise their residues are gathered into one contiguous buffer first.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "pd.h"
+#include "pd_host.cuh"
+#include "pd_internal.cuh"
+
+using namespace pdh;
+
+struct pd_batch {
+  pd_ctx* ctx = nullptr;
+  pd_batch_info info{};
+  Buf row_ptr, cols, s, job_ptr, a, b;
+};
+
+namespace {
+
+constexpr uint64_t kDefaultChunkWindows = 1ull << 29;
+constexpr uint64_t kChunkBitmapBytes = 1ull << 30;
+
+struct ByteRange {
+  unsigned long long src, dst, len;
+};
+
+// One job of a chunk: where its genes sit in the chunk and in the batch.
+struct ChunkJob {
+  uint32_t job;        // batch job index
+  uint32_t a0, nA;     // chunk gene ids of genome A: a0 .. a0+nA-1
+  uint32_t b0, nB;     // ... of genome B (b0 = a0 + nA)
+  uint32_t bbh_lo;     // first BBH pair of the job in the chunk's pair list (device-written)
+  unsigned long long row0;  // first batch row of the job
+};
+
+__global__ void k_gather_ranges(const uint8_t* __restrict__ src, const ByteRange* __restrict__ ranges, uint32_t n,
+                                uint8_t* __restrict__ dst) {
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    const ByteRange r = ranges[i];
+    for (unsigned long long p = threadIdx.x; p < r.len; p += blockDim.x) dst[r.dst + p] = src[r.src + p];
+  }
+}
+
+// Row lengths of a chunk's Best Hits into batch row order.
+__global__ void k_rows_len(const ChunkJob* __restrict__ jobs, uint32_t n_jobs, const uint32_t* __restrict__ row_len,
+                           uint32_t* __restrict__ batch_len) {
+  for (uint32_t j = blockIdx.x; j < n_jobs; j += gridDim.x) {
+    const ChunkJob J = jobs[j];
+    for (uint32_t r = threadIdx.x; r < J.nA + J.nB; r += blockDim.x) batch_len[J.row0 + r] = row_len[J.a0 + r];
+  }
+}
+
+// Best Hit rows of a chunk into the batch CSR, one warp per row; columns
+// become indices inside the partner genome.
+__global__ void k_rows_fill(const ChunkJob* __restrict__ jobs, uint32_t n_jobs,
+                            const unsigned long long* __restrict__ row_off, const uint32_t* __restrict__ row_len,
+                            const uint32_t* __restrict__ hit_b, const uint32_t* __restrict__ hit_s,
+                            const unsigned long long* __restrict__ batch_ptr, int32_t* __restrict__ cols,
+                            uint32_t* __restrict__ s) {
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  for (uint32_t j = blockIdx.x; j < n_jobs; j += gridDim.x) {
+    const ChunkJob J = jobs[j];
+    for (uint32_t r = warp; r < J.nA + J.nB; r += n_warps) {
+      const uint32_t g = J.a0 + r;
+      const uint32_t partner0 = r < J.nA ? J.b0 : J.a0;
+      const unsigned long long src = row_off[g], dst = batch_ptr[J.row0 + r];
+      const uint32_t len = row_len[g];
+      for (uint32_t i = lane; i < len; i += 32) {
+        cols[dst + i] = (int32_t)(hit_b[src + i] - partner0);
+        s[dst + i] = hit_s[src + i];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t lower_bound_i32(const int32_t* a, uint32_t n, int32_t x) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (a[mid] < x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// BBH pairs of each chunk job: the chunk's pairs are sorted by a and a job's
+// A genes are one range, so its pairs are the run [lower_bound(a0),
+// lower_bound(a0 + nA)).
+__global__ void k_bbh_runs(ChunkJob* __restrict__ jobs, uint32_t n_jobs, const int32_t* __restrict__ pa, uint32_t n_pairs,
+                           uint32_t* __restrict__ job_cnt) {
+  for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_jobs; j += gridDim.x * blockDim.x) {
+    const uint32_t lo = lower_bound_i32(pa, n_pairs, (int32_t)jobs[j].a0);
+    const uint32_t hi = lower_bound_i32(pa, n_pairs, (int32_t)(jobs[j].a0 + jobs[j].nA));
+    jobs[j].bbh_lo = lo;
+    job_cnt[jobs[j].job] = hi - lo;
+  }
+}
+
+__global__ void k_bbh_fill(const ChunkJob* __restrict__ jobs, uint32_t n_jobs, const int32_t* __restrict__ pa,
+                           const int32_t* __restrict__ pb, const unsigned long long* __restrict__ job_ptr,
+                           int32_t* __restrict__ a, int32_t* __restrict__ b) {
+  for (uint32_t j = blockIdx.x; j < n_jobs; j += gridDim.x) {
+    const ChunkJob J = jobs[j];
+    const unsigned long long dst = job_ptr[J.job], n = job_ptr[J.job + 1] - dst;
+    for (unsigned long long i = threadIdx.x; i < n; i += blockDim.x) {
+      a[dst + i] = pa[J.bbh_lo + i] - (int32_t)J.a0;
+      b[dst + i] = pb[J.bbh_lo + i] - (int32_t)J.b0;
+    }
+  }
+}
+
+unsigned grid_of(uint64_t items, unsigned per_block, unsigned cap) {
+  uint64_t b = (items + per_block - 1) / per_block;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, cap));
+}
+
+#define PD_KLAUNCH(name, ...)                            \
+  do {                                                   \
+    CK(pdg::launch_begin(&c->L, name));                  \
+    __VA_ARGS__;                                         \
+    CK(pdg::launch_end(&c->L, name));                    \
+  } while (0)
+
+// Results of one chunk, kept until the batch is assembled.
+struct ChunkOut {
+  std::vector<ChunkJob> jobs;
+  Buf d_jobs;
+  pd_hits hits;
+  pd_bbh_set bbh;
+};
+
+pd_status batch_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr, uint32_t n_genes,
+                     const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* jobs, const int32_t* job_k,
+                     uint32_t n_jobs, const pd_batch_tuning* tuning, pd_batch** out) {
+  if ((n_jobs && (!jobs || !job_k)) || !gene_ptr || !genome_ptr || (n_res && !residues))
+    return fail(c, PD_ERR_ARG, "null argument");
+  if (n_jobs && (is_device_ptr(jobs) || is_device_ptr(job_k)))
+    return fail(c, PD_ERR_ARG, "jobs and job_k must be host arrays");
+  if (n_genomes < 1) return fail(c, PD_ERR_ARG, "n_genomes must be >= 1");
+  CK(cudaSetDevice(c->device));
+  const uint64_t max_windows = (tuning && tuning->max_chunk_windows) ? tuning->max_chunk_windows
+                                                                     : kDefaultChunkWindows;
+
+  // ---- offsets on the host
+  std::vector<int64_t> hg(n_genes + 1);
+  std::vector<int32_t> hgn(n_genomes + 1);
+  CK(cudaMemcpyAsync(hg.data(), gene_ptr, sizeof(int64_t) * (n_genes + 1), cudaMemcpyDefault, c->stream));
+  CK(cudaMemcpyAsync(hgn.data(), genome_ptr, sizeof(int32_t) * (n_genomes + 1), cudaMemcpyDefault, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (hg[0] != 0 || (uint64_t)hg[n_genes] != n_res) return fail(c, PD_ERR_ARG, "gene_ptr must run from 0 to n_res");
+  if (hgn[0] != 0 || (uint32_t)hgn[n_genomes] != n_genes)
+    return fail(c, PD_ERR_ARG, "genome_ptr must run from 0 to n_genes");
+  for (uint32_t i = 0; i < n_genomes; ++i)
+    if (hgn[i + 1] < hgn[i]) return fail(c, PD_ERR_ARG, "genome_ptr is decreasing at " + std::to_string(i));
+  for (uint32_t g = 0; g < n_genes; ++g)
+    if (hg[g + 1] < hg[g]) return fail(c, PD_ERR_ARG, "gene_ptr is decreasing at " + std::to_string(g));
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    if (jobs[2 * j] >= n_genomes || jobs[2 * j + 1] >= n_genomes || jobs[2 * j] == jobs[2 * j + 1])
+      return fail(c, PD_ERR_ARG, "job " + std::to_string(j) + " needs two distinct genome indices < n_genomes");
+    if (job_k[j] < 1 || job_k[j] > PD_MAX_K)
+      return fail(c, PD_ERR_K_RANGE, "job " + std::to_string(j) + ": k must be in [1, " +
+                                          std::to_string(PD_MAX_K) + "]");
+  }
+  auto genes_of = [&](uint32_t i) { return (uint32_t)(hgn[i + 1] - hgn[i]); };
+  auto windows_of = [&](uint32_t i, int k) {
+    uint64_t w = 0;
+    for (int32_t g = hgn[i]; g < hgn[i + 1]; ++g) {
+      const int64_t len = hg[g + 1] - hg[g];
+      if (len >= k) w += (uint64_t)(len - k + 1);
+    }
+    return w;
+  };
+
+  // ---- residues on the device (one copy of host input)
+  Buf d_all;
+  const uint8_t* res_dev = residues;
+  if (n_res && !is_device_ptr(residues)) {
+    ALLOC(d_all, n_res);
+    CK(cudaMemcpyAsync(d_all.p, residues, n_res, cudaMemcpyHostToDevice, c->stream));
+    res_dev = d_all.as<uint8_t>();
+  }
+
+  // ---- batch rows
+  std::unique_ptr<pd_batch> B(new pd_batch());
+  B->ctx = c;
+  std::vector<unsigned long long> row0(n_jobs + 1, 0);
+  for (uint32_t j = 0; j < n_jobs; ++j) row0[j + 1] = row0[j] + genes_of(jobs[2 * j]) + genes_of(jobs[2 * j + 1]);
+  const uint64_t n_rows = row0[n_jobs];
+  Buf row_len, job_cnt, tmp;
+  ALLOC(row_len, sizeof(uint32_t) * std::max<uint64_t>(n_rows, 1));
+  ALLOC(job_cnt, sizeof(uint32_t) * (n_jobs + 1));
+  ALLOC(B->row_ptr, sizeof(unsigned long long) * (n_rows + 1));
+  ALLOC(B->job_ptr, sizeof(unsigned long long) * (n_jobs + 1));
+  ALLOC(tmp, pdg::scan_temp_bytes(std::max<uint64_t>(n_rows, n_jobs) + 1) + 64);
+  CK(cudaMemsetAsync(row_len.p, 0, sizeof(uint32_t) * std::max<uint64_t>(n_rows, 1), c->stream));
+  CK(cudaMemsetAsync(job_cnt.p, 0, sizeof(uint32_t) * (n_jobs + 1), c->stream));
+
+  // ---- chunks: jobs grouped by k (stable), cut by windows, bitmap and genome limits
+  std::vector<uint32_t> by_k(n_jobs);
+  for (uint32_t j = 0; j < n_jobs; ++j) by_k[j] = j;
+  std::stable_sort(by_k.begin(), by_k.end(), [&](uint32_t x, uint32_t y) { return job_k[x] < job_k[y]; });
+  std::vector<std::unique_ptr<ChunkOut>> chunks;
+  uint64_t walked = 0, n_hits_total = 0;
+  size_t pos = 0;
+  while (pos < by_k.size()) {
+    const int k = job_k[by_k[pos]];
+    uint64_t n_codes = 1;
+    for (int t = 0; t < k; ++t) n_codes *= 20;
+    uint64_t max_jobs = std::max<uint64_t>(1, kChunkBitmapBytes * 8 / n_codes);
+    max_jobs = std::min<uint64_t>(max_jobs, PD_MAX_GENOMES / 2);
+    if (tuning && tuning->max_chunk_jobs) max_jobs = std::min<uint64_t>(max_jobs, tuning->max_chunk_jobs);
+    std::vector<uint32_t> cj;  // batch jobs of this chunk
+    uint64_t W = 0;
+    while (pos < by_k.size() && job_k[by_k[pos]] == k && cj.size() < max_jobs) {
+      const uint32_t j = by_k[pos];
+      const uint64_t w = windows_of(jobs[2 * j], k) + windows_of(jobs[2 * j + 1], k);
+      if (!cj.empty() && W + w > max_windows) break;
+      cj.push_back(j);
+      W += w;
+      ++pos;
+    }
+
+    // chunk dataset: genomes A0, B0, A1, B1, ...; segment = job within the chunk
+    std::unique_ptr<ChunkOut> C(new ChunkOut());
+    std::vector<uint32_t> genomes;
+    std::vector<uint32_t> seg;
+    for (uint32_t x = 0; x < cj.size(); ++x) {
+      genomes.push_back(jobs[2 * cj[x]]);
+      genomes.push_back(jobs[2 * cj[x] + 1]);
+      seg.push_back(x);
+      seg.push_back(x);
+    }
+    std::vector<int32_t> cgn(genomes.size() + 1, 0);
+    std::vector<int64_t> cg(1, 0);
+    std::vector<ByteRange> ranges;
+    bool contiguous = true;
+    for (size_t i = 0; i < genomes.size(); ++i) {
+      const uint32_t gi = genomes[i];
+      if (i && gi != genomes[i - 1] + 1) contiguous = false;
+      const int64_t r0 = hg[hgn[gi]], r1 = hg[hgn[gi + 1]];
+      ranges.push_back(ByteRange{(unsigned long long)r0, (unsigned long long)cg.back(), (unsigned long long)(r1 - r0)});
+      for (int32_t g = hgn[gi]; g < hgn[gi + 1]; ++g) cg.push_back(cg.back() + (hg[g + 1] - hg[g]));
+      cgn[i + 1] = cgn[i] + (int32_t)genes_of(gi);
+    }
+    const uint64_t chunk_res = (uint64_t)cg.back();
+    const uint32_t chunk_genes = (uint32_t)cgn.back();
+    Buf gathered, d_ranges;
+    const uint8_t* chunk_dev = res_dev;
+    if (chunk_res) {
+      if (contiguous) {
+        chunk_dev = res_dev + ranges[0].src;
+      } else {
+        ALLOC(gathered, chunk_res);
+        ALLOC(d_ranges, sizeof(ByteRange) * ranges.size());
+        CK(cudaMemcpyAsync(d_ranges.p, ranges.data(), sizeof(ByteRange) * ranges.size(), cudaMemcpyHostToDevice,
+                           c->stream));
+        PD_KLAUNCH("batch_gather",
+                   (k_gather_ranges<<<grid_of(ranges.size(), 1, 152u * 8u), 256, 0, c->stream>>>(
+                       res_dev, d_ranges.as<ByteRange>(), (uint32_t)ranges.size(), gathered.as<uint8_t>())));
+        chunk_dev = gathered.as<uint8_t>();
+      }
+    }
+    pd_profiles* Praw = nullptr;
+    pd_status st = build_profiles_impl(c, chunk_dev, chunk_res, cg.data(), chunk_genes, cgn.data(),
+                                       (uint32_t)genomes.size(), k, seg.data(), &Praw);
+    if (st != PD_OK) return st;
+    std::unique_ptr<pd_profiles> P(Praw);
+
+    // one all-pairs Best Hit pass and one BBH pass over every job of the chunk
+    pdg::QuerySet Q{};
+    Q.all_pairs = 1;
+    Q.order = P->view.order;
+    Q.q0 = 0;
+    Q.n_queries = chunk_genes;
+    C->hits.ctx = c;
+    C->hits.all_pairs = 1;
+    if ((st = run_hits(c, P.get(), Q, false, &C->hits, 1)) != PD_OK) return st;
+    walked += C->hits.walked;
+    n_hits_total += C->hits.n_hits;
+    pdg::BbhRows R{};
+    R.all_pairs = 1;
+    R.n_rows = C->hits.n_rows;
+    R.gene_genome = P->view.gene_genome;
+    R.row_off = C->hits.row_off.as<unsigned long long>();
+    R.row_len = C->hits.row_len.as<uint32_t>();
+    R.hit_b = C->hits.out_b.as<uint32_t>();
+    if ((st = bbh_impl(c, R, C->hits.out_b.n / sizeof(uint32_t), 0, 0, &C->bbh)) != PD_OK) return st;
+
+    for (uint32_t x = 0; x < cj.size(); ++x) {
+      ChunkJob J{};
+      J.job = cj[x];
+      J.a0 = (uint32_t)cgn[2 * x];
+      J.nA = (uint32_t)(cgn[2 * x + 1] - cgn[2 * x]);
+      J.b0 = (uint32_t)cgn[2 * x + 1];
+      J.nB = (uint32_t)(cgn[2 * x + 2] - cgn[2 * x + 1]);
+      J.row0 = row0[cj[x]];
+      C->jobs.push_back(J);
+    }
+    ALLOC(C->d_jobs, sizeof(ChunkJob) * C->jobs.size());
+    CK(cudaMemcpyAsync(C->d_jobs.p, C->jobs.data(), sizeof(ChunkJob) * C->jobs.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+    const uint32_t nj = (uint32_t)C->jobs.size();
+    PD_KLAUNCH("batch_rows_len", (k_rows_len<<<grid_of(nj, 1, 152u * 16u), 256, 0, c->stream>>>(
+                                      C->d_jobs.as<ChunkJob>(), nj, C->hits.row_len.as<uint32_t>(),
+                                      row_len.as<uint32_t>())));
+    PD_KLAUNCH("batch_bbh_runs", (k_bbh_runs<<<grid_of(nj, 128, 152u * 4u), 128, 0, c->stream>>>(
+                                      C->d_jobs.as<ChunkJob>(), nj, C->bbh.a.as<int32_t>(), (uint32_t)C->bbh.n,
+                                      job_cnt.as<uint32_t>())));
+    CK(cudaStreamSynchronize(c->stream));  // host staging vectors and the gather buffer are released next
+    chunks.push_back(std::move(C));
+  }
+
+  // ---- assemble: rows and BBH pairs in job order
+  CK(pdg::scan_u32_to_u64(&c->L, row_len.as<uint32_t>(), n_rows, B->row_ptr.as<unsigned long long>(), tmp.p,
+                          c->stream));
+  CK(pdg::scan_u32_to_u64(&c->L, job_cnt.as<uint32_t>(), n_jobs, B->job_ptr.as<unsigned long long>(), tmp.p,
+                          c->stream));
+  unsigned long long tot[2] = {0, 0};
+  CK(cudaMemcpyAsync(&tot[0], B->row_ptr.as<unsigned long long>() + n_rows, sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(&tot[1], B->job_ptr.as<unsigned long long>() + n_jobs, sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (tot[0] != n_hits_total) return fail(c, PD_ERR_INTERNAL, "batch Best Hit count mismatch");
+  ALLOC(B->cols, sizeof(int32_t) * std::max<unsigned long long>(tot[0], 1));
+  ALLOC(B->s, sizeof(uint32_t) * std::max<unsigned long long>(tot[0], 1));
+  ALLOC(B->a, sizeof(int32_t) * std::max<unsigned long long>(tot[1], 1));
+  ALLOC(B->b, sizeof(int32_t) * std::max<unsigned long long>(tot[1], 1));
+  for (auto& C : chunks) {
+    const uint32_t nj = (uint32_t)C->jobs.size();
+    PD_KLAUNCH("batch_rows_fill",
+               (k_rows_fill<<<grid_of(nj, 1, 152u * 16u), 256, 0, c->stream>>>(
+                   C->d_jobs.as<ChunkJob>(), nj, C->hits.row_off.as<unsigned long long>(),
+                   C->hits.row_len.as<uint32_t>(), C->hits.out_b.as<uint32_t>(), C->hits.out_s.as<uint32_t>(),
+                   B->row_ptr.as<unsigned long long>(), B->cols.as<int32_t>(), B->s.as<uint32_t>())));
+    PD_KLAUNCH("batch_bbh_fill", (k_bbh_fill<<<grid_of(nj, 1, 152u * 16u), 256, 0, c->stream>>>(
+                                      C->d_jobs.as<ChunkJob>(), nj, C->bbh.a.as<int32_t>(), C->bbh.b.as<int32_t>(),
+                                      B->job_ptr.as<unsigned long long>(), B->a.as<int32_t>(),
+                                      B->b.as<int32_t>())));
+  }
+  CK(cudaStreamSynchronize(c->stream));  // chunk results are released on return
+  pd_batch_info& in = B->info;
+  in.n_jobs = n_jobs;
+  in.n_chunks = (uint32_t)chunks.size();
+  in.n_rows = n_rows;
+  in.n_hits = tot[0];
+  in.n_bbh = tot[1];
+  in.postings_walked = walked;
+  *out = B.release();
+  return PD_OK;
+}
+
+}  // namespace
+
+PD_API pd_status pd_bbh_batch(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                              uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* jobs,
+                              const int32_t* job_k, uint32_t n_jobs, const pd_batch_tuning* tuning, pd_batch** out) {
+  if (!c || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    return batch_impl(c, residues, n_res, gene_ptr, n_genes, genome_ptr, n_genomes, jobs, job_k, n_jobs, tuning,
+                      out);
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_bbh_batch");
+  }
+}
+
+PD_API pd_status pd_batch_get_info(const pd_batch* B, pd_batch_info* info) {
+  if (!B || !info) return PD_ERR_ARG;
+  *info = B->info;
+  return PD_OK;
+}
+
+PD_API pd_status pd_batch_copy_hits(pd_ctx* c, const pd_batch* B, int64_t* row_ptr, int32_t* cols, uint32_t* s) {
+  if (!c || !B) return PD_ERR_ARG;
+  try {
+    CK(cudaSetDevice(c->device));
+    pd_status st;
+    if ((st = copy_out(c, row_ptr, B->row_ptr.p, sizeof(int64_t) * (B->info.n_rows + 1))) != PD_OK) return st;
+    if ((st = copy_out(c, cols, B->cols.p, sizeof(int32_t) * B->info.n_hits)) != PD_OK) return st;
+    if ((st = copy_out(c, s, B->s.p, sizeof(uint32_t) * B->info.n_hits)) != PD_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return PD_OK;
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_batch_copy_hits");
+  }
+}
+
+PD_API pd_status pd_batch_copy_bbh(pd_ctx* c, const pd_batch* B, int64_t* job_ptr, int32_t* a, int32_t* b) {
+  if (!c || !B) return PD_ERR_ARG;
+  try {
+    CK(cudaSetDevice(c->device));
+    pd_status st;
+    if ((st = copy_out(c, job_ptr, B->job_ptr.p, sizeof(int64_t) * (B->info.n_jobs + 1))) != PD_OK) return st;
+    if ((st = copy_out(c, a, B->a.p, sizeof(int32_t) * B->info.n_bbh)) != PD_OK) return st;
+    if ((st = copy_out(c, b, B->b.p, sizeof(int32_t) * B->info.n_bbh)) != PD_OK) return st;
+    CK(cudaStreamSynchronize(c->stream));
+    return PD_OK;
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_batch_copy_bbh");
+  }
+}
+
+PD_API void pd_batch_free(pd_batch* B) { delete B; }

@@ -239,7 +239,8 @@ cudaError_t scan_u32_to_u64(Launcher* L, const uint32_t* in, uint64_t n, unsigne
 
 // profiles (k_profiles.cu)
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
-                            unsigned long long* bitmap, DevErr* err, cudaStream_t s);
+                            unsigned long long* bitmap, const uint16_t* gene_genome,
+                            const unsigned long long* genome_code_base, DevErr* err, cudaStream_t s);
 // Outputs of the multiplicity-vector build.
 struct MvOut {
   uint32_t* mv_id;
@@ -249,6 +250,8 @@ struct MvOut {
   uint32_t* minhash;
   uint32_t cnt_bits, cnt_cap;
   DevErr* err;
+  const uint16_t* gene_genome;                 // genome of each gene
+  const unsigned long long* genome_code_base;  // per genome: segment * 20^k, or null (one segment)
 };
 // Table slots used for a gene with La windows (genes above 16384 slots use
 // global scratch of that many 64-bit slots, listed in long_genes).

@@ -50,6 +50,15 @@ class HitsInfo(C.Structure):
                 ("col_base", C.c_uint32), ("n_deferred", C.c_uint32), ("postings_walked", C.c_uint64)]
 
 
+class BatchTuning(C.Structure):
+    _fields_ = [("max_chunk_windows", C.c_uint64), ("max_chunk_jobs", C.c_uint32), ("reserved", C.c_uint32)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("n_jobs", C.c_uint32), ("n_chunks", C.c_uint32), ("n_rows", C.c_uint64), ("n_hits", C.c_uint64),
+                ("n_bbh", C.c_uint64), ("postings_walked", C.c_uint64)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -70,6 +79,8 @@ _SIGNATURES = [
     ("pd_ctx_reset_timing", C.c_int, [_P]),
     ("pd_choose_k", C.c_int, [C.c_uint64, C.c_int]),
     ("pd_build_profiles", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, C.c_int, _PP]),
+    ("pd_build_profiles_segmented", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, _P, C.c_int,
+                                              _PP]),
     ("pd_profiles_get_info", C.c_int, [_P, C.POINTER(ProfilesInfo)]),
     ("pd_profiles_copy_mv", C.c_int, [_P, _P, _P, _P, _P, _P]),
     ("pd_profiles_copy_index", C.c_int, [_P, _P, _P, _P, _P, _P]),
@@ -85,6 +96,12 @@ _SIGNATURES = [
     ("pd_bbh_count", C.c_uint64, [_P]),
     ("pd_bbh_free", None, [_P]),
     ("pd_summin_pairs", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _P, _P, _P, C.POINTER(C.c_uint64)]),
+    ("pd_bbh_batch", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, _P, _P, C.c_uint32,
+                               C.POINTER(BatchTuning), _PP]),
+    ("pd_batch_get_info", C.c_int, [_P, C.POINTER(BatchInfo)]),
+    ("pd_batch_copy_hits", C.c_int, [_P, _P, _P, _P, _P]),
+    ("pd_batch_copy_bbh", C.c_int, [_P, _P, _P, _P, _P]),
+    ("pd_batch_free", None, [_P]),
     ("pd_best_hits_noalloc", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _P, _P, _P, C.c_uint64,
                                        C.POINTER(C.c_uint64)]),
 ]
@@ -250,6 +267,10 @@ class BbhSet(_Handle):
     _free_name = "pd_bbh_free"
 
 
+class Batch(_Handle):
+    _free_name = "pd_batch_free"
+
+
 def pd_build_profiles(ctx: Ctx, residues, gene_ptr, genome_ptr, k: int) -> Profiles:
     """residues uint8[N], gene_ptr int64[G+1], genome_ptr int32[n+1]: host or device."""
     n_res = int(residues.shape[0])
@@ -259,6 +280,20 @@ def pd_build_profiles(ctx: Ctx, residues, gene_ptr, genome_ptr, k: int) -> Profi
     st = _lib.pd_build_profiles(ctx.handle, _ptr(residues), n_res, _ptr(gene_ptr), n_genes, _ptr(genome_ptr),
                                 n_genomes, int(k), C.byref(h))
     _check(ctx, st, "pd_build_profiles")
+    return Profiles(ctx, h)
+
+
+def pd_build_profiles_segmented(ctx: Ctx, residues, gene_ptr, genome_ptr, genome_seg, k: int) -> Profiles:
+    """pd_build_profiles with a segment per genome (genome_seg: host uint32[n]);
+    genomes of different segments share no k-mer."""
+    n_res = int(residues.shape[0])
+    n_genes = int(gene_ptr.shape[0]) - 1
+    n_genomes = int(genome_ptr.shape[0]) - 1
+    seg = np.ascontiguousarray(genome_seg, dtype=np.uint32)
+    h = C.c_void_p()
+    st = _lib.pd_build_profiles_segmented(ctx.handle, _ptr(residues), n_res, _ptr(gene_ptr), n_genes,
+                                          _ptr(genome_ptr), n_genomes, _ptr(seg), int(k), C.byref(h))
+    _check(ctx, st, "pd_build_profiles_segmented")
     return Profiles(ctx, h)
 
 
@@ -383,3 +418,61 @@ def pd_best_hits_noalloc(ctx: Ctx, prof: Profiles, gi: int, gj: int, row_ptr, co
     _check(ctx, _lib.pd_best_hits_noalloc(ctx.handle, prof.handle, int(gi), int(gj), _ptr(row_ptr), _ptr(cols),
                                           _ptr(s), cap, C.byref(n)), "pd_best_hits_noalloc")
     return int(n.value)
+
+
+def pd_bbh_batch(ctx: Ctx, residues, gene_ptr, genome_ptr, jobs, job_k, max_chunk_windows: int = 0,
+                 max_chunk_jobs: int = 0) -> Batch:
+    """Best Hits (both directions) and BBH of many genome-pair jobs: jobs is a
+    host array [n_jobs, 2] of genome indices, job_k the k of each job."""
+    n_res = int(residues.shape[0])
+    n_genes = int(gene_ptr.shape[0]) - 1
+    n_genomes = int(genome_ptr.shape[0]) - 1
+    jb = np.ascontiguousarray(jobs, dtype=np.uint32).reshape(-1)
+    kk = np.ascontiguousarray(job_k, dtype=np.int32)
+    if jb.shape[0] != 2 * kk.shape[0]:
+        raise ValueError("jobs must have two genome indices per entry of job_k")
+    tun = BatchTuning(int(max_chunk_windows), int(max_chunk_jobs), 0)
+    h = C.c_void_p()
+    st = _lib.pd_bbh_batch(ctx.handle, _ptr(residues), n_res, _ptr(gene_ptr), n_genes, _ptr(genome_ptr), n_genomes,
+                           _ptr(jb) if jb.size else None, _ptr(kk) if kk.size else None, int(kk.shape[0]),
+                           C.byref(tun), C.byref(h))
+    _check(ctx, st, "pd_bbh_batch")
+    return Batch(ctx, h)
+
+
+def pd_batch_get_info(batch: Batch) -> BatchInfo:
+    info = BatchInfo()
+    _check(batch.ctx, _lib.pd_batch_get_info(batch.handle, C.byref(info)), "pd_batch_get_info")
+    return info
+
+
+def pd_batch_copy_hits(ctx: Ctx, batch: Batch, row_ptr=None, cols=None, s=None):
+    """Best Hits of all jobs as one CSR (rows: genes of A then B per job;
+    columns local to the partner genome).  Without buffers returns host arrays."""
+    if row_ptr is None and cols is None and s is None:
+        info = pd_batch_get_info(batch)
+        row_ptr = np.zeros(info.n_rows + 1, np.int64)
+        cols = np.zeros(max(info.n_hits, 1), np.int32)
+        s = np.zeros(max(info.n_hits, 1), np.uint32)
+        _check(ctx, _lib.pd_batch_copy_hits(ctx.handle, batch.handle, _ptr(row_ptr), _ptr(cols), _ptr(s)),
+               "pd_batch_copy_hits")
+        return row_ptr, cols[:info.n_hits], s[:info.n_hits]
+    _check(ctx, _lib.pd_batch_copy_hits(ctx.handle, batch.handle, _ptr(row_ptr), _ptr(cols), _ptr(s)),
+           "pd_batch_copy_hits")
+    return None
+
+
+def pd_batch_copy_bbh(ctx: Ctx, batch: Batch, job_ptr=None, a=None, b=None):
+    """BBH pairs of all jobs: (job_ptr int64[n_jobs+1], pairs int32[n, 2]) with
+    a local in A and b local in B.  Without buffers returns host arrays."""
+    if job_ptr is None and a is None and b is None:
+        info = pd_batch_get_info(batch)
+        job_ptr = np.zeros(info.n_jobs + 1, np.int64)
+        a = np.zeros(max(info.n_bbh, 1), np.int32)
+        b = np.zeros(max(info.n_bbh, 1), np.int32)
+        _check(ctx, _lib.pd_batch_copy_bbh(ctx.handle, batch.handle, _ptr(job_ptr), _ptr(a), _ptr(b)),
+               "pd_batch_copy_bbh")
+        return job_ptr, np.stack([a[:info.n_bbh], b[:info.n_bbh]], axis=1)
+    _check(ctx, _lib.pd_batch_copy_bbh(ctx.handle, batch.handle, _ptr(job_ptr), _ptr(a), _ptr(b)),
+           "pd_batch_copy_bbh")
+    return None

@@ -162,7 +162,7 @@ def generate(
 ) -> Pangenome:
     """Draw a seeded pangenome.
 
-    genes_per_genome  ("fixed", m) or ("poisson", mean)
+    genes_per_genome  ("fixed", m), ("poisson", mean) or ("list", [m_0, m_1, ...])
     accessory_draw    if set, the fraction of *all* families each genome draws
                       (no core set; used by the 4-genome workload); otherwise
                       every genome holds all core families and fills up to its
@@ -186,6 +186,8 @@ def generate(
     for _ in range(n_genomes):
         if genes_per_genome[0] == "fixed":
             m = int(genes_per_genome[1])
+        elif genes_per_genome[0] == "list":
+            m = int(genes_per_genome[1][len(specs)])
         else:
             m = int(rng.poisson(genes_per_genome[1]))
         n_single = int(round(singleton_frac * m))
@@ -281,6 +283,76 @@ WORKLOADS = {
                         accessory_draw=None, subst_max=0.30, indel_max=0.05, paralog_frac=0.10,
                         singleton_frac=0.05, seed=3),
 }
+
+
+# ---------------------------------------------------------------------------
+# batches of independent genome-pair jobs
+# ---------------------------------------------------------------------------
+
+def _job_params(rng, n_jobs, genes=(500, 6000)):
+    """Per-job generator parameters of a batch: gene counts U[genes] per
+    genome (default U[500, 6000]), half of the jobs with log-normal lengths of median 300 aa and half
+    with median 900 aa, and the pan50x3000 mutation model; families scale with
+    the larger genome (4000 families per 3000 genes)."""
+    m = rng.integers(genes[0], genes[1] + 1, size=(n_jobs, 2))
+    long_len = np.zeros(n_jobs, dtype=bool)
+    long_len[rng.permutation(n_jobs)[: n_jobs // 2]] = True
+    seeds = rng.integers(0, 2**62, size=n_jobs)
+    out = []
+    for j in range(n_jobs):
+        median = 900 if long_len[j] else 300
+        out.append(dict(n_genomes=2, genes_per_genome=("list", [int(m[j, 0]), int(m[j, 1])]),
+                        n_families=int(np.ceil(int(m[j].max()) * 4 / 3)),
+                        length_dist=("lognormal", median, 0.5, 30, 2500), core_frac=0.4, accessory_draw=None,
+                        subst_max=0.30, indel_max=0.05, paralog_frac=0.10, singleton_frac=0.05,
+                        seed=int(seeds[j]), name=f"job{j}"))
+    return out
+
+
+def _generate_job(params):
+    return generate(**params)
+
+
+def concat(parts) -> Pangenome:
+    """Datasets one after the other (genome i of part p keeps its order)."""
+    res, gptr, gnm, fam = [], [np.zeros(1, np.int64)], [np.zeros(1, np.int64)], []
+    r0, g0 = 0, 0
+    for d in parts:
+        res.append(d.residues)
+        gptr.append(d.gene_ptr[1:] + r0)
+        gnm.append(d.genome_ptr[1:].astype(np.int64) + g0)
+        fam.append(d.family)
+        r0 += d.n_residues
+        g0 += d.n_genes
+    return Pangenome(
+        residues=np.concatenate(res) if res else np.zeros(0, np.uint8),
+        gene_ptr=np.concatenate(gptr).astype(np.int64),
+        genome_ptr=np.concatenate(gnm).astype(np.int32),
+        family=np.concatenate(fam) if fam else np.zeros(0, np.int32),
+        name="+".join(d.name for d in parts[:3]) + ("..." if len(parts) > 3 else ""),
+    )
+
+
+def job_batch(n_jobs: int = 2000, seed: int = 4, workers: int = 1, genes=(500, 6000)):
+    """A batch of independent genome-pair jobs: returns (dataset, jobs) where
+    job j compares genomes jobs[j, 0] = 2j and jobs[j, 1] = 2j+1 of the
+    dataset.  Each job is its own two-genome pangenome (own families) drawn
+    with the parameters of ``_job_params``; ``workers`` > 1 draws jobs in
+    parallel processes (spawned, so it is safe after CUDA initialisation).
+    ``genes`` is the range of genes per genome (smaller for quick tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    params = _job_params(rng, n_jobs, genes)
+    if workers > 1 and n_jobs > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.map(_generate_job, params, chunksize=max(1, n_jobs // (4 * workers)))
+    else:
+        parts = [_generate_job(p) for p in params]
+    ds = concat(parts)
+    ds.name = f"jobs{n_jobs}"
+    ds.params = dict(n_jobs=n_jobs, seed=seed)
+    jobs = np.stack([np.arange(0, 2 * n_jobs, 2), np.arange(1, 2 * n_jobs, 2)], axis=1).astype(np.uint32)
+    return ds, jobs
 
 
 def workload(name: str, **overrides) -> Pangenome:
