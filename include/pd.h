@@ -243,7 +243,7 @@ typedef struct pd_batch pd_batch;
  * jobs.  Zero fields take the defaults. */
 typedef struct {
   uint64_t max_chunk_windows; /* k-mer windows profiled together (default 2^29) */
-  uint32_t max_chunk_jobs;    /* jobs per chunk (default: as many as the 1 GiB
+  uint32_t max_chunk_jobs;    /* jobs per chunk (default: as many as the 256 MiB
                                  chunk dictionary bitmap holds at the job's k,
                                  at most PD_MAX_GENOMES / 2) */
   uint32_t reserved;
@@ -286,6 +286,81 @@ pd_status pd_batch_copy_hits(pd_ctx* ctx, const pd_batch* batch, int64_t* row_pt
  * or device pointers, NULL to skip. */
 pd_status pd_batch_copy_bbh(pd_ctx* ctx, const pd_batch* batch, int64_t* job_ptr, int32_t* a, int32_t* b);
 void pd_batch_free(pd_batch* batch);
+
+/* ---------------------------------------------------------------- served index */
+
+typedef struct pd_index pd_index;
+typedef struct pd_reply pd_reply;
+
+typedef struct {
+  uint64_t ticket;
+  int32_t status;             /* PD_OK, or the error that failed this request */
+  uint32_t snapshot_genomes;  /* resident genomes 0 .. snapshot_genomes-1 were compared */
+  uint32_t n_genes;           /* genes of the submitted genome (rows) */
+  uint32_t tick_requests;     /* requests that shared this request's launches */
+  uint64_t n_hits;            /* Best Hit entries */
+  uint64_t n_bbh;             /* BBH pairs */
+  int64_t t_submit_ns, t_start_ns, t_done_ns; /* steady-clock stamps: submitted, its tick began, answered */
+} pd_reply_info;
+
+typedef struct {
+  int k;
+  uint32_t n_genomes;         /* resident genomes (initial + answered requests) */
+  uint64_t n_genes;
+  uint32_t queued;            /* requests waiting for admission */
+  uint32_t max_tick_requests; /* most requests answered by one tick */
+  uint64_t device_bytes;      /* resident residues + index */
+  uint64_t budget;
+  uint64_t ticks;             /* launch sequences run */
+  uint64_t requests_done;
+} pd_index_info;
+
+/* Served form: a pangenome index kept on the device, answering incoming
+ * genomes.  The index starts from the dataset given here (offsets as in
+ * pd_build_profiles; residues host or device) at a fixed k (the k rule of
+ * Eq. (4) is applied by the caller, on the resident set, once).  A request
+ * (pd_index_submit) is one genome: its answer holds the Best Hits (Eq. (8))
+ * of each of its genes in every genome resident when it was submitted, and
+ * its Bidirectional Best Hits (Eq. (9)) with those genomes; after answering,
+ * the genome becomes resident (genome id = n_genomes at that moment, genes
+ * appended in order).
+ * A worker thread of the library admits queued requests in arrival order while
+ * its estimate of device memory (resident residues and index, the rebuild and
+ * the tick's outputs) stays within hbm_budget bytes, and answers all admitted
+ * requests with one launch sequence (continuous batching).  A request's answer
+ * depends only on its genome and its snapshot, not on the requests that
+ * shared its launches.  Work runs on a stream and memory pool of the index's
+ * own; ctx supplies the device and receives creation errors. */
+pd_status pd_index_create(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                          uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
+                          uint64_t hbm_budget, pd_index** out);
+/* Queue one genome (HOST buffers, copied before return): residues and its
+ * gene_ptr (n_genes+1 int64 from 0 to n_res).  *ticket identifies the request.
+ * Errors: PD_ERR_ARG (malformed), PD_ERR_GENE_TOO_LONG, PD_ERR_BUDGET (this
+ * genome cannot fit the budget next to the resident index), PD_ERR_BUSY (the
+ * index would exceed PD_MAX_GENOMES). */
+pd_status pd_index_submit(pd_index* index, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                          uint32_t n_genes, uint64_t* ticket);
+/* Wait up to wait_ms (negative: no limit) for a request's answer; on PD_OK
+ * *out receives it (the caller frees it with pd_reply_free); PD_ERR_TIMEOUT if
+ * it is not ready.  Each answer is returned once. */
+pd_status pd_index_poll(pd_index* index, uint64_t ticket, int wait_ms, pd_reply** out);
+pd_status pd_index_get_info(pd_index* index, pd_index_info* info);
+/* genome_ptr of the first n_genomes resident genomes (n_genomes+1 int32, host). */
+pd_status pd_index_genome_ptr(pd_index* index, uint32_t n_genomes, int32_t* genome_ptr);
+/* Stops the worker (after its current tick) and frees the index; requests
+ * still queued are dropped. */
+void pd_index_free(pd_index* index);
+
+pd_status pd_reply_get_info(const pd_reply* reply, pd_reply_info* info);
+const char* pd_reply_error(const pd_reply* reply);
+/* Answer arrays (HOST pointers, NULL to skip): row_ptr n_genes+1 int64; cols
+ * n_hits int32 resident gene ids; s n_hits uint32 sum-min; bbh_a n_bbh int32
+ * gene of the submitted genome; bbh_b n_bbh int32 resident gene id.  Rows and
+ * pairs ascending.  Returns the request's status if it failed. */
+pd_status pd_reply_copy(const pd_reply* reply, int64_t* row_ptr, int32_t* cols, uint32_t* s, int32_t* bbh_a,
+                        int32_t* bbh_b);
+void pd_reply_free(pd_reply* reply);
 
 /* ---------------------------------------------------------------- no allocation */
 

@@ -49,14 +49,15 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 __global__ void __launch_bounds__(kEncThreads)
     k_encode_mark(const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr, uint32_t n_genes, int k,
                   unsigned long long* __restrict__ bitmap, const uint16_t* __restrict__ gene_genome,
-                  const unsigned long long* __restrict__ genome_code_base, DevErr* err) {
+                  const unsigned long long* __restrict__ genome_code_base, const int64_t* __restrict__ gene_src,
+                  DevErr* err) {
   __shared__ uint8_t lut[256];
   init_letter_table(lut);
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_genes; g += warps) {
-    const int64_t r0 = gene_ptr[g];
-    const uint32_t len = (uint32_t)(gene_ptr[g + 1] - r0);
+    const int64_t r0 = gene_src ? gene_src[g] : gene_ptr[g];
+    const uint32_t len = (uint32_t)(gene_ptr[g + 1] - gene_ptr[g]);
     const uint8_t* s = res + r0;
     const unsigned long long base = genome_code_base ? genome_code_base[gene_genome[g]] : 0ull;
     for (uint32_t p = lane; p < len; p += 32) {
@@ -102,7 +103,7 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
   constexpr unsigned long long kFree = ~0ull;
   const uint32_t off = win_off[g];
   const uint32_t La = win_off[g + 1] - off;
-  const uint8_t* s = res + gene_ptr[g];
+  const uint8_t* s = res + (M.gene_src ? M.gene_src[g] : gene_ptr[g]);
   const unsigned long long base = M.genome_code_base ? M.genome_code_base[M.gene_genome[g]] : 0ull;
   for (uint32_t h = threadIdx.x; h < cap; h += blockDim.x) table[h] = kFree;
   __syncthreads();
@@ -353,10 +354,12 @@ unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
 
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
                             unsigned long long* bitmap, const uint16_t* gene_genome,
-                            const unsigned long long* genome_code_base, DevErr* err, cudaStream_t s) {
+                            const unsigned long long* genome_code_base, const int64_t* gene_src, DevErr* err,
+                            cudaStream_t s) {
   const unsigned grid = grid_for((uint64_t)n_genes * 32, kEncThreads, 152u * 16u);
   PD_LAUNCH(L, "encode_mark", k_encode_mark<<<grid, kEncThreads, 0, s>>>(res, gene_ptr, n_genes, k, bitmap,
-                                                                        gene_genome, genome_code_base, err));
+                                                                        gene_genome, genome_code_base, gene_src,
+                                                                        err));
   return cudaSuccess;
 }
 

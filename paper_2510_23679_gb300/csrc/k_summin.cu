@@ -21,6 +21,10 @@
 //      table is clean for the next query.  Each hit is written at its rank
 //      among the query's hits (ascending gene): rows come out sorted without a
 //      sorting network.
+// Served queries (new genomes against a resident set) may limit the targets
+// to genes below a bound, and may also keep each target's best ratio over the
+// query's genome in global memory (the reverse-direction maximum needed for
+// the mutual check of Eq. (9)).
 // The similarity matrix S_ij is never materialised: only pairs sharing a
 // k-mer are touched.  A query whose insertions probe too far (a nearly full
 // table), or whose Best Hit list does not fit, is deferred to the next tier:
@@ -183,7 +187,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
   unsigned long long* out = tb.out;
   const uint32_t mask = tb.cap - 1u;
   // ---- query gene, its output row and its targets
-  uint32_t a, row, own0 = 0, own1 = 0;
+  uint32_t a, row, own0 = 0, own1 = 0, tend = 0xFFFFFFFFu, col = 0;
   unsigned long long key_lo = 0, key_hi = 0;
   if (Q.all_pairs) {
     a = Q.order ? Q.order[qi] : Q.q0 + qi;
@@ -191,6 +195,8 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
     const uint32_t gg = P.gene_genome[a];
     own0 = (uint32_t)P.genome_ptr[gg];
     own1 = (uint32_t)P.genome_ptr[gg + 1];
+    if (Q.tgt_end) tend = Q.tgt_end[gg];
+    col = gg - Q.col_genome0;
   } else {
     uint32_t tlo, thi;
     if (qi < Q.nA) {
@@ -329,9 +335,11 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
       for (uint32_t u = tid; u < n_occ; u += kThreads) {
         uint32_t b, s;
         acc.get(tb.used[u], &b, &s);
-        if (Q.all_pairs && b >= own0 && b < own1) continue;  // same genome: not a target
+        if (Q.all_pairs && ((b >= own0 && b < own1) || b >= tend)) continue;  // not a target
         const uint32_t gi = P.ginfo[b];
-        best_update(&best[Q.all_pairs ? (gi >> 16) : 0u], s, La_a + (gi & 0xFFFFu) - s);
+        const uint32_t den = La_a + (gi & 0xFFFFu) - s;
+        best_update(&best[Q.all_pairs ? (gi >> 16) : 0u], s, den);
+        if (Q.colbest) best_update(&Q.colbest[(size_t)b * Q.col_stride + col], s, den);
       }
       __syncthreads();
       for (uint32_t u = tid; u < n_occ; u += kThreads) {
@@ -340,7 +348,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
         acc.get(h, &b, &s);
         const uint32_t gi = P.ginfo[b];
         const unsigned long long bv = best[Q.all_pairs ? (gi >> 16) : 0u];
-        if (!(Q.all_pairs && b >= own0 && b < own1) &&
+        if (!(Q.all_pairs && ((b >= own0 && b < own1) || b >= tend)) &&
             ratio_equal(s, La_a + (gi & 0xFFFFu) - s, (uint32_t)(bv >> 32), (uint32_t)bv)) {
           const uint32_t slot = atomicAdd(&sh->n_out, 1u);
           if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | s;

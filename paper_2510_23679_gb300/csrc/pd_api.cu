@@ -219,7 +219,7 @@ static constexpr uint64_t kMaxBitmapBytes = (uint64_t)4 << 30;
 
 pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                                      uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
-                                     const uint32_t* genome_seg, pd_profiles** out) {
+                                     const uint32_t* genome_seg, pd_profiles** out, const int64_t* gene_src) {
   if (k < 1 || k > PD_MAX_K) return fail(c, PD_ERR_K_RANGE, "k must be in [1, " + std::to_string(PD_MAX_K) + "]");
   if (!gene_ptr || !genome_ptr || (n_res > 0 && !residues))
     return fail(c, PD_ERR_ARG, "null residues, gene_ptr or genome_ptr");
@@ -235,7 +235,8 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   CK(cudaMemcpyAsync(hg.data(), gene_ptr, sizeof(int64_t) * (n_genes + 1), cudaMemcpyDefault, c->stream));
   CK(cudaMemcpyAsync(hgn.data(), genome_ptr, sizeof(int32_t) * (n_genomes + 1), cudaMemcpyDefault, c->stream));
   if (gp_dev || gn_dev) CK(cudaStreamSynchronize(c->stream));
-  if (hg[0] != 0 || (uint64_t)hg[n_genes] != n_res) return fail(c, PD_ERR_ARG, "gene_ptr must run from 0 to n_res");
+  if (hg[0] != 0 || (!gene_src && (uint64_t)hg[n_genes] != n_res))
+    return fail(c, PD_ERR_ARG, "gene_ptr must run from 0 to n_res");
   if (hgn[0] != 0 || (uint32_t)hgn[n_genomes] != n_genes)
     return fail(c, PD_ERR_ARG, "genome_ptr must run from 0 to n_genes");
   for (uint32_t i = 0; i < n_genomes; ++i)
@@ -330,8 +331,8 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   CK(cudaMemsetAsync(P->bitmap.p, 0, sizeof(unsigned long long) * n_words, c->stream));
   if (n_genes)
     CK(pdg::run_encode_mark(L, res_dev, gp_devp, n_genes, k, P->bitmap.as<unsigned long long>(),
-                            P->gene_genome.as<uint16_t>(), d_code_base.as<unsigned long long>(), c->d_err,
-                            c->stream));
+                            P->gene_genome.as<uint16_t>(), d_code_base.as<unsigned long long>(), gene_src,
+                            c->d_err, c->stream));
   const uint32_t kOrderShift = 16;  // 65536 min-hash buckets
   const uint64_t n_order_b = (uint64_t)1 << (32 - kOrderShift);
   ALLOC(tmp, pdg::scan_temp_bytes(std::max<uint64_t>(std::max<uint64_t>(n_words, n_order_b), 24577)) + 64);
@@ -382,6 +383,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   M.err = c->d_err;
   M.gene_genome = P->gene_genome.as<uint16_t>();
   M.genome_code_base = d_code_base.as<unsigned long long>();
+  M.gene_src = gene_src;
   if (n_genes)
     CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
                          P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), M,

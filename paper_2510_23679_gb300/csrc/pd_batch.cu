@@ -15,8 +15,8 @@
 //      with columns made local to the partner genome; BBH pairs likewise with
 //      one scan over the jobs.
 //
-// A chunk's genomes are read in place when they are consecutive in the input;
-// otherwise their residues are gathered into one contiguous buffer first.
+// Genes are read in place from the input residues (a per-gene source offset),
+// so a chunk's genomes need not be consecutive in the input.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,11 +40,8 @@ struct pd_batch {
 namespace {
 
 constexpr uint64_t kDefaultChunkWindows = 1ull << 29;
-constexpr uint64_t kChunkBitmapBytes = 1ull << 30;
-
-struct ByteRange {
-  unsigned long long src, dst, len;
-};
+// Dictionary bitmap per chunk: small enough that its random marks mostly hit L2.
+constexpr uint64_t kChunkBitmapBytes = 256ull << 20;
 
 // One job of a chunk: where its genes sit in the chunk and in the batch.
 struct ChunkJob {
@@ -54,14 +51,6 @@ struct ChunkJob {
   uint32_t bbh_lo;     // first BBH pair of the job in the chunk's pair list (device-written)
   unsigned long long row0;  // first batch row of the job
 };
-
-__global__ void k_gather_ranges(const uint8_t* __restrict__ src, const ByteRange* __restrict__ ranges, uint32_t n,
-                                uint8_t* __restrict__ dst) {
-  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
-    const ByteRange r = ranges[i];
-    for (unsigned long long p = threadIdx.x; p < r.len; p += blockDim.x) dst[r.dst + p] = src[r.src + p];
-  }
-}
 
 // Row lengths of a chunk's Best Hits into batch row order.
 __global__ void k_rows_len(const ChunkJob* __restrict__ jobs, uint32_t n_jobs, const uint32_t* __restrict__ row_len,
@@ -251,39 +240,25 @@ pd_status batch_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const i
       seg.push_back(x);
       seg.push_back(x);
     }
+    // chunk gene lengths (CSR) and where each gene starts in the input
     std::vector<int32_t> cgn(genomes.size() + 1, 0);
-    std::vector<int64_t> cg(1, 0);
-    std::vector<ByteRange> ranges;
-    bool contiguous = true;
+    std::vector<int64_t> cg(1, 0), src;
     for (size_t i = 0; i < genomes.size(); ++i) {
       const uint32_t gi = genomes[i];
-      if (i && gi != genomes[i - 1] + 1) contiguous = false;
-      const int64_t r0 = hg[hgn[gi]], r1 = hg[hgn[gi + 1]];
-      ranges.push_back(ByteRange{(unsigned long long)r0, (unsigned long long)cg.back(), (unsigned long long)(r1 - r0)});
-      for (int32_t g = hgn[gi]; g < hgn[gi + 1]; ++g) cg.push_back(cg.back() + (hg[g + 1] - hg[g]));
+      for (int32_t g = hgn[gi]; g < hgn[gi + 1]; ++g) {
+        cg.push_back(cg.back() + (hg[g + 1] - hg[g]));
+        src.push_back(hg[g]);
+      }
       cgn[i + 1] = cgn[i] + (int32_t)genes_of(gi);
     }
-    const uint64_t chunk_res = (uint64_t)cg.back();
     const uint32_t chunk_genes = (uint32_t)cgn.back();
-    Buf gathered, d_ranges;
-    const uint8_t* chunk_dev = res_dev;
-    if (chunk_res) {
-      if (contiguous) {
-        chunk_dev = res_dev + ranges[0].src;
-      } else {
-        ALLOC(gathered, chunk_res);
-        ALLOC(d_ranges, sizeof(ByteRange) * ranges.size());
-        CK(cudaMemcpyAsync(d_ranges.p, ranges.data(), sizeof(ByteRange) * ranges.size(), cudaMemcpyHostToDevice,
-                           c->stream));
-        PD_KLAUNCH("batch_gather",
-                   (k_gather_ranges<<<grid_of(ranges.size(), 1, 152u * 8u), 256, 0, c->stream>>>(
-                       res_dev, d_ranges.as<ByteRange>(), (uint32_t)ranges.size(), gathered.as<uint8_t>())));
-        chunk_dev = gathered.as<uint8_t>();
-      }
-    }
+    Buf d_src;
+    ALLOC(d_src, sizeof(int64_t) * std::max<size_t>(src.size(), 1));
+    if (!src.empty())
+      CK(cudaMemcpyAsync(d_src.p, src.data(), sizeof(int64_t) * src.size(), cudaMemcpyHostToDevice, c->stream));
     pd_profiles* Praw = nullptr;
-    pd_status st = build_profiles_impl(c, chunk_dev, chunk_res, cg.data(), chunk_genes, cgn.data(),
-                                       (uint32_t)genomes.size(), k, seg.data(), &Praw);
+    pd_status st = build_profiles_impl(c, res_dev, (uint64_t)cg.back(), cg.data(), chunk_genes, cgn.data(),
+                                       (uint32_t)genomes.size(), k, seg.data(), &Praw, d_src.as<int64_t>());
     if (st != PD_OK) return st;
     std::unique_ptr<pd_profiles> P(Praw);
 
@@ -327,7 +302,7 @@ pd_status batch_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const i
     PD_KLAUNCH("batch_bbh_runs", (k_bbh_runs<<<grid_of(nj, 128, 152u * 4u), 128, 0, c->stream>>>(
                                       C->d_jobs.as<ChunkJob>(), nj, C->bbh.a.as<int32_t>(), (uint32_t)C->bbh.n,
                                       job_cnt.as<uint32_t>())));
-    CK(cudaStreamSynchronize(c->stream));  // host staging vectors and the gather buffer are released next
+    CK(cudaStreamSynchronize(c->stream));  // host staging vectors and the source offsets are released next
     chunks.push_back(std::move(C));
   }
 

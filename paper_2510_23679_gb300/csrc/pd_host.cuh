@@ -47,6 +47,8 @@ struct pd_ctx {
   pdg::Launcher L{nullptr};
   pdg::DevErr* d_err = nullptr;  // device error block
   pdg::DevErr* h_err = nullptr;  // pinned host mirror
+  cudaMemPool_t pool = nullptr;  // without hooks: allocate from this pool (null: the device's default pool)
+  uint64_t pool_bytes = 0;       // bytes currently allocated through this context (pool allocations only)
 };
 
 // ------------------------------------------------------------------ helpers
@@ -97,6 +99,13 @@ struct Buf {
     n = (std::max<size_t>(bytes, 16) + 255) & ~(size_t)255;
     if (c->alloc) {
       p = c->alloc(n, (void*)c->stream, c->user);
+    } else if (c->pool) {
+      if (cudaMallocFromPoolAsync(&p, n, c->pool, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+      } else {
+        c->pool_bytes += n;
+      }
     } else if (cudaMallocAsync(&p, n, c->stream) != cudaSuccess) {
       cudaGetLastError();
       p = nullptr;
@@ -105,8 +114,12 @@ struct Buf {
   }
   void release() {
     if (p && c) {
-      if (c->free_fn) c->free_fn(p, n, (void*)c->stream, c->user);
-      else cudaFreeAsync(p, c->stream);
+      if (c->free_fn) {
+        c->free_fn(p, n, (void*)c->stream, c->user);
+      } else {
+        cudaFreeAsync(p, c->stream);
+        if (c->pool) c->pool_bytes -= n;
+      }
     }
     p = nullptr;
   }
@@ -204,10 +217,12 @@ struct pd_bbh_set {
 namespace pdh {
 
 // Profiles of a dataset; genome_seg (host, per genome, or null) gives each
-// segment its own k-mer namespace.
+// segment its own k-mer namespace.  gene_src (device, per gene, or null):
+// gene g starts at residues + gene_src[g] instead of residues + gene_ptr[g];
+// gene_ptr then gives only the lengths, and residues must be a device pointer.
 pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                               uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
-                              const uint32_t* genome_seg, pd_profiles** out);
+                              const uint32_t* genome_seg, pd_profiles** out, const int64_t* gene_src = nullptr);
 // Sum-min + Best Hits of the query set Q into H (all tiers, output sized
 // exactly).  genomes_per_query (0 = n_genomes - 1) bounds the genomes one
 // query can hit; it only sizes the first output allocation.

@@ -186,6 +186,14 @@ struct QuerySet {
   uint32_t q0, n_queries;
   uint32_t qa0, nA, ta0, ta1;
   uint32_t qb0, tb0, tb1;
+  // Served queries (all-pairs form; null = off).  tgt_end[genome of the
+  // query]: only genes below it are targets.  colbest: for every target gene
+  // b and query genome g, the best (s << 32 | den) of b over the genes of g,
+  // at colbest[b * col_stride + (g - col_genome0)] (the reverse-direction
+  // Best Hit maximum, kept by compare-and-swap).
+  const uint32_t* tgt_end;
+  unsigned long long* colbest;
+  uint32_t col_genome0, col_stride;
 };
 
 struct HitsOut {
@@ -240,7 +248,8 @@ cudaError_t scan_u32_to_u64(Launcher* L, const uint32_t* in, uint64_t n, unsigne
 // profiles (k_profiles.cu)
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
                             unsigned long long* bitmap, const uint16_t* gene_genome,
-                            const unsigned long long* genome_code_base, DevErr* err, cudaStream_t s);
+                            const unsigned long long* genome_code_base, const int64_t* gene_src, DevErr* err,
+                            cudaStream_t s);
 // Outputs of the multiplicity-vector build.
 struct MvOut {
   uint32_t* mv_id;
@@ -252,6 +261,7 @@ struct MvOut {
   DevErr* err;
   const uint16_t* gene_genome;                 // genome of each gene
   const unsigned long long* genome_code_base;  // per genome: segment * 20^k, or null (one segment)
+  const int64_t* gene_src;                     // per gene: first residue, or null (gene_ptr[g])
 };
 // Table slots used for a gene with La windows (genes above 16384 slots use
 // global scratch of that many 64-bit slots, listed in long_genes).

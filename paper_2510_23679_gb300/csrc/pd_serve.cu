@@ -1,0 +1,604 @@
+// pd_serve.cu -- served form: a pangenome index resident on the device and a
+// request loop that compares incoming genomes with it (pd_index_* in pd.h).
+//
+// Each incoming genome X asks for Best Hits BH(a, G_j) of its genes a in every
+// resident genome G_j (Eq. (8)) and for its Bidirectional Best Hits with the
+// resident genes (Eq. (9)); X then becomes resident itself.
+//
+// Request loop (one worker thread, one stream, one memory pool):
+//   * submit copies the genome to the host queue and stamps it with the
+//     resident set it will be compared with (its snapshot: the genomes
+//     resident at submission);
+//   * continuous batching: whenever the GPU is free the worker admits queued
+//     requests in arrival order while the HBM estimate of the tick stays within
+//     the budget, and runs them together -- one profile build over the resident
+//     genomes plus the tick's genomes (this build is also the insertion: the
+//     tick's genomes are resident afterwards), ONE sum-min / Best Hit launch
+//     sequence over the genes of every admitted genome, one mutual-check pass;
+//   * each query is limited to the genes of its snapshot, so a result does not
+//     depend on which other requests shared its tick;
+//   * the reverse direction of Eq. (9) -- is a among the Best Hits of b in X?
+//     -- needs, for every resident gene b, its best ratio over the genes of X.
+//     The sum-min kernel keeps that maximum per (b, X) in global memory while
+//     it selects the forward Best Hits; a pair (a, b) is a BBH when b is a
+//     forward Best Hit of a and the ratio of (a, b) equals b's maximum over X.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "pd.h"
+#include "pd_host.cuh"
+#include "pd_internal.cuh"
+
+using namespace pdh;
+
+struct pd_reply {
+  pd_reply_info info{};
+  std::string err;
+  std::vector<int64_t> row_ptr;
+  std::vector<int32_t> cols;
+  std::vector<uint32_t> s;
+  std::vector<int32_t> bbh_a, bbh_b;
+};
+
+namespace {
+
+int64_t now_ns() {
+  return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Request {
+  uint64_t ticket = 0;
+  std::vector<uint8_t> res;
+  std::vector<int64_t> gene_ptr;  // local CSR, n_genes + 1 entries
+  uint32_t snapshot = 0;          // resident genomes this request is compared with
+  uint64_t windows = 0;
+  int64_t t_submit = 0;
+};
+
+// Device bytes of one tick beyond the resident data: the profile build over
+// W windows and G genes, the Best Hit output and the reverse-maximum table.
+uint64_t tick_bytes(uint64_t W, uint64_t G, uint64_t tick_genes, uint64_t res_genes, uint64_t res_genomes,
+                    uint64_t tick_genomes) {
+  return 48 * W + 64 * G + 8 * res_genes * tick_genomes + 24 * tick_genes * (res_genomes + 1) + (64ull << 20);
+}
+
+// Mutual check of the served Best Hits: warp per row of the tick.
+__global__ void k_serve_bbh_count(uint32_t n_rows, uint32_t g0, const unsigned long long* __restrict__ row_ptr,
+                                  const int32_t* __restrict__ cols, const uint32_t* __restrict__ s,
+                                  const uint32_t* __restrict__ La, const uint16_t* __restrict__ gene_genome,
+                                  uint32_t col_genome0, uint32_t stride,
+                                  const unsigned long long* __restrict__ colbest, uint8_t* __restrict__ flag,
+                                  uint32_t* __restrict__ cnt) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += warps) {
+    const uint32_t a = g0 + r;
+    const uint32_t x = gene_genome[a] - col_genome0;
+    const unsigned long long lo = row_ptr[r], hi = row_ptr[r + 1];
+    uint32_t n = 0;
+    for (unsigned long long i = lo + lane; i < hi; i += 32) {
+      const uint32_t b = (uint32_t)cols[i], sv = s[i];
+      const unsigned long long cb = colbest[(size_t)b * stride + x];
+      const bool f = pdg::ratio_equal(sv, La[a] + La[b] - sv, (uint32_t)(cb >> 32), (uint32_t)cb);
+      flag[i] = f ? 1 : 0;
+      n += f ? 1u : 0u;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
+    if (lane == 0) cnt[r] = n;
+  }
+}
+
+__global__ void k_serve_bbh_write(uint32_t n_rows, const unsigned long long* __restrict__ row_ptr,
+                                  const int32_t* __restrict__ cols, const uint8_t* __restrict__ flag,
+                                  const uint32_t* __restrict__ start, int32_t* __restrict__ out_a,
+                                  int32_t* __restrict__ out_b) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += warps) {
+    const unsigned long long lo = row_ptr[r], hi = row_ptr[r + 1];
+    uint32_t pos = start[r];
+    for (unsigned long long i0 = lo; i0 < hi; i0 += 32) {
+      const unsigned long long i = i0 + lane;
+      const bool f = i < hi && flag[i];
+      const uint32_t m = __ballot_sync(0xffffffffu, f);
+      if (f) {
+        const uint32_t p = pos + __popc(m & ((1u << lane) - 1u));
+        out_a[p] = (int32_t)r;
+        out_b[p] = cols[i];
+      }
+      pos += __popc(m);
+    }
+  }
+}
+
+__global__ void k_iota(uint32_t* out, uint32_t n, uint32_t base) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = base + i;
+}
+
+unsigned grid_of(uint64_t items, unsigned per_block, unsigned cap) {
+  uint64_t b = (items + per_block - 1) / per_block;
+  return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(b, cap));
+}
+
+#define PD_KLAUNCH(name, ...)               \
+  do {                                      \
+    CK(pdg::launch_begin(&c->L, name));     \
+    __VA_ARGS__;                            \
+    CK(pdg::launch_end(&c->L, name));       \
+  } while (0)
+
+uint64_t windows_of(const std::vector<int64_t>& gp, size_t g0, size_t g1, int k) {
+  uint64_t w = 0;
+  for (size_t g = g0; g < g1; ++g) {
+    const int64_t len = gp[g + 1] - gp[g];
+    if (len >= k) w += (uint64_t)(len - k + 1);
+  }
+  return w;
+}
+
+}  // namespace
+
+struct pd_index {
+  pd_ctx* c = nullptr;  // worker context: own stream and memory pool
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  int device = 0, k = 0;
+  uint64_t budget = 0;
+  uint32_t max_tick = 64;
+  // resident data (owned by the worker once it runs)
+  Buf res;
+  uint64_t res_used = 0;
+  uint64_t res_windows = 0;
+  std::vector<int64_t> gene_ptr;
+  std::vector<int32_t> genome_ptr;
+  std::unique_ptr<pd_profiles> P;
+  // shared with the API threads
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<Request> queue;
+  std::map<uint64_t, std::unique_ptr<pd_reply>> done;
+  uint64_t next_ticket = 1;
+  uint32_t committed = 0;
+  uint64_t committed_windows = 0;
+  uint64_t committed_genes = 0;
+  uint64_t committed_res = 0;  // resident residues (res_used as of the last commit)
+  std::vector<int32_t> committed_genome_ptr;
+  uint64_t resident_bytes = 0;
+  bool stop = false;
+  std::thread worker;
+  pd_index_info stats{};
+
+  ~pd_index() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    cv_work.notify_all();
+    if (worker.joinable()) worker.join();
+    if (c) {
+      cudaSetDevice(device);
+      P.reset();
+      res.release();
+      cudaStreamSynchronize(stream);
+      pd_ctx_destroy(c);
+    }
+    if (pool) cudaMemPoolDestroy(pool);
+    if (stream) cudaStreamDestroy(stream);
+  }
+};
+
+namespace {
+
+// Appends the genomes of `tick` to the resident data, rebuilds the index over
+// all of them and answers every request of the tick.
+pd_status run_tick(pd_index* I, std::vector<Request>& tick, std::vector<std::unique_ptr<pd_reply>>& replies) {
+  pd_ctx* c = I->c;
+  const uint32_t n_tick = (uint32_t)tick.size();
+  const uint32_t g_res = (uint32_t)I->genome_ptr.size() - 1;       // resident genomes
+  const uint32_t G_res = (uint32_t)I->gene_ptr.size() - 1;         // resident genes
+  if (g_res + n_tick > PD_MAX_GENOMES) return fail(c, PD_ERR_BUDGET, "the index holds at most PD_MAX_GENOMES genomes");
+  uint64_t add = 0;
+  for (auto& r : tick) add += r.res.size();
+  // ---- residues: grow the resident buffer (doubling), then append
+  if (I->res_used + add > I->res.n || !I->res.p) {
+    Buf bigger;
+    const uint64_t want = std::max<uint64_t>(I->res_used + add, std::max<uint64_t>(2 * I->res.n, 1 << 20));
+    ALLOC(bigger, want);
+    if (I->res_used) CK(cudaMemcpyAsync(bigger.p, I->res.p, I->res_used, cudaMemcpyDeviceToDevice, c->stream));
+    I->res = std::move(bigger);
+  }
+  uint64_t off = I->res_used;
+  for (auto& r : tick) {
+    if (!r.res.empty())
+      CK(cudaMemcpyAsync(I->res.as<uint8_t>() + off, r.res.data(), r.res.size(), cudaMemcpyHostToDevice, c->stream));
+    for (size_t g = 1; g < r.gene_ptr.size(); ++g) I->gene_ptr.push_back((int64_t)off + r.gene_ptr[g]);
+    I->genome_ptr.push_back((int32_t)(I->gene_ptr.size() - 1));
+    off += r.res.size();
+  }
+  I->res_used = off;
+  const uint32_t G = (uint32_t)I->gene_ptr.size() - 1, n_genomes = g_res + n_tick;
+  const uint32_t n_q = G - G_res;
+
+  // ---- the index over resident + tick genomes (the insertion)
+  I->P.reset();
+  pd_profiles* Praw = nullptr;
+  pd_status st = build_profiles_impl(c, I->res.as<uint8_t>(), I->res_used, I->gene_ptr.data(), G,
+                                     I->genome_ptr.data(), n_genomes, I->k, nullptr, &Praw);
+  if (st != PD_OK) return st;
+  std::unique_ptr<pd_profiles> P(Praw);
+
+  // ---- queries: every gene of the tick against its snapshot
+  std::vector<uint32_t> tgt_end(n_genomes, 0);
+  for (uint32_t x = 0; x < n_tick; ++x) tgt_end[g_res + x] = (uint32_t)I->genome_ptr[tick[x].snapshot];
+  Buf order, d_tgt, colbest;
+  ALLOC(order, sizeof(uint32_t) * std::max<uint32_t>(n_q, 1));
+  ALLOC(d_tgt, sizeof(uint32_t) * n_genomes);
+  ALLOC(colbest, sizeof(unsigned long long) * std::max<uint64_t>((uint64_t)G_res * n_tick, 1));
+  CK(cudaMemcpyAsync(d_tgt.p, tgt_end.data(), sizeof(uint32_t) * n_genomes, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(colbest.p, 0, sizeof(unsigned long long) * std::max<uint64_t>((uint64_t)G_res * n_tick, 1),
+                     c->stream));
+  if (n_q) PD_KLAUNCH("serve_iota", (k_iota<<<grid_of(n_q, 256, 152u * 4u), 256, 0, c->stream>>>(
+                                        order.as<uint32_t>(), n_q, G_res)));
+  pdg::QuerySet Q{};
+  Q.all_pairs = 1;
+  Q.order = order.as<uint32_t>();
+  Q.n_queries = n_q;
+  Q.tgt_end = d_tgt.as<uint32_t>();
+  Q.colbest = colbest.as<unsigned long long>();
+  Q.col_genome0 = g_res;
+  Q.col_stride = n_tick;
+  pd_hits H;
+  H.ctx = c;
+  H.all_pairs = 1;
+  if ((st = run_hits(c, P.get(), Q, false, &H, std::max<uint32_t>(g_res, 1))) != PD_OK) return st;
+
+  // ---- the tick's rows as one CSR (global resident gene ids as columns)
+  Buf row_ptr, cols, sv, tmp, flag, cnt, start, pa, pb;
+  ALLOC(row_ptr, sizeof(unsigned long long) * (n_q + 1));
+  ALLOC(tmp, pdg::scan_temp_bytes(n_q + 1) + 64);
+  CK(pdg::scan_u32_to_u64(&c->L, H.row_len.as<uint32_t>() + G_res, n_q, row_ptr.as<unsigned long long>(), tmp.p,
+                          c->stream));
+  unsigned long long n_hits = 0;
+  CK(cudaMemcpyAsync(&n_hits, row_ptr.as<unsigned long long>() + n_q, sizeof(n_hits), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  ALLOC(cols, sizeof(int32_t) * std::max<unsigned long long>(n_hits, 1));
+  ALLOC(sv, sizeof(uint32_t) * std::max<unsigned long long>(n_hits, 1));
+  if (n_q)
+    CK(pdg::run_gather_rows(&c->L, n_q, H.row_off.as<unsigned long long>() + G_res, H.row_len.as<uint32_t>() + G_res,
+                            row_ptr.as<unsigned long long>(), H.out_b.as<uint32_t>(), H.out_s.as<uint32_t>(), 0,
+                            cols.as<int32_t>(), sv.as<uint32_t>(), c->stream));
+  // ---- mutual check against the reverse maxima
+  ALLOC(flag, std::max<unsigned long long>(n_hits, 1));
+  ALLOC(cnt, sizeof(uint32_t) * std::max<uint32_t>(n_q, 1));
+  ALLOC(start, sizeof(uint32_t) * (n_q + 1));
+  if (n_q)
+    PD_KLAUNCH("serve_bbh_count",
+               (k_serve_bbh_count<<<grid_of((uint64_t)n_q * 32, 256, 152u * 16u), 256, 0, c->stream>>>(
+                   n_q, G_res, row_ptr.as<unsigned long long>(), cols.as<int32_t>(), sv.as<uint32_t>(),
+                   P->view.La, P->view.gene_genome, g_res, n_tick, colbest.as<unsigned long long>(),
+                   flag.as<uint8_t>(), cnt.as<uint32_t>())));
+  CK(pdg::scan_u32(&c->L, cnt.as<uint32_t>(), n_q, start.as<uint32_t>(), tmp.p, c->stream));
+  uint32_t n_bbh = 0;
+  CK(cudaMemcpyAsync(&n_bbh, start.as<uint32_t>() + n_q, sizeof(n_bbh), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  ALLOC(pa, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
+  ALLOC(pb, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
+  if (n_q && n_bbh)
+    PD_KLAUNCH("serve_bbh_write", (k_serve_bbh_write<<<grid_of((uint64_t)n_q * 32, 256, 152u * 16u), 256, 0,
+                                                       c->stream>>>(n_q, row_ptr.as<unsigned long long>(),
+                                                                    cols.as<int32_t>(), flag.as<uint8_t>(),
+                                                                    start.as<uint32_t>(), pa.as<int32_t>(),
+                                                                    pb.as<int32_t>())));
+  // ---- to the host, split per request
+  std::vector<unsigned long long> h_rp(n_q + 1);
+  std::vector<int32_t> h_cols(n_hits), h_a(n_bbh), h_b(n_bbh);
+  std::vector<uint32_t> h_s(n_hits);
+  CK(cudaMemcpyAsync(h_rp.data(), row_ptr.p, sizeof(unsigned long long) * (n_q + 1), cudaMemcpyDeviceToHost,
+                     c->stream));
+  if (n_hits) {
+    CK(cudaMemcpyAsync(h_cols.data(), cols.p, sizeof(int32_t) * n_hits, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(h_s.data(), sv.p, sizeof(uint32_t) * n_hits, cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (n_bbh) {
+    CK(cudaMemcpyAsync(h_a.data(), pa.p, sizeof(int32_t) * n_bbh, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(h_b.data(), pb.p, sizeof(int32_t) * n_bbh, cudaMemcpyDeviceToHost, c->stream));
+  }
+  if ((st = check_dev_err(c)) != PD_OK) return st;  // synchronizes
+  uint32_t r0 = 0;
+  size_t p = 0;
+  for (uint32_t x = 0; x < n_tick; ++x) {
+    const uint32_t nx = (uint32_t)tick[x].gene_ptr.size() - 1;
+    std::unique_ptr<pd_reply> R(new pd_reply());
+    const unsigned long long h0 = h_rp[r0], h1 = h_rp[r0 + nx];
+    R->row_ptr.resize(nx + 1);
+    for (uint32_t i = 0; i <= nx; ++i) R->row_ptr[i] = (int64_t)(h_rp[r0 + i] - h0);
+    R->cols.assign(h_cols.begin() + h0, h_cols.begin() + h1);
+    R->s.assign(h_s.begin() + h0, h_s.begin() + h1);
+    while (p < n_bbh && (uint32_t)h_a[p] < r0 + nx) {
+      R->bbh_a.push_back(h_a[p] - (int32_t)r0);
+      R->bbh_b.push_back(h_b[p]);
+      ++p;
+    }
+    R->info.ticket = tick[x].ticket;
+    R->info.status = PD_OK;
+    R->info.snapshot_genomes = tick[x].snapshot;
+    R->info.n_genes = nx;
+    R->info.n_hits = h1 - h0;
+    R->info.n_bbh = R->bbh_a.size();
+    R->info.tick_requests = n_tick;
+    replies.push_back(std::move(R));
+    r0 += nx;
+  }
+  I->P = std::move(P);
+  return PD_OK;
+}
+
+void worker_main(pd_index* I) {
+  cudaSetDevice(I->device);
+  for (;;) {
+    std::vector<Request> tick;
+    {
+      std::unique_lock<std::mutex> lk(I->mu);
+      I->cv_work.wait(lk, [&] { return I->stop || !I->queue.empty(); });
+      if (I->stop) return;
+      // admission in arrival order while the tick's estimate fits the budget
+      uint64_t W = I->committed_windows, G = I->committed_genes, tick_genes = 0;
+      while (!I->queue.empty() && tick.size() < I->max_tick) {
+        const Request& r = I->queue.front();
+        const uint64_t ng = r.gene_ptr.size() - 1;
+        const uint64_t est = I->resident_bytes + tick_bytes(W + r.windows, G + ng, tick_genes + ng,
+                                                            I->committed_genes, I->committed, tick.size() + 1) +
+                             2 * (I->res_used + r.res.size());
+        if (est > I->budget && !tick.empty()) break;
+        if (est > I->budget) {  // cannot fit even alone: answer with an error
+          std::unique_ptr<pd_reply> R(new pd_reply());
+          R->info.ticket = r.ticket;
+          R->info.status = PD_ERR_BUDGET;
+          R->info.t_submit_ns = r.t_submit;
+          R->info.t_done_ns = now_ns();
+          R->err = "request does not fit the HBM budget next to the resident index";
+          I->done[r.ticket] = std::move(R);
+          I->queue.pop_front();
+          I->cv_done.notify_all();
+          continue;
+        }
+        W += r.windows;
+        G += ng;
+        tick_genes += ng;
+        tick.push_back(std::move(I->queue.front()));
+        I->queue.pop_front();
+      }
+    }
+    if (tick.empty()) continue;
+    const int64_t t_start = now_ns();
+    std::vector<std::unique_ptr<pd_reply>> replies;
+    const uint64_t res_used0 = I->res_used;
+    const size_t gp0 = I->gene_ptr.size(), gn0 = I->genome_ptr.size();
+    pd_status st;
+    try {
+      st = run_tick(I, tick, replies);
+    } catch (...) {
+      st = PD_ERR_INTERNAL;
+      I->c->err = "exception in the request loop";
+    }
+    const int64_t t_done = now_ns();
+    std::lock_guard<std::mutex> lk(I->mu);
+    if (st == PD_OK) {
+      I->committed += (uint32_t)tick.size();
+      I->committed_genes = I->gene_ptr.size() - 1;
+      I->committed_res = I->res_used;
+      for (auto& r : tick) I->committed_windows += r.windows;
+      I->committed_genome_ptr = I->genome_ptr;
+      I->resident_bytes = I->res.n + (I->P ? I->P->info.device_bytes : 0);
+      I->stats.ticks += 1;
+      I->stats.max_tick_requests = std::max<uint32_t>(I->stats.max_tick_requests, (uint32_t)tick.size());
+      for (auto& R : replies) {
+        R->info.t_start_ns = t_start;
+        R->info.t_done_ns = t_done;
+      }
+      for (size_t x = 0; x < tick.size(); ++x) {
+        replies[x]->info.t_submit_ns = tick[x].t_submit;
+        I->done[tick[x].ticket] = std::move(replies[x]);
+      }
+      I->stats.requests_done += tick.size();
+    } else {
+      // roll the resident data back; every request of the tick gets the error
+      I->res_used = res_used0;
+      I->gene_ptr.resize(gp0);
+      I->genome_ptr.resize(gn0);
+      for (auto& r : tick) {
+        std::unique_ptr<pd_reply> R(new pd_reply());
+        R->info.ticket = r.ticket;
+        R->info.status = st;
+        R->info.t_submit_ns = r.t_submit;
+        R->info.t_start_ns = t_start;
+        R->info.t_done_ns = t_done;
+        R->err = I->c->err;
+        I->done[r.ticket] = std::move(R);
+      }
+    }
+    I->cv_done.notify_all();
+  }
+}
+
+pd_status index_create(pd_ctx* caller, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                       uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k, uint64_t hbm_budget,
+                       pd_index** out) {
+  pd_ctx* c = caller;
+  if (k < 1 || k > PD_MAX_K) return fail(c, PD_ERR_K_RANGE, "k must be in [1, " + std::to_string(PD_MAX_K) + "]");
+  if (!gene_ptr || !genome_ptr || (n_res && !residues)) return fail(c, PD_ERR_ARG, "null argument");
+  if (n_genomes < 1 || n_genomes > PD_MAX_GENOMES) return fail(c, PD_ERR_ARG, "n_genomes must be in [1, 4096]");
+  std::unique_ptr<pd_index> I(new pd_index());
+  I->device = caller->device;
+  I->k = k;
+  I->budget = hbm_budget;
+  CK(cudaSetDevice(I->device));
+  CK(cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking));
+  cudaMemPoolProps props = {};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = I->device;
+  CK(cudaMemPoolCreate(&I->pool, &props));
+  uint64_t keep = hbm_budget;
+  CK(cudaMemPoolSetAttribute(I->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  pd_status st = pd_ctx_create(I->device, I->stream, nullptr, nullptr, nullptr, &I->c);
+  if (st != PD_OK) return fail(caller, st, "could not create the index context");
+  I->c->pool = I->pool;
+  c = I->c;
+  // resident offsets on the host
+  I->gene_ptr.resize(n_genes + 1);
+  I->genome_ptr.resize(n_genomes + 1);
+  CK(cudaMemcpy(I->gene_ptr.data(), gene_ptr, sizeof(int64_t) * (n_genes + 1), cudaMemcpyDefault));
+  CK(cudaMemcpy(I->genome_ptr.data(), genome_ptr, sizeof(int32_t) * (n_genomes + 1), cudaMemcpyDefault));
+  if (I->gene_ptr[0] != 0 || (uint64_t)I->gene_ptr[n_genes] != n_res || I->genome_ptr[0] != 0 ||
+      (uint32_t)I->genome_ptr[n_genomes] != n_genes)
+    return fail(caller, PD_ERR_ARG, "malformed gene_ptr or genome_ptr");
+  if (!I->res.alloc(c, std::max<uint64_t>(n_res, 1 << 20))) return fail(caller, PD_ERR_OOM, "resident residues");
+  if (n_res) {
+    if (cudaMemcpyAsync(I->res.p, residues, n_res, cudaMemcpyDefault, I->stream) != cudaSuccess)
+      return fail_cuda(caller, cudaGetLastError(), "copy of the resident residues");
+  }
+  I->res_used = n_res;
+  pd_profiles* Praw = nullptr;
+  st = build_profiles_impl(c, I->res.as<uint8_t>(), n_res, I->gene_ptr.data(), n_genes, I->genome_ptr.data(),
+                           n_genomes, k, nullptr, &Praw);
+  if (st != PD_OK) return fail(caller, st, c->err);
+  I->P.reset(Praw);
+  I->committed = n_genomes;
+  I->committed_genes = n_genes;
+  I->committed_windows = windows_of(I->gene_ptr, 0, n_genes, k);
+  I->committed_genome_ptr = I->genome_ptr;
+  I->committed_res = n_res;
+  I->resident_bytes = I->res.n + I->P->info.device_bytes;
+  if (I->resident_bytes > hbm_budget) return fail(caller, PD_ERR_BUDGET, "the resident index exceeds the budget");
+  I->worker = std::thread(worker_main, I.get());
+  *out = I.release();
+  return PD_OK;
+}
+
+}  // namespace
+
+PD_API pd_status pd_index_create(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                                 uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
+                                 uint64_t hbm_budget, pd_index** out) {
+  if (!c || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    return index_create(c, residues, n_res, gene_ptr, n_genes, genome_ptr, n_genomes, k, hbm_budget, out);
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_index_create");
+  }
+}
+
+PD_API pd_status pd_index_submit(pd_index* I, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                                 uint32_t n_genes, uint64_t* ticket) {
+  if (!I || !ticket || !gene_ptr || (n_res && !residues)) return PD_ERR_ARG;
+  try {
+    Request r;
+    r.gene_ptr.assign(gene_ptr, gene_ptr + n_genes + 1);
+    if (r.gene_ptr[0] != 0 || (uint64_t)r.gene_ptr[n_genes] != n_res) return PD_ERR_ARG;
+    for (uint32_t g = 0; g < n_genes; ++g) {
+      if (r.gene_ptr[g + 1] < r.gene_ptr[g]) return PD_ERR_ARG;
+      if (r.gene_ptr[g + 1] - r.gene_ptr[g] - I->k + 1 > (int64_t)PD_MAX_WINDOWS) return PD_ERR_GENE_TOO_LONG;
+    }
+    r.res.assign(residues, residues + n_res);
+    r.windows = windows_of(r.gene_ptr, 0, n_genes, I->k);
+    r.t_submit = now_ns();
+    std::lock_guard<std::mutex> lk(I->mu);
+    const uint64_t est = I->resident_bytes +
+                         tick_bytes(I->committed_windows + r.windows, I->committed_genes + n_genes, n_genes,
+                                    I->committed_genes, I->committed, 1) +
+                         2 * (I->committed_res + n_res);
+    if (est > I->budget) return PD_ERR_BUDGET;
+    if (I->committed + I->queue.size() + 1 > PD_MAX_GENOMES) return PD_ERR_BUSY;
+    r.ticket = I->next_ticket++;
+    r.snapshot = I->committed;
+    *ticket = r.ticket;
+    I->queue.push_back(std::move(r));
+    I->cv_work.notify_one();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return PD_ERR_OOM;
+  } catch (...) {
+    return PD_ERR_INTERNAL;
+  }
+}
+
+PD_API pd_status pd_index_poll(pd_index* I, uint64_t ticket, int wait_ms, pd_reply** out) {
+  if (!I || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  std::unique_lock<std::mutex> lk(I->mu);
+  if (ticket == 0 || ticket >= I->next_ticket) return PD_ERR_ARG;
+  auto ready = [&] { return I->done.count(ticket) != 0; };
+  if (!ready()) {
+    if (wait_ms < 0)
+      I->cv_done.wait(lk, ready);
+    else if (!I->cv_done.wait_for(lk, std::chrono::milliseconds(wait_ms), ready))
+      return PD_ERR_TIMEOUT;
+  }
+  auto it = I->done.find(ticket);
+  *out = it->second.release();
+  I->done.erase(it);
+  return PD_OK;
+}
+
+PD_API pd_status pd_index_get_info(pd_index* I, pd_index_info* info) {
+  if (!I || !info) return PD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(I->mu);
+  *info = I->stats;
+  info->k = I->k;
+  info->n_genomes = I->committed;
+  info->n_genes = I->committed_genes;
+  info->queued = (uint32_t)I->queue.size();
+  info->device_bytes = I->resident_bytes;
+  info->budget = I->budget;
+  return PD_OK;
+}
+
+PD_API pd_status pd_index_genome_ptr(pd_index* I, uint32_t n_genomes, int32_t* genome_ptr) {
+  if (!I || !genome_ptr) return PD_ERR_ARG;
+  std::lock_guard<std::mutex> lk(I->mu);
+  if (n_genomes > I->committed) return PD_ERR_ARG;
+  std::copy(I->committed_genome_ptr.begin(), I->committed_genome_ptr.begin() + n_genomes + 1, genome_ptr);
+  return PD_OK;
+}
+
+PD_API void pd_index_free(pd_index* I) { delete I; }
+
+PD_API pd_status pd_reply_get_info(const pd_reply* R, pd_reply_info* info) {
+  if (!R || !info) return PD_ERR_ARG;
+  *info = R->info;
+  return PD_OK;
+}
+
+PD_API const char* pd_reply_error(const pd_reply* R) { return R ? R->err.c_str() : "null reply"; }
+
+PD_API pd_status pd_reply_copy(const pd_reply* R, int64_t* row_ptr, int32_t* cols, uint32_t* s, int32_t* bbh_a,
+                               int32_t* bbh_b) {
+  if (!R) return PD_ERR_ARG;
+  if (R->info.status != PD_OK) return (pd_status)R->info.status;
+  if (row_ptr) std::copy(R->row_ptr.begin(), R->row_ptr.end(), row_ptr);
+  if (cols) std::copy(R->cols.begin(), R->cols.end(), cols);
+  if (s) std::copy(R->s.begin(), R->s.end(), s);
+  if (bbh_a) std::copy(R->bbh_a.begin(), R->bbh_a.end(), bbh_a);
+  if (bbh_b) std::copy(R->bbh_b.begin(), R->bbh_b.end(), bbh_b);
+  return PD_OK;
+}
+
+PD_API void pd_reply_free(pd_reply* R) { delete R; }

@@ -59,6 +59,19 @@ class BatchInfo(C.Structure):
                 ("n_bbh", C.c_uint64), ("postings_walked", C.c_uint64)]
 
 
+class ReplyInfo(C.Structure):
+    _fields_ = [("ticket", C.c_uint64), ("status", C.c_int32), ("snapshot_genomes", C.c_uint32),
+                ("n_genes", C.c_uint32), ("tick_requests", C.c_uint32), ("n_hits", C.c_uint64),
+                ("n_bbh", C.c_uint64), ("t_submit_ns", C.c_int64), ("t_start_ns", C.c_int64),
+                ("t_done_ns", C.c_int64)]
+
+
+class IndexInfo(C.Structure):
+    _fields_ = [("k", C.c_int), ("n_genomes", C.c_uint32), ("n_genes", C.c_uint64), ("queued", C.c_uint32),
+                ("max_tick_requests", C.c_uint32), ("device_bytes", C.c_uint64), ("budget", C.c_uint64),
+                ("ticks", C.c_uint64), ("requests_done", C.c_uint64)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 
@@ -102,6 +115,16 @@ _SIGNATURES = [
     ("pd_batch_copy_hits", C.c_int, [_P, _P, _P, _P, _P]),
     ("pd_batch_copy_bbh", C.c_int, [_P, _P, _P, _P, _P]),
     ("pd_batch_free", None, [_P]),
+    ("pd_index_create", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, C.c_int, C.c_uint64, _PP]),
+    ("pd_index_submit", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, C.POINTER(C.c_uint64)]),
+    ("pd_index_poll", C.c_int, [_P, C.c_uint64, C.c_int, _PP]),
+    ("pd_index_get_info", C.c_int, [_P, C.POINTER(IndexInfo)]),
+    ("pd_index_genome_ptr", C.c_int, [_P, C.c_uint32, _P]),
+    ("pd_index_free", None, [_P]),
+    ("pd_reply_get_info", C.c_int, [_P, C.POINTER(ReplyInfo)]),
+    ("pd_reply_error", C.c_char_p, [_P]),
+    ("pd_reply_copy", C.c_int, [_P, _P, _P, _P, _P, _P]),
+    ("pd_reply_free", None, [_P]),
     ("pd_best_hits_noalloc", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _P, _P, _P, C.c_uint64,
                                        C.POINTER(C.c_uint64)]),
 ]
@@ -269,6 +292,14 @@ class BbhSet(_Handle):
 
 class Batch(_Handle):
     _free_name = "pd_batch_free"
+
+
+class Index(_Handle):
+    _free_name = "pd_index_free"
+
+
+class Reply(_Handle):
+    _free_name = "pd_reply_free"
 
 
 def pd_build_profiles(ctx: Ctx, residues, gene_ptr, genome_ptr, k: int) -> Profiles:
@@ -476,3 +507,72 @@ def pd_batch_copy_bbh(ctx: Ctx, batch: Batch, job_ptr=None, a=None, b=None):
     _check(ctx, _lib.pd_batch_copy_bbh(ctx.handle, batch.handle, _ptr(job_ptr), _ptr(a), _ptr(b)),
            "pd_batch_copy_bbh")
     return None
+
+
+# ---------------------------------------------------------------- served index
+def _check_status(st, func, msg=""):
+    if st != PD_OK:
+        raise PdError(st, func, msg)
+
+
+def pd_index_create(ctx: Ctx, residues, gene_ptr, genome_ptr, k: int, hbm_budget: int) -> Index:
+    """Resident index over a dataset (host or device arrays) at a fixed k,
+    with a worker that answers submitted genomes within hbm_budget bytes."""
+    h = C.c_void_p()
+    st = _lib.pd_index_create(ctx.handle, _ptr(residues), int(residues.shape[0]), _ptr(gene_ptr),
+                              int(gene_ptr.shape[0]) - 1, _ptr(genome_ptr), int(genome_ptr.shape[0]) - 1, int(k),
+                              int(hbm_budget), C.byref(h))
+    _check(ctx, st, "pd_index_create")
+    return Index(ctx, h)
+
+
+def pd_index_submit(index: Index, residues, gene_ptr) -> int:
+    """Queue one genome (host uint8 residues, int64 gene_ptr); returns its ticket."""
+    res = np.ascontiguousarray(residues, dtype=np.uint8)
+    gp = np.ascontiguousarray(gene_ptr, dtype=np.int64)
+    t = C.c_uint64(0)
+    _check_status(_lib.pd_index_submit(index.handle, _ptr(res) if res.size else None, int(res.shape[0]), _ptr(gp),
+                                       int(gp.shape[0]) - 1, C.byref(t)), "pd_index_submit")
+    return int(t.value)
+
+
+def pd_index_poll(index: Index, ticket: int, wait_ms: int = -1) -> Reply:
+    """The answer of a request (waits up to wait_ms; negative = no limit)."""
+    h = C.c_void_p()
+    _check_status(_lib.pd_index_poll(index.handle, int(ticket), int(wait_ms), C.byref(h)), "pd_index_poll")
+    return Reply(index.ctx, h)
+
+
+def pd_index_get_info(index: Index) -> IndexInfo:
+    info = IndexInfo()
+    _check_status(_lib.pd_index_get_info(index.handle, C.byref(info)), "pd_index_get_info")
+    return info
+
+
+def pd_index_genome_ptr(index: Index, n_genomes: int):
+    out = np.zeros(int(n_genomes) + 1, np.int32)
+    _check_status(_lib.pd_index_genome_ptr(index.handle, int(n_genomes), _ptr(out)), "pd_index_genome_ptr")
+    return out
+
+
+def pd_reply_get_info(reply: Reply) -> ReplyInfo:
+    info = ReplyInfo()
+    _check_status(_lib.pd_reply_get_info(reply.handle, C.byref(info)), "pd_reply_get_info")
+    return info
+
+
+def pd_reply_copy(reply: Reply):
+    """(row_ptr int64[n_genes+1], cols int32 resident gene ids, s uint32,
+    bbh int32[n, 2] = (gene of the request, resident gene)); raises PdError if
+    the request failed."""
+    info = pd_reply_get_info(reply)
+    if info.status != PD_OK:
+        msg = _lib.pd_reply_error(reply.handle)
+        raise PdError(info.status, "pd_reply_copy", msg.decode() if msg else "")
+    rp = np.zeros(info.n_genes + 1, np.int64)
+    cols = np.zeros(max(info.n_hits, 1), np.int32)
+    s = np.zeros(max(info.n_hits, 1), np.uint32)
+    a = np.zeros(max(info.n_bbh, 1), np.int32)
+    b = np.zeros(max(info.n_bbh, 1), np.int32)
+    _check_status(_lib.pd_reply_copy(reply.handle, _ptr(rp), _ptr(cols), _ptr(s), _ptr(a), _ptr(b)), "pd_reply_copy")
+    return rp, cols[:info.n_hits], s[:info.n_hits], np.stack([a[:info.n_bbh], b[:info.n_bbh]], axis=1)

@@ -355,6 +355,38 @@ def job_batch(n_jobs: int = 2000, seed: int = 4, workers: int = 1, genes=(500, 6
     return ds, jobs
 
 
+# ---------------------------------------------------------------------------
+# a resident pangenome and a stream of incoming genomes
+# ---------------------------------------------------------------------------
+
+def served_stream(n_resident: int = 100, n_incoming: int = 500, seed: int = 5, resident_genes=("poisson", 3000),
+                  incoming_genes=(1000, 7000), n_families: int = 4000) -> Pangenome:
+    """One pangenome of n_resident + n_incoming genomes drawn from shared
+    families with the pan50x3000 model: the first n_resident genomes (gene
+    counts Poisson(3000) by default) form the resident set, the others (gene
+    counts U[incoming_genes]) arrive one by one."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if resident_genes[0] == "poisson":
+        res_counts = rng.poisson(resident_genes[1], size=n_resident)
+    else:
+        res_counts = rng.integers(resident_genes[1], resident_genes[2] + 1, size=n_resident)
+    inc_counts = rng.integers(incoming_genes[0], incoming_genes[1] + 1, size=n_incoming)
+    counts = [int(x) for x in np.concatenate([res_counts, inc_counts])]
+    ds = generate(n_genomes=n_resident + n_incoming, genes_per_genome=("list", counts), n_families=n_families,
+                  length_dist=("lognormal", 300, 0.5, 30, 2500), core_frac=0.4, accessory_draw=None,
+                  subst_max=0.30, indel_max=0.05, paralog_frac=0.10, singleton_frac=0.05,
+                  seed=int(rng.integers(0, 2**62)), name=f"served{n_resident}+{n_incoming}")
+    ds.params.update(n_resident=n_resident, n_incoming=n_incoming)
+    return ds
+
+
+def genome_of(ds: Pangenome, i: int):
+    """(residues, gene_ptr) of genome i alone."""
+    g0, g1 = int(ds.genome_ptr[i]), int(ds.genome_ptr[i + 1])
+    r0, r1 = int(ds.gene_ptr[g0]), int(ds.gene_ptr[g1])
+    return ds.residues[r0:r1].copy(), (ds.gene_ptr[g0:g1 + 1] - r0).astype(np.int64)
+
+
 def workload(name: str, **overrides) -> Pangenome:
     """Generate a named workload; keyword overrides replace model parameters."""
     params = dict(WORKLOADS[name])
