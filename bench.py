@@ -40,8 +40,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pan50x3000", choices=sorted(synth.WORKLOADS) + ["jobs"],
-                    help="a plain pangenome, or 'jobs': a batch of independent genome-pair jobs")
+    ap.add_argument("--workload", default="pan50x3000", choices=sorted(synth.WORKLOADS) + ["jobs", "served"],
+                    help="a plain pangenome, 'jobs': a batch of independent genome-pair jobs, or 'served': "
+                         "genomes arriving at a resident index")
+    ap.add_argument("--rates", default="2,5,10,20,50", help="arrival rates (genomes/s) of --workload served")
+    ap.add_argument("--seconds-per-rate", type=float, default=20.0,
+                    help="arrivals per rate: min(incoming, rate x this)")
+    ap.add_argument("--incoming", type=int, default=500, help="incoming genomes of --workload served")
     ap.add_argument("--jobs", type=int, default=2000, help="jobs in the batch (--workload jobs)")
     ap.add_argument("--no-per-pair", action="store_true", help="skip the one-pair-per-launch comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -301,12 +306,113 @@ def run_batch(args):
     return 0
 
 
+# --------------------------------------------------------------------------- served index
+def run_served(args):
+    """Served form: a resident index of 100 genomes (the pan50x3000 model)
+    answers incoming genomes (gene counts U[1000, 7000]) arriving as a
+    Poisson process; each answer holds the genome's Best Hits in every
+    resident genome and its BBH pairs, after which the genome is resident.
+    For each arrival rate a fresh index serves min(incoming, rate x
+    seconds-per-rate) arrivals; latency = answer time - submission time (the
+    library's steady clock).  Beside it: one full recomputation (profiles,
+    all-pairs Best Hits and BBH of every genome) at the final size."""
+    t0 = time.perf_counter()
+    ds = synth.served_stream(100, args.incoming, seed=5)
+    gen_s = time.perf_counter() - t0
+    import torch
+    from paper_2510_23679_gb300 import pd
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n_res = 100
+    res = ds.subset(list(range(n_res)))
+    k = pd.pd_choose_k(res.n_residues)
+    ctx = pd.pd_ctx_create(0)
+    budget = 120 << 30
+    incoming = [synth.genome_of(ds, x) for x in range(n_res, ds.n_genomes)]
+    rng = np.random.Generator(np.random.PCG64(55))
+    per_rate = {}
+    clk_all = None
+    with ClockSampler(0) as clk:
+        for rate in [float(x) for x in args.rates.split(",")]:
+            n = int(min(len(incoming), max(1, round(rate * args.seconds_per_rate))))
+            gaps = rng.exponential(1.0 / rate, size=n)
+            index = pd.pd_index_create(ctx, res.residues, res.gene_ptr, res.genome_ptr, k, budget)
+            # warm-up: one request through a separate index of the same size
+            warm = pd.pd_index_create(ctx, res.residues, res.gene_ptr, res.genome_ptr, k, budget)
+            pd.pd_index_poll(warm, pd.pd_index_submit(warm, *incoming[0]), -1)
+            warm.free()
+            tickets = []
+            start = time.perf_counter()
+            due = start
+            for i in range(n):
+                due += gaps[i]
+                d = due - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(pd.pd_index_submit(index, *incoming[i]))
+            lat, t_first, t_last, ticks = [], None, None, []
+            for t in tickets:
+                info = pd.pd_reply_get_info(pd.pd_index_poll(index, t, -1))
+                assert info.status == 0, info.status
+                lat.append((info.t_done_ns - info.t_submit_ns) / 1e6)
+                t_first = info.t_submit_ns if t_first is None else min(t_first, info.t_submit_ns)
+                t_last = info.t_done_ns if t_last is None else max(t_last, info.t_done_ns)
+                ticks.append(info.tick_requests)
+            ii = pd.pd_index_get_info(index)
+            per_rate[str(rate)] = {"arrivals": n, "p50_ms": float(np.percentile(lat, 50)),
+                                   "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(np.mean(lat)),
+                                   "sustained_genomes_per_s": n / ((t_last - t_first) / 1e9),
+                                   "offered_genomes_per_s": rate, "ticks": int(ii.ticks),
+                                   "max_requests_per_tick": int(ii.max_tick_requests),
+                                   "resident_genomes_at_end": int(ii.n_genomes),
+                                   "index_device_bytes_at_end": int(ii.device_bytes)}
+            index.free()
+            torch.cuda.synchronize()
+        clk_all = clk.summary()
+    # full recomputation at the final size (every genome, all pairs)
+    n_last = 100 + max(v["arrivals"] for v in per_rate.values())
+    full = ds.subset(list(range(n_last)))
+    r_d = torch.from_numpy(full.residues).to(dev)
+    g_d = torch.from_numpy(full.gene_ptr).to(dev)
+    n_d = torch.from_numpy(full.genome_ptr).to(dev)
+
+    def recompute():
+        p = pd.pd_build_profiles(ctx, r_d, g_d, n_d, k)
+        h = pd.pd_best_hits_all(ctx, p)
+        return pd.pd_bbh_count(pd.pd_bbh_all(ctx, p, h))
+
+    recompute()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    recompute()
+    e1.record()
+    torch.cuda.synchronize()
+    full_ms = e0.elapsed_time(e1)
+    top = per_rate[max(per_rate, key=lambda r: float(r))]
+    line = {"metric": "p50/p99 genome-add latency; sustained genomes/s", "value": top["sustained_genomes_per_s"],
+            "unit": "genomes/s", "n_gpus": 1, "steps": len(per_rate), "warmup": 1,
+            "ms_per_step": top["mean_ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "u32", "data": "synthetic", "impl": "served",
+            "config": {"workload": f"served: resident 100 genomes ({res.n_genes} genes, k={k}), "
+                                   f"{args.incoming} incoming genomes of U[1000,7000] genes, Poisson arrivals",
+                       "hbm_budget_bytes": budget, "generation_s": gen_s},
+            "latency_by_rate": per_rate,
+            "recompute_all": {"genomes": n_last, "ms": full_ms, "genomes_per_s_if_recomputed_per_arrival":
+                              1e3 / full_ms},
+            "clocks": clk_all}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "jobs":
         return run_batch(args)
+    if args.workload == "served":
+        return run_served(args)
     import torch
     from paper_2510_23679_gb300 import pd
 
