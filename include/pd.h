@@ -219,11 +219,36 @@ pd_status pd_bbh_all(pd_ctx* ctx, const pd_profiles* prof, const pd_hits* hits, 
  * b in G_gj), ascending. */
 pd_status pd_bbh(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32_t gj, pd_bbh_set** out);
 
+/* Within-genome (paralog) Best Hits: Eq. (8) with both genes in the same
+ * genome, the gene itself excluded -- BH(a, G_i minus a) for every gene a of
+ * every genome G_i, same candidate and tie rules as across genomes.  Rows are
+ * all genes, columns global ids; copy with pd_hits_copy. */
+pd_status pd_paralog_hits(pd_ctx* ctx, const pd_profiles* prof, pd_hits** out);
+/* Mutual within-genome Best Hits of a pd_paralog_hits result (Eq. (9) inside
+ * one genome): pairs (a, b), a < b, same genome, ascending. */
+pd_status pd_paralog_bbh(pd_ctx* ctx, const pd_profiles* prof, const pd_hits* hits, pd_bbh_set** out);
+
 /* Copy pairs: a and b n_pairs int32 each (host or device, NULL to skip);
  * *n_pairs (if not NULL) receives the count. */
 pd_status pd_bbh_copy(pd_ctx* ctx, const pd_bbh_set* set, int32_t* a, int32_t* b, uint64_t* n_pairs);
 uint64_t pd_bbh_count(const pd_bbh_set* set);
 void pd_bbh_free(pd_bbh_set* set);
+
+/* ---------------------------------------------------------------- families */
+
+/* Connected components of an undirected graph of n_nodes nodes given by
+ * n_edges edges (a[e], b[e]) (int32, host or device): label[v] (n_nodes
+ * int32, host or device) receives the smallest node id of v's component;
+ * *n_components (if not NULL) the number of components.  An edge naming a
+ * node outside [0, n_nodes) is PD_ERR_ARG. */
+pd_status pd_components(pd_ctx* ctx, const int32_t* a, const int32_t* b, uint64_t n_edges, uint32_t n_nodes,
+                        int32_t* label, uint32_t* n_components);
+/* Gene families (phase (c), "extract gene families from the Bidirectional
+ * Best Hits"): the connected components of the BBH graph of pd_bbh_all, one
+ * label per gene (global ids, n_genes of the profiled dataset), each family
+ * labelled by its smallest gene id.  The refinement PanDelos applies to the
+ * components is not specified by the paper and is not applied. */
+pd_status pd_families(pd_ctx* ctx, const pd_bbh_set* bbh, uint32_t n_genes, int32_t* family, uint32_t* n_families);
 
 /* ---------------------------------------------------------------- sum-min */
 

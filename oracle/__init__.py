@@ -13,7 +13,9 @@ function follows the passage of the paper named in its docstring:
 * ``Profiles``     Eqs. (1)-(3) and Algorithm 1 (multiplicity vectors);
 * ``summin``       Eq. (5) numerator and denominator of one gene pair;
 * ``pair``         Algorithm 2 (S_ij, Best Hits of rows, Eq. (8)) and
-                   Algorithm 3 (Bidirectional Best Hits, Eq. (9)).
+                   Algorithm 3 (Bidirectional Best Hits, Eq. (9));
+* ``families``     phase (c): connected components of the BBH graph;
+* ``paralog_hits`` Eq. (8) within one genome (the gene itself excluded).
 """
 from __future__ import annotations
 
@@ -212,3 +214,79 @@ def pair_for_dataset(ds, gi: int, gj: int, k: int, n_threads: int = 1) -> PairRe
     if gi == gj:
         return pair(prof, sub.genome_ptr, 0, 0, n_threads)
     return pair(prof, sub.genome_ptr, 0, 1, n_threads)
+
+
+def all_pairs_bbh(ds, k: int, n_threads: int = 1) -> np.ndarray:
+    """Algorithm 3 on every genome pair i < j of a dataset: BBH pairs (a, b)
+    as global gene ids, genome(a) < genome(b), ascending."""
+    gp = ds.genome_ptr
+    out = []
+    for i in range(ds.n_genomes):
+        for j in range(i + 1, ds.n_genomes):
+            R = pair_for_dataset(ds, i, j, k, n_threads)
+            if len(R.bbh):
+                out.append(R.bbh.astype(np.int64) + [int(gp[i]), int(gp[j])])
+    if not out:
+        return np.zeros((0, 2), np.int64)
+    pairs = np.concatenate(out)
+    return pairs[np.lexsort((pairs[:, 1], pairs[:, 0]))]
+
+
+def families(n_nodes: int, pairs) -> np.ndarray:
+    """Phase (c), "extract gene families from the Bidirectional Best Hits",
+    read as the connected components of the BBH graph (the refinement
+    PanDelos applies afterwards is not specified).  Breadth-first search from
+    every unvisited node in ascending order, so the first node of each
+    component -- its label -- is the component's smallest id."""
+    adj = [[] for _ in range(n_nodes)]
+    for a, b in pairs:
+        adj[int(a)].append(int(b))
+        adj[int(b)].append(int(a))
+    label = np.full(n_nodes, -1, np.int64)
+    for s in range(n_nodes):
+        if label[s] >= 0:
+            continue
+        label[s] = s
+        frontier = [s]
+        while frontier:
+            nxt = []
+            for u in frontier:
+                for v in adj[u]:
+                    if label[v] < 0:
+                        label[v] = s
+                        nxt.append(v)
+            frontier = nxt
+    return label
+
+
+def paralog_hits(ds, k: int, n_threads: int = 1):
+    """Eq. (8) inside each genome with the gene itself excluded (the
+    within-genome comparison): for every gene a of genome G_i, the genes b of
+    G_i, b != a, with s(a, b) >= 1 that maximise s / sum-max, ties kept.
+    Uses the oracle's own S and sum-max matrices of the pair (G_i, G_i).
+    Returns one (columns, s values) per gene, columns as global gene ids."""
+    gp = ds.genome_ptr
+    rows = []
+    for i in range(ds.n_genomes):
+        g0 = int(gp[i])
+        n = int(gp[i + 1] - gp[i])
+        R = pair_for_dataset(ds, i, i, k, n_threads) if n else None
+        for a in range(n):
+            best, hits = None, []
+            for b in range(n):
+                s = int(R.S[a, b])
+                if b == a or s < 1:
+                    continue
+                den = int(R.Den[a, b])
+                if best is None or s * best[1] > best[0] * den:
+                    best, hits = (s, den), [b]
+                elif s * best[1] == best[0] * den:
+                    hits.append(b)
+            rows.append(([g0 + b for b in hits], [int(R.S[a, b]) for b in hits]))
+    return rows
+
+
+def paralog_bbh(rows):
+    """Eq. (9) inside a genome: pairs (a, b), a < b, each a Best Hit of the other."""
+    sets = [set(c) for c, _ in rows]
+    return [(a, b) for a in range(len(rows)) for b in sorted(sets[a]) if b > a and a in sets[b]]

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256) k_bbh_count(BbhRows R, uint8_t* __restric
         bool f = false;
         if (e < n) {
           const uint32_t b = R.hit_b[off + e];
-          if (!R.all_pairs || R.gene_genome[b] > ga) {
+          if (!R.all_pairs || (R.paralog ? b > a : R.gene_genome[b] > ga)) {
             const uint32_t y = partner_row(R, b);
             f = row_contains(R.hit_b, R.row_off[y], R.row_len[y], a);
           }

@@ -187,7 +187,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
   unsigned long long* out = tb.out;
   const uint32_t mask = tb.cap - 1u;
   // ---- query gene, its output row and its targets
-  uint32_t a, row, own0 = 0, own1 = 0, tend = 0xFFFFFFFFu, col = 0;
+  uint32_t a, row, own0 = 0, own1 = 0, tend = 0xFFFFFFFFu, col = 0, self = kEmpty;
   unsigned long long key_lo = 0, key_hi = 0;
   if (Q.all_pairs) {
     a = Q.order ? Q.order[qi] : Q.q0 + qi;
@@ -199,7 +199,13 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
     col = gg - Q.col_genome0;
   } else {
     uint32_t tlo, thi;
-    if (qi < Q.nA) {
+    if (Q.paralog) {
+      a = Q.q0 + qi;
+      const uint32_t gg = P.gene_genome[a];
+      tlo = (uint32_t)P.genome_ptr[gg];
+      thi = (uint32_t)P.genome_ptr[gg + 1];
+      self = a;
+    } else if (qi < Q.nA) {
       a = Q.qa0 + qi;
       tlo = Q.ta0;
       thi = Q.ta1;
@@ -335,7 +341,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
       for (uint32_t u = tid; u < n_occ; u += kThreads) {
         uint32_t b, s;
         acc.get(tb.used[u], &b, &s);
-        if (Q.all_pairs && ((b >= own0 && b < own1) || b >= tend)) continue;  // not a target
+        if ((Q.all_pairs && ((b >= own0 && b < own1) || b >= tend)) || b == self) continue;  // not a target
         const uint32_t gi = P.ginfo[b];
         const uint32_t den = La_a + (gi & 0xFFFFu) - s;
         best_update(&best[Q.all_pairs ? (gi >> 16) : 0u], s, den);
@@ -348,7 +354,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
         acc.get(h, &b, &s);
         const uint32_t gi = P.ginfo[b];
         const unsigned long long bv = best[Q.all_pairs ? (gi >> 16) : 0u];
-        if (!(Q.all_pairs && ((b >= own0 && b < own1) || b >= tend)) &&
+        if (!(Q.all_pairs && ((b >= own0 && b < own1) || b >= tend)) && b != self &&
             ratio_equal(s, La_a + (gi & 0xFFFFu) - s, (uint32_t)(bv >> 32), (uint32_t)bv)) {
           const uint32_t slot = atomicAdd(&sh->n_out, 1u);
           if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | s;

@@ -826,7 +826,7 @@ pd_status pdh::bbh_impl(pd_ctx* c, const pdg::BbhRows& R, uint64_t n_hit_slots, 
 PD_API pd_status pd_bbh_all(pd_ctx* c, const pd_profiles* P, const pd_hits* H, pd_bbh_set** out) {
   if (!c || !P || !H || !out) return PD_ERR_ARG;
   *out = nullptr;
-  if (!H->all_pairs) return fail(c, PD_ERR_ARG, "pd_bbh_all needs the result of pd_best_hits_all");
+  if (!H->all_pairs || H->paralog) return fail(c, PD_ERR_ARG, "pd_bbh_all needs the result of pd_best_hits_all");
   try {
     CK(cudaSetDevice(c->device));
     pdg::BbhRows R{};
@@ -845,6 +845,58 @@ PD_API pd_status pd_bbh_all(pd_ctx* c, const pd_profiles* P, const pd_hits* H, p
     return fail(c, PD_ERR_OOM, "host allocation failed");
   } catch (...) {
     return fail(c, PD_ERR_INTERNAL, "exception in pd_bbh_all");
+  }
+}
+
+PD_API pd_status pd_paralog_hits(pd_ctx* c, const pd_profiles* P, pd_hits** out) {
+  if (!c || !P || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    CK(cudaSetDevice(c->device));
+    std::unique_ptr<pd_hits> H(new pd_hits());
+    H->ctx = c;
+    pdg::QuerySet Q{};
+    Q.all_pairs = 0;
+    Q.paralog = 1;
+    Q.q0 = 0;
+    Q.n_queries = P->view.n_genes;
+    pd_status st = run_hits(c, P, Q, false, H.get());
+    if (st != PD_OK) return st;
+    H->all_pairs = 1;  // rows are all genes, columns global ids
+    H->paralog = 1;
+    H->n_rows = P->view.n_genes;
+    *out = H.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_paralog_hits");
+  }
+}
+
+PD_API pd_status pd_paralog_bbh(pd_ctx* c, const pd_profiles* P, const pd_hits* H, pd_bbh_set** out) {
+  if (!c || !P || !H || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  if (!H->paralog) return fail(c, PD_ERR_ARG, "pd_paralog_bbh needs the result of pd_paralog_hits");
+  try {
+    CK(cudaSetDevice(c->device));
+    pdg::BbhRows R{};
+    R.all_pairs = 1;
+    R.paralog = 1;
+    R.n_rows = H->n_rows;
+    R.gene_genome = P->view.gene_genome;
+    R.row_off = H->row_off.as<unsigned long long>();
+    R.row_len = H->row_len.as<uint32_t>();
+    R.hit_b = H->out_b.as<uint32_t>();
+    std::unique_ptr<pd_bbh_set> S(new pd_bbh_set());
+    pd_status st = bbh_impl(c, R, H->out_b.n / sizeof(uint32_t), 0, 0, S.get());
+    if (st != PD_OK) return st;
+    *out = S.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_paralog_bbh");
   }
 }
 

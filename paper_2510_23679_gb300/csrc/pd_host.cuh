@@ -199,6 +199,7 @@ struct pd_profiles {
 struct pd_hits {
   pd_ctx* ctx = nullptr;
   int all_pairs = 0;
+  int paralog = 0;  // within-genome Best Hits (rows = all genes)
   uint32_t n_rows = 0, row_base = 0, col_base = 0;
   uint32_t nA = 0, qa0 = 0, qb0 = 0;  // pair form with both directions (internal)
   uint64_t n_hits = 0, walked = 0;

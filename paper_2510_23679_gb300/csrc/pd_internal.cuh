@@ -194,6 +194,9 @@ struct QuerySet {
   const uint32_t* tgt_end;
   unsigned long long* colbest;
   uint32_t col_genome0, col_stride;
+  // Within-genome form (pair indexing, row = q0 + query): each query gene is
+  // compared with the other genes of its own genome (not with itself).
+  int paralog;
 };
 
 struct HitsOut {
@@ -317,6 +320,7 @@ cudaError_t run_gather_rows(Launcher* L, uint32_t n_rows, const unsigned long lo
 // of a target gene b is row_of_gene(b).  See k_bbh.cu for the two forms.
 struct BbhRows {
   int all_pairs;               // 1: rows = all genes (row x = gene x)
+  int paralog;                 // with all_pairs: hits inside one genome, pairs (a, b) with a < b
   uint32_t n_rows;
   uint32_t nA, qa0, qb0;       // pair form: rows 0..nA-1 = genes qa0.., rest = genes qb0..
   const uint16_t* gene_genome; // all form: genome of each gene

@@ -115,6 +115,10 @@ _SIGNATURES = [
     ("pd_batch_copy_hits", C.c_int, [_P, _P, _P, _P, _P]),
     ("pd_batch_copy_bbh", C.c_int, [_P, _P, _P, _P, _P]),
     ("pd_batch_free", None, [_P]),
+    ("pd_paralog_hits", C.c_int, [_P, _P, _PP]),
+    ("pd_paralog_bbh", C.c_int, [_P, _P, _P, _PP]),
+    ("pd_components", C.c_int, [_P, _P, _P, C.c_uint64, C.c_uint32, _P, C.POINTER(C.c_uint32)]),
+    ("pd_families", C.c_int, [_P, _P, C.c_uint32, _P, C.POINTER(C.c_uint32)]),
     ("pd_index_create", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, C.c_int, C.c_uint64, _PP]),
     ("pd_index_submit", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, C.POINTER(C.c_uint64)]),
     ("pd_index_poll", C.c_int, [_P, C.c_uint64, C.c_int, _PP]),
@@ -408,6 +412,20 @@ def pd_bbh(ctx: Ctx, prof: Profiles, gi: int, gj: int) -> BbhSet:
     return BbhSet(ctx, h)
 
 
+def pd_paralog_hits(ctx: Ctx, prof: Profiles) -> Hits:
+    """Within-genome Best Hits of every gene (itself excluded)."""
+    h = C.c_void_p()
+    _check(ctx, _lib.pd_paralog_hits(ctx.handle, prof.handle, C.byref(h)), "pd_paralog_hits")
+    return Hits(ctx, h)
+
+
+def pd_paralog_bbh(ctx: Ctx, prof: Profiles, hits: Hits) -> BbhSet:
+    """Mutual within-genome Best Hits (a < b, same genome)."""
+    h = C.c_void_p()
+    _check(ctx, _lib.pd_paralog_bbh(ctx.handle, prof.handle, hits.handle, C.byref(h)), "pd_paralog_bbh")
+    return BbhSet(ctx, h)
+
+
 def pd_bbh_count(bbh: BbhSet) -> int:
     return int(_lib.pd_bbh_count(bbh.handle))
 
@@ -576,3 +594,25 @@ def pd_reply_copy(reply: Reply):
     b = np.zeros(max(info.n_bbh, 1), np.int32)
     _check_status(_lib.pd_reply_copy(reply.handle, _ptr(rp), _ptr(cols), _ptr(s), _ptr(a), _ptr(b)), "pd_reply_copy")
     return rp, cols[:info.n_hits], s[:info.n_hits], np.stack([a[:info.n_bbh], b[:info.n_bbh]], axis=1)
+
+
+# ---------------------------------------------------------------- families
+def pd_components(ctx: Ctx, a, b, n_nodes: int):
+    """Connected components of the graph with edges (a[e], b[e]) (host or
+    device int32): (labels int32[n_nodes] on the host, n_components)."""
+    aa = a if hasattr(a, "data_ptr") else np.ascontiguousarray(a, dtype=np.int32)
+    bb = b if hasattr(b, "data_ptr") else np.ascontiguousarray(b, dtype=np.int32)
+    n_edges = int(aa.shape[0])
+    lab = np.zeros(max(int(n_nodes), 1), np.int32)
+    n = C.c_uint32(0)
+    _check(ctx, _lib.pd_components(ctx.handle, _ptr(aa) if n_edges else None, _ptr(bb) if n_edges else None, n_edges,
+                                   int(n_nodes), _ptr(lab), C.byref(n)), "pd_components")
+    return lab[:int(n_nodes)], int(n.value)
+
+
+def pd_families(ctx: Ctx, bbh: BbhSet, n_genes: int):
+    """Gene families of an all-pairs BBH set: (labels int32[n_genes], count)."""
+    lab = np.zeros(max(int(n_genes), 1), np.int32)
+    n = C.c_uint32(0)
+    _check(ctx, _lib.pd_families(ctx.handle, bbh.handle, int(n_genes), _ptr(lab), C.byref(n)), "pd_families")
+    return lab[:int(n_genes)], int(n.value)
