@@ -74,7 +74,8 @@ def make_workload(name, rank):
 
 def config_of(ds, name, k, flush):
     return {"workload": f"{name}: {ds.n_genomes} genomes, {ds.n_genes} genes, {ds.n_residues} residues, "
-                        f"k={k}, amino-acid alphabet, all {ds.n_genomes * (ds.n_genomes - 1) // 2} genome pairs",
+                        f"k={k}, {'nucleotide' if alphabet_of(name) == 4 else 'amino-acid'} alphabet, "
+                        f"all {ds.n_genomes * (ds.n_genomes - 1) // 2} genome pairs",
             "n_genomes": ds.n_genomes, "n_genes": ds.n_genes, "n_residues": ds.n_residues, "k": k,
             "logical_pairs_per_step": ds.logical_pairs(), "l2": flush, "parallelism": "replicas"}
 
@@ -98,14 +99,18 @@ def captured_traffic(kernel_src, summary):
     return int(m_val.group(1))
 
 
-def oracle_sample(ds, k, seconds, threads):
+def alphabet_of(name):
+    return 4 if synth.WORKLOADS.get(name, {}).get("alphabet") == "nt" else 20
+
+
+def oracle_sample(ds, k, seconds, threads, alphabet=20):
     """Time the oracle (as it stands) on whole genome pairs until `seconds` pass."""
     import oracle
     n = ds.n_genomes
     pairs = [(i, i + 1) for i in range(0, n - 1, 2)]
     done, pairs_done, t0 = [], 0, time.perf_counter()
     for gi, gj in pairs:
-        oracle.pair_for_dataset(ds, gi, gj, k, n_threads=threads)
+        oracle.pair_for_dataset(ds, gi, gj, k, n_threads=threads, alphabet=alphabet)
         done.append((gi, gj))
         pairs_done += int(ds.genome_ptr[gi + 1] - ds.genome_ptr[gi]) * int(ds.genome_ptr[gj + 1] - ds.genome_ptr[gj])
         if time.perf_counter() - t0 >= seconds:
@@ -173,14 +178,15 @@ def run_reference(args):
         return 0
     ds = make_workload(args.workload, 0)
     import oracle
-    k = oracle.choose_k(ds.n_residues)
+    alpha = alphabet_of(args.workload)
+    k = oracle.choose_k(ds.n_residues, alphabet=alpha)
     cores = host_cores()
     per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
     for _ in range(args.warmup):
-        oracle_sample(ds, k, 0.0, cores)  # one genome pair each
+        oracle_sample(ds, k, 0.0, cores, alpha)  # one genome pair each
     rates, samples = [], []
     for _ in range(args.steps):
-        r, dt, done, npairs = oracle_sample(ds, k, per_step, cores)
+        r, dt, done, npairs = oracle_sample(ds, k, per_step, cores, alpha)
         rates.append(r)
         samples.append(npairs)
     value = statistics.median(rates)
@@ -423,7 +429,8 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     ds = make_workload(args.workload, rank)
-    k = pd.pd_choose_k(ds.n_residues)
+    alpha = alphabet_of(args.workload)
+    k = pd.pd_choose_k(ds.n_residues, alpha)
     ctx = pd.pd_ctx_create(local)
     stream = torch.cuda.current_stream(dev)
 
@@ -433,7 +440,7 @@ def main():
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
     def step_device():
-        prof = pd.pd_build_profiles(ctx, res_d, gp_d, gn_d, k)
+        prof = pd.pd_build_profiles_alphabet(ctx, res_d, gp_d, gn_d, alpha, k)
         hits = pd.pd_best_hits_all(ctx, prof)
         bbh = pd.pd_bbh_all(ctx, prof, hits)
         return prof, hits, bbh
@@ -507,7 +514,7 @@ def main():
 
         def step_e2e():
             nonlocal d2h
-            p = pd.pd_build_profiles(ctx, res_h, gp_h, gn_h, k)
+            p = pd.pd_build_profiles_alphabet(ctx, res_h, gp_h, gn_h, alpha, k)
             h = pd.pd_best_hits_all(ctx, p)
             b = pd.pd_bbh_all(ctx, p, h)
             n = pd.pd_bbh_count(b)
@@ -541,7 +548,7 @@ def main():
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = host_cores()
-        rate, dt, done, npairs = oracle_sample(ds, k, args.cpu_seconds, cores)
+        rate, dt, done, npairs = oracle_sample(ds, k, args.cpu_seconds, cores, alpha)
         cpu = {"value": rate, "unit": "gene-pairs/s", "cores": cores, "kind": "oracle",
                "sample": f"genome pairs {done} of the same workload ({npairs} gene pairs, {dt:.1f} s, "
                          f"profiles of both genomes included), oracle threads={cores}"}

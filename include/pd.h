@@ -58,8 +58,12 @@ typedef enum {
   PD_ERR_INTERNAL = 10       /* an internal invariant failed (a bug) */
 } pd_status;
 
-/* Largest k: the k-mer dictionary is a bitmap over all 20^k codes. */
+/* Alphabets ("nucleotide or amino acid", Basic notions). */
+#define PD_ALPHABET_AMINO 20      /* ACDEFGHIKLMNPQRSTVWY */
+#define PD_ALPHABET_NUCLEOTIDE 4  /* ACGT */
+/* Largest k: the k-mer dictionary is a bitmap over all |alphabet|^k codes. */
 #define PD_MAX_K 8
+#define PD_MAX_K_NUCLEOTIDE 16
 /* Largest number of windows (|g| - k + 1) of one gene: counts are 16-bit. */
 #define PD_MAX_WINDOWS 65535u
 /* Largest number of genomes in one dataset (per-genome maxima live in shared memory). */
@@ -127,6 +131,15 @@ pd_status pd_build_profiles(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res
                             const int64_t* gene_ptr, uint32_t n_genes, const int32_t* genome_ptr,
                             uint32_t n_genomes, int k, pd_profiles** out);
 
+/* pd_build_profiles over an alphabet of PD_ALPHABET_AMINO (20, k <= PD_MAX_K)
+ * or PD_ALPHABET_NUCLEOTIDE (4: ACGT, k <= PD_MAX_K_NUCLEOTIDE) letters; every
+ * later call is the same for either alphabet.  pd_build_profiles is this call
+ * with the amino-acid alphabet.  Codes returned by the copy calls are base-4
+ * for nucleotides. */
+pd_status pd_build_profiles_alphabet(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res,
+                                     const int64_t* gene_ptr, uint32_t n_genes, const int32_t* genome_ptr,
+                                     uint32_t n_genomes, int alphabet, int k, pd_profiles** out);
+
 /* pd_build_profiles over several independent problems at once.  genome_seg
  * (HOST array, n_genomes entries, each < n_genomes) assigns every genome to a
  * segment; k-mers of different segments are different dictionary entries
@@ -151,6 +164,7 @@ typedef struct {
   uint32_t max_posting; /* longest posting list */
   uint32_t count_bits;  /* bits of the count field in a packed posting */
   uint64_t device_bytes;/* device memory held by the handle */
+  int alphabet;         /* 20 or 4 */
 } pd_profiles_info;
 
 pd_status pd_profiles_get_info(const pd_profiles* prof, pd_profiles_info* info);

@@ -62,6 +62,8 @@ def _load():
         lib.orc_choose_k.argtypes = [C.c_uint64, C.c_int]
         lib.orc_build.restype = P
         lib.orc_build.argtypes = [u8p, C.c_uint64, i64p, C.c_uint32, C.c_int, C.POINTER(C.c_int)]
+        lib.orc_build_alphabet.restype = P
+        lib.orc_build_alphabet.argtypes = [u8p, C.c_uint64, i64p, C.c_uint32, C.c_int, C.c_int, C.POINTER(C.c_int)]
         lib.orc_free.argtypes = [P]
         lib.orc_mv_len.restype = C.c_uint32
         lib.orc_mv_len.argtypes = [P, C.c_uint32]
@@ -103,7 +105,7 @@ def choose_k(total_residues: int, alphabet: int = 20) -> int:
 class Profiles:
     """Multiplicity vectors of every gene of a dataset (Algorithm 1)."""
 
-    def __init__(self, residues: np.ndarray, gene_ptr: np.ndarray, k: int):
+    def __init__(self, residues: np.ndarray, gene_ptr: np.ndarray, k: int, alphabet: int = 20):
         lib = _load()
         self._res = np.ascontiguousarray(residues, dtype=np.uint8)
         self._gptr = np.ascontiguousarray(gene_ptr, dtype=np.int64)
@@ -111,8 +113,8 @@ class Profiles:
         self.n_genes = int(self._gptr.shape[0] - 1)
         st = C.c_int(0)
         res = self._res if self._res.size else np.zeros(1, np.uint8)
-        self._h = lib.orc_build(_ptr(res, C.c_uint8), self._res.size, _ptr(self._gptr, C.c_int64),
-                                self.n_genes, self.k, C.byref(st))
+        self._h = lib.orc_build_alphabet(_ptr(res, C.c_uint8), self._res.size, _ptr(self._gptr, C.c_int64),
+                                         self.n_genes, self.k, int(alphabet), C.byref(st))
         if not self._h:
             raise OracleError(st.value, "build")
 
@@ -207,10 +209,10 @@ def pair(prof: Profiles, genome_ptr: np.ndarray, gi: int, gj: int, n_threads: in
         lib.orc_pair_free(h)
 
 
-def pair_for_dataset(ds, gi: int, gj: int, k: int, n_threads: int = 1) -> PairResult:
+def pair_for_dataset(ds, gi: int, gj: int, k: int, n_threads: int = 1, alphabet: int = 20) -> PairResult:
     """Algorithms 1-3 on genomes gi and gj of a dataset (only their genes are profiled)."""
     sub = ds.subset([gi, gj]) if gi != gj else ds.subset([gi])
-    prof = Profiles(sub.residues, sub.gene_ptr, k)
+    prof = Profiles(sub.residues, sub.gene_ptr, k, alphabet)
     if gi == gj:
         return pair(prof, sub.genome_ptr, 0, 0, n_threads)
     return pair(prof, sub.genome_ptr, 0, 1, n_threads)

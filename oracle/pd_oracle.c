@@ -56,11 +56,15 @@
 #define ORC_ERR_IDENTITY 3
 #define ORC_ERR_OOM 4
 
-static const char kAlphabet[] = "ACDEFGHIKLMNPQRSTVWY";
+static const char kAmino[] = "ACDEFGHIKLMNPQRSTVWY";
+static const char kNucleotide[] = "ACGT";
 
-static int valid_letter(uint8_t c) {
-  for (int i = 0; i < 20; ++i)
-    if ((uint8_t)kAlphabet[i] == c) return 1;
+/* "nucleotide or amino acid" alphabets (Basic notions): 20 upper-case amino
+ * acids, or the 4 upper-case nucleotides. */
+static int valid_letter(uint8_t c, int alphabet) {
+  const char* letters = alphabet == 4 ? kNucleotide : kAmino;
+  for (int i = 0; letters[i]; ++i)
+    if ((uint8_t)letters[i] == c) return 1;
   return 0;
 }
 
@@ -155,15 +159,17 @@ void orc_free(orc_profiles* P) {
   free(P);
 }
 
-/* Build the MVs of all genes.  *status receives an ORC_* code. */
-orc_profiles* orc_build(const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
-                        uint32_t n_genes, int k, int* status) {
+/* Build the MVs of all genes over an alphabet of 20 (amino acids) or 4
+ * (nucleotides) letters.  *status receives an ORC_* code. */
+orc_profiles* orc_build_alphabet(const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                                 uint32_t n_genes, int k, int alphabet, int* status) {
   *status = ORC_ERR_ARG;
-  if (k < 1 || !gene_ptr || gene_ptr[0] != 0 || (uint64_t)gene_ptr[n_genes] != n_res) return NULL;
+  if (k < 1 || (alphabet != 20 && alphabet != 4)) return NULL;
+  if (!gene_ptr || gene_ptr[0] != 0 || (uint64_t)gene_ptr[n_genes] != n_res) return NULL;
   for (uint32_t g = 0; g < n_genes; ++g)
     if (gene_ptr[g + 1] < gene_ptr[g]) return NULL;
   for (uint64_t i = 0; i < n_res; ++i)
-    if (!valid_letter(residues[i])) {
+    if (!valid_letter(residues[i], alphabet)) {
       *status = ORC_ERR_ALPHABET;
       return NULL;
     }
@@ -192,6 +198,11 @@ orc_profiles* orc_build(const uint8_t* residues, uint64_t n_res, const int64_t* 
   }
   *status = ORC_OK;
   return P;
+}
+
+orc_profiles* orc_build(const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr, uint32_t n_genes, int k,
+                        int* status) {
+  return orc_build_alphabet(residues, n_res, gene_ptr, n_genes, k, 20, status);
 }
 
 uint32_t orc_mv_len(const orc_profiles* P, uint32_t g) { return P->mv[g].n; }

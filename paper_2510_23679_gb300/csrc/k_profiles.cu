@@ -2,9 +2,10 @@
 // phase", Algorithm 1, and the inverted index the sum-min kernel walks).
 //
 // Steps (one launch each):
-//   encode_mark    residue -> 0..19, base-20 code of every window (Eq. (1):
+//   encode_mark    letter -> 0..|G|-1 (|G| = 20 amino acids or 4
+//                  nucleotides), base-|G| code of every window (Eq. (1):
 //                  windows of exactly k letters), one bit per code in a bitmap
-//                  over all 20^k codes; letters outside the alphabet raise
+//                  over all |G|^k codes; letters outside the alphabet raise
 //                  PD_ERR_ALPHABET.  Segmented datasets (independent problems
 //                  profiled together) give each segment its own 20^k range of
 //                  the bitmap, code + segment * 20^k, so k-mers of different
@@ -50,9 +51,9 @@ __global__ void __launch_bounds__(kEncThreads)
     k_encode_mark(const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr, uint32_t n_genes, int k,
                   unsigned long long* __restrict__ bitmap, const uint16_t* __restrict__ gene_genome,
                   const unsigned long long* __restrict__ genome_code_base, const int64_t* __restrict__ gene_src,
-                  DevErr* err) {
+                  int alpha, DevErr* err) {
   __shared__ uint8_t lut[256];
-  init_letter_table(lut);
+  init_letter_table(lut, alpha);
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_genes; g += warps) {
@@ -61,15 +62,15 @@ __global__ void __launch_bounds__(kEncThreads)
     const uint8_t* s = res + r0;
     const unsigned long long base = genome_code_base ? genome_code_base[gene_genome[g]] : 0ull;
     for (uint32_t p = lane; p < len; p += 32) {
-      if (lut[s[p]] >= kAlphabetSize) raise_error(err, PD_ERR_ALPHABET, (unsigned long long)(r0 + p));
+      if (lut[s[p]] >= (uint32_t)alpha) raise_error(err, PD_ERR_ALPHABET, (unsigned long long)(r0 + p));
     }
     for (uint32_t p = lane; p + (uint32_t)k <= len; p += 32) {
       unsigned long long code = 0;
       bool ok = true;
       for (int t = 0; t < k; ++t) {
         uint32_t c = lut[s[p + t]];
-        ok &= c < (uint32_t)kAlphabetSize;
-        code = code * (unsigned long long)kAlphabetSize + (c < (uint32_t)kAlphabetSize ? c : 0u);
+        ok &= c < (uint32_t)alpha;
+        code = code * (unsigned long long)alpha + (c < (uint32_t)alpha ? c : 0u);
       }
       code += base;
       if (ok) atomicOr(&bitmap[code >> 6], 1ull << (code & 63u));
@@ -111,7 +112,7 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
     unsigned long long code = 0;
     for (int t = 0; t < k; ++t) {
       const uint32_t c = lut[s[p + t]];
-      code = code * (unsigned long long)kAlphabetSize + (c < (uint32_t)kAlphabetSize ? c : 0u);
+      code = code * (unsigned long long)M.alpha + (c < (uint32_t)M.alpha ? c : 0u);
     }
     const uint32_t id = code_rank(code + base, bitmap, word_rank);
     uint32_t h = mix32(id) & (cap - 1u);
@@ -182,7 +183,7 @@ __global__ void __launch_bounds__(kThreads)
   extern __shared__ unsigned long long table[];
   __shared__ uint8_t lut[256];
   __shared__ uint32_t warp_tmp[kThreads / 32 + 1];
-  init_letter_table(lut);
+  init_letter_table(lut, M.alpha);
   const uint32_t n = list ? n_list : n_genes;
   for (uint32_t x = blockIdx.x; x < n; x += gridDim.x) {
     const uint32_t g = list ? list[x] : x;
@@ -200,7 +201,7 @@ __global__ void __launch_bounds__(kMvLongThreads)
                     uint32_t n_long, unsigned long long* scratch, const unsigned long long* __restrict__ scratch_off) {
   __shared__ uint8_t lut[256];
   __shared__ uint32_t warp_tmp[kMvLongThreads / 32 + 1];
-  init_letter_table(lut);
+  init_letter_table(lut, M.alpha);
   for (uint32_t x = blockIdx.x; x < n_long; x += gridDim.x) {
     const uint32_t g = long_genes[x];
     mv_build_one(g, scratch + scratch_off[x], mv_table_cap(win_off[g + 1] - win_off[g]), lut, warp_tmp, res,
@@ -354,12 +355,12 @@ unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
 
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
                             unsigned long long* bitmap, const uint16_t* gene_genome,
-                            const unsigned long long* genome_code_base, const int64_t* gene_src, DevErr* err,
-                            cudaStream_t s) {
+                            const unsigned long long* genome_code_base, const int64_t* gene_src, int alpha,
+                            DevErr* err, cudaStream_t s) {
   const unsigned grid = grid_for((uint64_t)n_genes * 32, kEncThreads, 152u * 16u);
   PD_LAUNCH(L, "encode_mark", k_encode_mark<<<grid, kEncThreads, 0, s>>>(res, gene_ptr, n_genes, k, bitmap,
                                                                         gene_genome, genome_code_base, gene_src,
-                                                                        err));
+                                                                        alpha, err));
   return cudaSuccess;
 }
 

@@ -219,8 +219,12 @@ static constexpr uint64_t kMaxBitmapBytes = (uint64_t)4 << 30;
 
 pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                                      uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
-                                     const uint32_t* genome_seg, pd_profiles** out, const int64_t* gene_src) {
-  if (k < 1 || k > PD_MAX_K) return fail(c, PD_ERR_K_RANGE, "k must be in [1, " + std::to_string(PD_MAX_K) + "]");
+                                     const uint32_t* genome_seg, pd_profiles** out, const int64_t* gene_src,
+                                     int alphabet) {
+  if (alphabet != PD_ALPHABET_AMINO && alphabet != PD_ALPHABET_NUCLEOTIDE)
+    return fail(c, PD_ERR_ARG, "alphabet must be 20 (amino acids) or 4 (nucleotides)");
+  const int max_k = alphabet == PD_ALPHABET_AMINO ? PD_MAX_K : PD_MAX_K_NUCLEOTIDE;
+  if (k < 1 || k > max_k) return fail(c, PD_ERR_K_RANGE, "k must be in [1, " + std::to_string(max_k) + "]");
   if (!gene_ptr || !genome_ptr || (n_res > 0 && !residues))
     return fail(c, PD_ERR_ARG, "null residues, gene_ptr or genome_ptr");
   if (n_genomes < 1 || n_genomes > PD_MAX_GENOMES)
@@ -273,7 +277,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   P->ctx = c;
   P->h_genome_ptr = hgn;
   std::unique_ptr<pd_profiles> guard(P);
-  const uint64_t n_codes = pow_u64(20, k);
+  const uint64_t n_codes = pow_u64((uint64_t)alphabet, k);
   uint64_t n_seg = 1;
   std::vector<unsigned long long> code_base;
   if (genome_seg) {
@@ -332,7 +336,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   if (n_genes)
     CK(pdg::run_encode_mark(L, res_dev, gp_devp, n_genes, k, P->bitmap.as<unsigned long long>(),
                             P->gene_genome.as<uint16_t>(), d_code_base.as<unsigned long long>(), gene_src,
-                            c->d_err, c->stream));
+                            alphabet, c->d_err, c->stream));
   const uint32_t kOrderShift = 16;  // 65536 min-hash buckets
   const uint64_t n_order_b = (uint64_t)1 << (32 - kOrderShift);
   ALLOC(tmp, pdg::scan_temp_bytes(std::max<uint64_t>(std::max<uint64_t>(n_words, n_order_b), 24577)) + 64);
@@ -384,6 +388,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   M.gene_genome = P->gene_genome.as<uint16_t>();
   M.genome_code_base = d_code_base.as<unsigned long long>();
   M.gene_src = gene_src;
+  M.alpha = alphabet;
   if (n_genes)
     CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
                          P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), M,
@@ -462,6 +467,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   in.n_entries = E;
   in.max_posting = max_posting;
   in.count_bits = cnt_bits;
+  in.alphabet = alphabet;
   in.device_bytes = P->genome_ptr.n + P->La.n + P->win_off.n + P->mv_n.n + P->mv_id.n + P->mv_cnt.n +
                     P->mv_post.n + P->mv_plen.n + P->gene_genome.n + P->ginfo.n + P->bitmap.n + P->word_rank.n +
                     P->post_ptr.n + P->post.n + P->order.n;
@@ -480,6 +486,21 @@ PD_API pd_status pd_build_profiles(pd_ctx* c, const uint8_t* residues, uint64_t 
     return fail(c, PD_ERR_OOM, "host allocation failed");
   } catch (...) {
     return fail(c, PD_ERR_INTERNAL, "exception in pd_build_profiles");
+  }
+}
+
+PD_API pd_status pd_build_profiles_alphabet(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                                            uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes,
+                                            int alphabet, int k, pd_profiles** out) {
+  if (!c || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    return build_profiles_impl(c, residues, n_res, gene_ptr, n_genes, genome_ptr, n_genomes, k, nullptr, out,
+                               nullptr, alphabet);
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_build_profiles_alphabet");
   }
 }
 

@@ -168,7 +168,7 @@ inline pd_status check_dev_err(pd_ctx* c) {
     CK(cudaMemsetAsync(c->d_err, 0, sizeof(DevErr), c->stream));
     if (code == PD_ERR_ALPHABET)
       return fail(c, PD_ERR_ALPHABET, "residue at offset " + std::to_string(det) +
-                                          " is not one of ACDEFGHIKLMNPQRSTVWY");
+                                          " is not a letter of the alphabet (ACDEFGHIKLMNPQRSTVWY or ACGT)");
     return fail(c, (pd_status)code, "device reported error " + std::to_string(code) + " (detail " +
                                         std::to_string(det) + ")");
   }
@@ -223,7 +223,8 @@ namespace pdh {
 // gene_ptr then gives only the lengths, and residues must be a device pointer.
 pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                               uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
-                              const uint32_t* genome_seg, pd_profiles** out, const int64_t* gene_src = nullptr);
+                              const uint32_t* genome_seg, pd_profiles** out, const int64_t* gene_src = nullptr,
+                              int alphabet = PD_ALPHABET_AMINO);
 // Sum-min + Best Hits of the query set Q into H (all tiers, output sized
 // exactly).  genomes_per_query (0 = n_genomes - 1) bounds the genomes one
 // query can hit; it only sizes the first output allocation.

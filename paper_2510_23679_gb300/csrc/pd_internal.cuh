@@ -65,11 +65,13 @@ __host__ __device__ __forceinline__ uint32_t next_pow2(uint32_t x) {
   return x + 1;
 }
 
-// Letter -> 0..19 in ACDEFGHIKLMNPQRSTVWY order, 255 otherwise; built per block.
-__device__ __forceinline__ void init_letter_table(uint8_t* lut) {
+// Letter -> 0..alpha-1, 255 otherwise; built per block.  alpha 20: amino
+// acids in ACDEFGHIKLMNPQRSTVWY order; alpha 4: nucleotides in ACGT order.
+__device__ __forceinline__ void init_letter_table(uint8_t* lut, int alpha) {
   for (int i = threadIdx.x; i < 256; i += blockDim.x) lut[i] = 255;
   __syncthreads();
-  if (threadIdx.x < kAlphabetSize) lut[(uint8_t)("ACDEFGHIKLMNPQRSTVWY"[threadIdx.x])] = (uint8_t)threadIdx.x;
+  const char* letters = alpha == 4 ? "ACGT" : "ACDEFGHIKLMNPQRSTVWY";
+  if ((int)threadIdx.x < alpha) lut[(uint8_t)letters[threadIdx.x]] = (uint8_t)threadIdx.x;
   __syncthreads();
 }
 
@@ -251,8 +253,8 @@ cudaError_t scan_u32_to_u64(Launcher* L, const uint32_t* in, uint64_t n, unsigne
 // profiles (k_profiles.cu)
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
                             unsigned long long* bitmap, const uint16_t* gene_genome,
-                            const unsigned long long* genome_code_base, const int64_t* gene_src, DevErr* err,
-                            cudaStream_t s);
+                            const unsigned long long* genome_code_base, const int64_t* gene_src, int alpha,
+                            DevErr* err, cudaStream_t s);
 // Outputs of the multiplicity-vector build.
 struct MvOut {
   uint32_t* mv_id;
@@ -265,6 +267,7 @@ struct MvOut {
   const uint16_t* gene_genome;                 // genome of each gene
   const unsigned long long* genome_code_base;  // per genome: segment * 20^k, or null (one segment)
   const int64_t* gene_src;                     // per gene: first residue, or null (gene_ptr[g])
+  int alpha;                                   // alphabet size: 20 or 4
 };
 // Table slots used for a gene with La windows (genes above 16384 slots use
 // global scratch of that many 64-bit slots, listed in long_genes).

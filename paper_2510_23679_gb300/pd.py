@@ -42,7 +42,8 @@ class PdError(RuntimeError):
 class ProfilesInfo(C.Structure):
     _fields_ = [("k", C.c_int), ("n_genes", C.c_uint32), ("n_genomes", C.c_uint32),
                 ("n_windows", C.c_uint64), ("n_distinct", C.c_uint64), ("n_entries", C.c_uint64),
-                ("max_posting", C.c_uint32), ("count_bits", C.c_uint32), ("device_bytes", C.c_uint64)]
+                ("max_posting", C.c_uint32), ("count_bits", C.c_uint32), ("device_bytes", C.c_uint64),
+                ("alphabet", C.c_int)]
 
 
 class HitsInfo(C.Structure):
@@ -92,6 +93,8 @@ _SIGNATURES = [
     ("pd_ctx_reset_timing", C.c_int, [_P]),
     ("pd_choose_k", C.c_int, [C.c_uint64, C.c_int]),
     ("pd_build_profiles", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, C.c_int, _PP]),
+    ("pd_build_profiles_alphabet", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, C.c_int, C.c_int,
+                                             _PP]),
     ("pd_build_profiles_segmented", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, _P, C.c_int,
                                               _PP]),
     ("pd_profiles_get_info", C.c_int, [_P, C.POINTER(ProfilesInfo)]),
@@ -315,6 +318,22 @@ def pd_build_profiles(ctx: Ctx, residues, gene_ptr, genome_ptr, k: int) -> Profi
     st = _lib.pd_build_profiles(ctx.handle, _ptr(residues), n_res, _ptr(gene_ptr), n_genes, _ptr(genome_ptr),
                                 n_genomes, int(k), C.byref(h))
     _check(ctx, st, "pd_build_profiles")
+    return Profiles(ctx, h)
+
+
+PD_ALPHABET_AMINO = 20
+PD_ALPHABET_NUCLEOTIDE = 4
+PD_MAX_K_NUCLEOTIDE = 16
+
+
+def pd_build_profiles_alphabet(ctx: Ctx, residues, gene_ptr, genome_ptr, alphabet: int, k: int) -> Profiles:
+    """pd_build_profiles over 20 amino acids or 4 nucleotides (ACGT)."""
+    n_res = int(residues.shape[0])
+    h = C.c_void_p()
+    st = _lib.pd_build_profiles_alphabet(ctx.handle, _ptr(residues), n_res, _ptr(gene_ptr), int(gene_ptr.shape[0]) - 1,
+                                         _ptr(genome_ptr), int(genome_ptr.shape[0]) - 1, int(alphabet), int(k),
+                                         C.byref(h))
+    _check(ctx, st, "pd_build_profiles_alphabet")
     return Profiles(ctx, h)
 
 

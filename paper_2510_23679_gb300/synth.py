@@ -43,6 +43,11 @@ BACKGROUND = np.array([_BACKGROUND_PCT[chr(c)] for c in ALPHABET], dtype=np.floa
 BACKGROUND /= BACKGROUND.sum()
 _LETTERS = np.frombuffer(ALPHABET, dtype=np.uint8)
 
+# Nucleotide datasets: ACGT with 50% GC content.
+NT_ALPHABET = b"ACGT"
+NT_BACKGROUND = np.array([0.25, 0.25, 0.25, 0.25])
+_NT_LETTERS = np.frombuffer(NT_ALPHABET, dtype=np.uint8)
+
 
 @dataclass
 class Pangenome:
@@ -141,8 +146,8 @@ def _lengths(rng, n, dist):
     raise ValueError(f"unknown length distribution {dist!r}")
 
 
-def _random_codes(rng, n):
-    return rng.choice(20, size=n, p=BACKGROUND).astype(np.uint8)
+def _random_codes(rng, n, bg=BACKGROUND):
+    return rng.choice(len(bg), size=n, p=bg).astype(np.uint8)
 
 
 def generate(
@@ -159,6 +164,7 @@ def generate(
     singleton_frac: float,
     seed: int,
     name: str = "",
+    alphabet: str = "aa",
 ) -> Pangenome:
     """Draw a seeded pangenome.
 
@@ -170,10 +176,11 @@ def generate(
                       replacement from the non-core ones.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
+    bg, letters = (BACKGROUND, _LETTERS) if alphabet == "aa" else (NT_BACKGROUND, _NT_LETTERS)
     fam_len = _lengths(rng, n_families, length_dist)
     fam_ptr = np.zeros(n_families + 1, dtype=np.int64)
     np.cumsum(fam_len, out=fam_ptr[1:])
-    fam_seq = _random_codes(rng, int(fam_ptr[-1]))
+    fam_seq = _random_codes(rng, int(fam_ptr[-1]), bg)
     fam_sub = rng.uniform(0.0, subst_max, size=n_families)
     fam_indel = rng.uniform(0.0, indel_max, size=n_families)
     n_core = int(round(core_frac * n_families))
@@ -221,12 +228,12 @@ def generate(
     src = np.empty(N0, dtype=np.uint8)
     fam_mask = fam_of >= 0
     src[fam_mask] = fam_seq[fam_ptr[fam_of[fam_mask]] + pos_in_gene[fam_mask]]
-    src[~fam_mask] = _random_codes(rng, int((~fam_mask).sum()))
+    src[~fam_mask] = _random_codes(rng, int((~fam_mask).sum()), bg)
 
     # ---- substitutions (family copies only)
     sub_rate = np.where(fam_mask, fam_sub[np.maximum(fam_of, 0)], 0.0)
     hit = rng.random(N0) < sub_rate
-    src[hit] = _random_codes(rng, int(hit.sum()))
+    src[hit] = _random_codes(rng, int(hit.sum()), bg)
 
     # ---- single-residue indels (family copies only)
     indel_rate = np.where(fam_mask, fam_indel[np.maximum(fam_of, 0)], 0.0)
@@ -239,14 +246,14 @@ def generate(
     first = np.zeros(N0 + 1, dtype=np.int64)
     np.cumsum(reps, out=first[1:])
     ins_slots = first[:-1][insert] + 1
-    out[ins_slots] = _random_codes(rng, len(ins_slots))
+    out[ins_slots] = _random_codes(rng, len(ins_slots), bg)
     new_len = np.add.reduceat(reps, src_ptr[:-1]) if G else np.zeros(0, np.int64)
     new_len = np.where(src_len > 0, new_len, 0)
 
     gene_ptr = np.zeros(G + 1, dtype=np.int64)
     np.cumsum(new_len, out=gene_ptr[1:])
     return Pangenome(
-        residues=_LETTERS[out],
+        residues=letters[out],
         gene_ptr=gene_ptr,
         genome_ptr=np.asarray(gnm, dtype=np.int32),
         family=family.astype(np.int32),
@@ -254,7 +261,7 @@ def generate(
         params=dict(n_genomes=n_genomes, genes_per_genome=genes_per_genome, n_families=n_families,
                     length_dist=length_dist, core_frac=core_frac, accessory_draw=accessory_draw,
                     subst_max=subst_max, indel_max=indel_max, paralog_frac=paralog_frac,
-                    singleton_frac=singleton_frac, seed=seed),
+                    singleton_frac=singleton_frac, seed=seed, alphabet=alphabet),
     )
 
 
@@ -282,6 +289,13 @@ WORKLOADS = {
                         length_dist=("lognormal", 300, 0.5, 30, 2500), core_frac=0.25,
                         accessory_draw=None, subst_max=0.30, indel_max=0.05, paralog_frac=0.10,
                         singleton_frac=0.05, seed=3),
+    # Nucleotide stand-in: 8 genomes x Poisson(600) genes, gene lengths
+    # log-normal with median 900 nt (300 codons), clipped to 90..7500, ACGT at
+    # 50% GC, the pan50x3000 mutation model.
+    "nt8x600": dict(n_genomes=8, genes_per_genome=("poisson", 600), n_families=800,
+                    length_dist=("lognormal", 900, 0.5, 90, 7500), core_frac=0.4, accessory_draw=None,
+                    subst_max=0.30, indel_max=0.05, paralog_frac=0.10, singleton_frac=0.05, seed=6,
+                    alphabet="nt"),
 }
 
 

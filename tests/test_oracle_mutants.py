@@ -32,7 +32,7 @@ MUTANTS = {
         "      if (!contains(R->col_row, R->col_ptr[k], R->col_ptr[k + 1], (int32_t)l)) continue;\n",
         ""),
     "union_term_dropped": ("      smax += a->cnt[i];\n      ++i;\n    } else {", "      ++i;\n    } else {"),
-    "alphabet_unchecked": ("if (!valid_letter(residues[i])) {", "if (0) {"),
+    "alphabet_unchecked": ("if (!valid_letter(residues[i], alphabet)) {", "if (0) {"),
 }
 
 
