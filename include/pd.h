@@ -233,6 +233,28 @@ pd_status pd_bbh_all(pd_ctx* ctx, const pd_profiles* prof, const pd_hits* hits, 
  * b in G_gj), ascending. */
 pd_status pd_bbh(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32_t gj, pd_bbh_set** out);
 
+/* Candidate filters of Eqs. (6) and (7), applied before the Best Hit argmax:
+ * a pair (a, b) with s >= 1 stays a candidate only if
+ *   theta: |a| * theta_den >= theta_num * |b| and |b| * theta_den >= theta_num * |a|
+ *          (gene lengths in letters, Eq. (6));
+ *   tau:   p_k(a -> b) >= tau and p_k(b -> a) >= tau, where p_k(a -> b) is the
+ *          sum of mult_a(w) over the k-mers w shared with b, divided by
+ *          |a| - k + 1 (Eq. (7)), compared exactly as
+ *          p_num * tau_den >= tau_num * (|a| - k + 1).
+ * theta = theta_num / theta_den and tau = tau_num / tau_den must lie in [0, 1]
+ * (den >= 1); a numerator of 0 turns that filter off.  The paper gives no
+ * values; both default to off in every other call. */
+typedef struct {
+  uint32_t theta_num, theta_den;
+  uint32_t tau_num, tau_den;
+} pd_filter;
+
+/* pd_best_hits_all / pd_best_hits with the candidate filters; the results
+ * feed pd_bbh_all / are read with pd_hits_copy like the unfiltered ones. */
+pd_status pd_best_hits_all_filtered(pd_ctx* ctx, const pd_profiles* prof, const pd_filter* filter, pd_hits** out);
+pd_status pd_best_hits_filtered(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32_t gj,
+                                const pd_filter* filter, pd_hits** out);
+
 /* Within-genome (paralog) Best Hits: Eq. (8) with both genes in the same
  * genome, the gene itself excluded -- BH(a, G_i minus a) for every gene a of
  * every genome G_i, same candidate and tie rules as across genomes.  Rows are

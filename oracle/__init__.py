@@ -15,7 +15,8 @@ function follows the passage of the paper named in its docstring:
 * ``pair``         Algorithm 2 (S_ij, Best Hits of rows, Eq. (8)) and
                    Algorithm 3 (Bidirectional Best Hits, Eq. (9));
 * ``families``     phase (c): connected components of the BBH graph;
-* ``paralog_hits`` Eq. (8) within one genome (the gene itself excluded).
+* ``paralog_hits`` Eq. (8) within one genome (the gene itself excluded);
+* ``filtered_pair`` Algorithms 2-3 with the theta and tau filters of Eqs. (6)-(7).
 """
 from __future__ import annotations
 
@@ -62,6 +63,8 @@ def _load():
         lib.orc_choose_k.argtypes = [C.c_uint64, C.c_int]
         lib.orc_build.restype = P
         lib.orc_build.argtypes = [u8p, C.c_uint64, i64p, C.c_uint32, C.c_int, C.POINTER(C.c_int)]
+        lib.orc_directional.restype = C.c_int
+        lib.orc_directional.argtypes = [P, C.c_uint32, C.c_uint32, C.POINTER(C.c_uint32), C.POINTER(C.c_uint32)]
         lib.orc_build_alphabet.restype = P
         lib.orc_build_alphabet.argtypes = [u8p, C.c_uint64, i64p, C.c_uint32, C.c_int, C.c_int, C.POINTER(C.c_int)]
         lib.orc_free.argtypes = [P]
@@ -136,6 +139,14 @@ class Profiles:
         _lib.orc_mv_get(self._h, g, _ptr(kmers, C.c_uint8), _ptr(cnt, C.c_uint32))
         kb = kmers[: n * self.k].tobytes()
         return [kb[e * self.k:(e + 1) * self.k] for e in range(n)], cnt[:n].copy()
+
+    def directional(self, a: int, b: int):
+        """Eq. (7) numerators: (sum of mult_a, sum of mult_b) over the shared k-mers."""
+        x, y = C.c_uint32(0), C.c_uint32(0)
+        st = _lib.orc_directional(self._h, a, b, C.byref(x), C.byref(y))
+        if st != OK:
+            raise OracleError(st, "directional")
+        return x.value, y.value
 
     def summin(self, a: int, b: int):
         """(sum of min(mult) over shared k-mers, sum of max(mult) over the union)."""
@@ -292,3 +303,45 @@ def paralog_bbh(rows):
     """Eq. (9) inside a genome: pairs (a, b), a < b, each a Best Hit of the other."""
     sets = [set(c) for c, _ in rows]
     return [(a, b) for a in range(len(rows)) for b in sorted(sets[a]) if b > a and a in sets[b]]
+
+
+def filtered_pair(ds, gi: int, gj: int, k: int, theta=(0, 1), tau=(0, 1), alphabet: int = 20):
+    """Algorithms 2-3 for genomes gi, gj with the candidate filters of Eq. (6)
+    (length ratio theta) and Eq. (7) (directional similarity tau) applied
+    before the Best Hit argmax; theta and tau are (numerator, denominator),
+    numerator 0 = off.  Returns (row Best Hits, column Best Hits, BBH pairs) as
+    lists of local indices."""
+    sub = ds.subset([gi, gj])
+    prof = Profiles(sub.residues, sub.gene_ptr, k, alphabet)
+    R = pair(prof, sub.genome_ptr, 0, 1)
+    n_a, n_b = R.S.shape
+    glen = np.diff(sub.gene_ptr).astype(np.int64)
+
+    def candidate(a, b):
+        s = int(R.S[a, b])
+        if s < 1:
+            return False
+        la, lb = int(glen[a]), int(glen[n_a + b])
+        if theta[0] and (la * theta[1] < theta[0] * lb or lb * theta[1] < theta[0] * la):
+            return False
+        if tau[0]:
+            pa, pb = prof.directional(a, n_a + b)
+            if pa * tau[1] < tau[0] * (la - k + 1) or pb * tau[1] < tau[0] * (lb - k + 1):
+                return False
+        return True
+
+    cand = [[candidate(a, b) for b in range(n_b)] for a in range(n_a)]
+
+    def best_set(pairs):  # [(index, s, den)] -> indices at the maximum s / den
+        best, out = None, []
+        for x, s, d in pairs:
+            if best is None or s * best[1] > best[0] * d:
+                best, out = (s, d), [x]
+            elif s * best[1] == best[0] * d:
+                out.append(x)
+        return out
+
+    rows = [best_set([(b, int(R.S[a, b]), int(R.Den[a, b])) for b in range(n_b) if cand[a][b]]) for a in range(n_a)]
+    cols = [best_set([(a, int(R.S[a, b]), int(R.Den[a, b])) for a in range(n_a) if cand[a][b]]) for b in range(n_b)]
+    bbh = [(a, b) for a in range(n_a) for b in rows[a] if a in cols[b]]
+    return rows, cols, bbh

@@ -256,6 +256,32 @@ int orc_summin(const orc_profiles* P, uint32_t a, uint32_t b, uint32_t* s_min, u
   return pair_sums(&P->mv[a], &P->mv[b], P->k, s_min, s_max);
 }
 
+/* Eq. (7) numerators: the sum of mult_a(w) (and of mult_b(w)) over the
+ * k-mers w in both dictionaries, by the same walk over the two sorted MVs. */
+int orc_directional(const orc_profiles* P, uint32_t a, uint32_t b, uint32_t* pa, uint32_t* pb) {
+  if (a >= P->n_genes || b >= P->n_genes) return ORC_ERR_ARG;
+  const orc_mv* x = &P->mv[a];
+  const orc_mv* y = &P->mv[b];
+  uint32_t i = 0, j = 0;
+  uint64_t sa = 0, sb = 0;
+  while (i < x->n && j < y->n) {
+    int c = memcmp(x->res + x->start[i], y->res + y->start[j], (size_t)P->k);
+    if (c == 0) {
+      sa += x->cnt[i];
+      sb += y->cnt[j];
+      ++i;
+      ++j;
+    } else if (c < 0) {
+      ++i;
+    } else {
+      ++j;
+    }
+  }
+  *pa = (uint32_t)sa;
+  *pb = (uint32_t)sb;
+  return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /* One genome pair: S_ij, A_ij (rows), A_ji (columns), BBH                  */
 /* ------------------------------------------------------------------------ */

@@ -63,17 +63,30 @@ constexpr uint32_t kMaxProbe = 64;
 //   split (tiers 2 and 3): keys[] = b, vals[] = s.
 // Slots are found by multiplicative hashing (top bits of key * odd constant)
 // and linear probing.
-template <bool kPacked>
+template <bool kPacked, bool kFilter = false>
 struct Acc {
+  static_assert(!(kPacked && kFilter), "filtered queries use the split layout");
   uint32_t* keys;  // packed: slot words
   uint32_t* vals;  // split only
+  uint32_t* vpa;   // filtered only: sum of mult_a over the shared k-mers (Eq. (7) numerator, a -> b)
+  uint32_t* vpb;   // filtered only: sum of mult_b over the shared k-mers (b -> a)
   uint32_t cnt_bits;
   uint32_t hash_shift;  // 32 - log2(cap)
+
+  __device__ __forceinline__ void bump(uint32_t h, uint32_t m, uint32_t ca, uint32_t cb) const {
+    atomicAdd(&vals[h], m);
+    if (kFilter) {
+      atomicAdd(&vpa[h], ca);
+      atomicAdd(&vpb[h], cb);
+    }
+  }
 
   __device__ __forceinline__ uint32_t home(uint32_t key) const { return (key * 0x9E3779B1u) >> hash_shift; }
 
   // key: bkey (packed) or b (split).  Returns false after kMaxProbe probes.
-  __device__ __forceinline__ bool add(uint32_t mask, uint32_t key, uint32_t m) const {
+  // ca, cb (the two multiplicities) feed the directional sums of filtered queries.
+  __device__ __forceinline__ bool add(uint32_t mask, uint32_t key, uint32_t m, uint32_t ca = 0,
+                                      uint32_t cb = 0) const {
     uint32_t h = home(key);
     const uint32_t hi = ~((1u << cnt_bits) - 1u);
     for (uint32_t probe = 0; probe < kMaxProbe; ++probe) {
@@ -93,13 +106,13 @@ struct Acc {
         }
       } else {
         if (k == key) {
-          atomicAdd(&vals[h], m);
+          bump(h, m, ca, cb);
           return true;
         }
         if (k == kEmpty) {
           const uint32_t prev = atomicCAS(&keys[h], kEmpty, key);
           if (prev == kEmpty || prev == key) {
-            atomicAdd(&vals[h], m);
+            bump(h, m, ca, cb);
             return true;
           }
         }
@@ -122,8 +135,28 @@ struct Acc {
   __device__ __forceinline__ void clear(uint32_t h) const {
     keys[h] = kEmpty;
     if (!kPacked) vals[h] = 0;
+    if (kFilter) {
+      vpa[h] = 0;
+      vpb[h] = 0;
+    }
   }
 };
+
+// Eqs. (6) and (7) as candidate masks: lengths |g| = La + k - 1 (a candidate
+// shares a k-mer, so La >= 1 on both sides), directional sums against La.
+__device__ __forceinline__ bool filter_pass(const QuerySet& Q, uint32_t k, uint32_t La_a, uint32_t La_b, uint32_t pa,
+                                            uint32_t pb) {
+  if (Q.theta_num) {
+    const unsigned long long la = La_a + k - 1u, lb = La_b + k - 1u;
+    if (la * Q.theta_den < (unsigned long long)Q.theta_num * lb) return false;
+    if (lb * Q.theta_den < (unsigned long long)Q.theta_num * la) return false;
+  }
+  if (Q.tau_num) {
+    if ((unsigned long long)pa * Q.tau_den < (unsigned long long)Q.tau_num * La_a) return false;
+    if ((unsigned long long)pb * Q.tau_den < (unsigned long long)Q.tau_num * La_b) return false;
+  }
+  return true;
+}
 
 __device__ __forceinline__ uint32_t lower_bound_post(const uint32_t* __restrict__ post, uint32_t lo, uint32_t hi,
                                                      unsigned long long key) {
@@ -171,19 +204,21 @@ template <typename TIdx>
 struct Table {
   uint32_t* keys;
   uint32_t* vals;          // split layout only
+  uint32_t* vpa;           // filtered queries only
+  uint32_t* vpb;
   TIdx* used;              // capacity cap
   unsigned long long* out; // capacity out_cap
   uint32_t cap;            // power of two, a multiple of the block size
   uint32_t out_cap;
 };
 
-template <int kThreads, bool kEmitAll, bool kPacked, typename TIdx>
+template <int kThreads, bool kEmitAll, bool kPacked, bool kFilter, typename TIdx>
 __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P, const QuerySet& Q,
                                               const HitsOut& O, const TierIO& T, DevErr* err,
                                               const Table<TIdx>& tb, uint32_t* c_post, uint32_t* c_off,
                                               uint16_t* c_cnt, unsigned long long* best, Scalars* sh) {
   constexpr uint32_t kChunk = Chunk<kThreads>::kSize, kItems = Chunk<kThreads>::kItems;
-  const Acc<kPacked> acc{tb.keys, tb.vals, P.cnt_bits, 32u - (31u - (uint32_t)__clz(tb.cap))};
+  const Acc<kPacked, kFilter> acc{tb.keys, tb.vals, tb.vpa, tb.vpb, P.cnt_bits, 32u - (31u - (uint32_t)__clz(tb.cap))};
   unsigned long long* out = tb.out;
   const uint32_t mask = tb.cap - 1u;
   // ---- query gene, its output row and its targets
@@ -302,7 +337,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
             uint32_t cb = p & cnt_mask;
             if (cb == P.cnt_cap && cav[j] > cb) cb = mv_count_of(P, p >> P.cnt_bits, P.mv_id[m0 + c0 + ev[j]]);
             const uint32_t key = kPacked ? (p & ~cnt_mask) : (p >> P.cnt_bits);
-            if (!acc.add(mask, key, min(cav[j], cb))) sh->overflow = 1;
+            if (!acc.add(mask, key, min(cav[j], cb), cav[j], cb)) sh->overflow = 1;
           }
         }
       }
@@ -343,6 +378,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
         acc.get(tb.used[u], &b, &s);
         if ((Q.all_pairs && ((b >= own0 && b < own1) || b >= tend)) || b == self) continue;  // not a target
         const uint32_t gi = P.ginfo[b];
+        if (kFilter && !filter_pass(Q, P.k, La_a, gi & 0xFFFFu, acc.vpa[tb.used[u]], acc.vpb[tb.used[u]])) continue;
         const uint32_t den = La_a + (gi & 0xFFFFu) - s;
         best_update(&best[Q.all_pairs ? (gi >> 16) : 0u], s, den);
         if (Q.colbest) best_update(&Q.colbest[(size_t)b * Q.col_stride + col], s, den);
@@ -355,6 +391,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
         const uint32_t gi = P.ginfo[b];
         const unsigned long long bv = best[Q.all_pairs ? (gi >> 16) : 0u];
         if (!(Q.all_pairs && ((b >= own0 && b < own1) || b >= tend)) && b != self &&
+            (!kFilter || filter_pass(Q, P.k, La_a, gi & 0xFFFFu, acc.vpa[h], acc.vpb[h])) &&
             ratio_equal(s, La_a + (gi & 0xFFFFu) - s, (uint32_t)(bv >> 32), (uint32_t)bv)) {
           const uint32_t slot = atomicAdd(&sh->n_out, 1u);
           if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | s;
@@ -405,26 +442,29 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
 }
 
 // ---- shared-memory tiers: [table][chunk | (used list, hits)][best]
-template <int kThreads, uint32_t kCap, uint32_t kOutCap, bool kPacked>
+template <int kThreads, uint32_t kCap, uint32_t kOutCap, bool kPacked, bool kFilter = false>
 struct SmemTier {
   static_assert(kCap % kThreads == 0, "table must split evenly over the block");
   static_assert(kCap <= 65536, "slot indices are 16-bit");
-  static constexpr size_t kTable = (size_t)kCap * (kPacked ? 4 : 8);
+  static constexpr size_t kTable = (size_t)kCap * (kPacked ? 4 : (kFilter ? 16 : 8));
   static constexpr size_t kUsed = (size_t)kCap * 2;
   static constexpr size_t kAfterWalk = kUsed + (size_t)kOutCap * 8;
   static constexpr size_t kUnion = Chunk<kThreads>::kBytes > kAfterWalk ? Chunk<kThreads>::kBytes : kAfterWalk;
   static size_t bytes(uint32_t n_best) { return kTable + kUnion + (size_t)(n_best ? n_best : 1) * 8; }
 };
 
-template <int kThreads, int kMinBlocks, uint32_t kCap, uint32_t kOutCap, bool kPacked, bool kEmitAll>
+template <int kThreads, int kMinBlocks, uint32_t kCap, uint32_t kOutCap, bool kPacked, bool kEmitAll,
+          bool kFilter = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_summin_smem(ProfilesView P, QuerySet Q, HitsOut O,
                                                                       TierIO T, DevErr* err) {
-  using S = SmemTier<kThreads, kCap, kOutCap, kPacked>;
+  using S = SmemTier<kThreads, kCap, kOutCap, kPacked, kFilter>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Scalars sh;
   Table<uint16_t> tb;
   tb.keys = (uint32_t*)smem;
   tb.vals = kPacked ? nullptr : tb.keys + kCap;
+  tb.vpa = kFilter ? tb.vals + kCap : nullptr;
+  tb.vpb = kFilter ? tb.vpa + kCap : nullptr;
   tb.cap = kCap;
   tb.out_cap = kOutCap;
   unsigned char* uni = smem + S::kTable;
@@ -437,16 +477,20 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_summin_smem(ProfilesVi
   for (uint32_t h = threadIdx.x; h < kCap; h += kThreads) {
     tb.keys[h] = kEmpty;
     if (!kPacked) tb.vals[h] = 0;
+    if (kFilter) {
+      tb.vpa[h] = 0;
+      tb.vpb[h] = 0;
+    }
   }
   __syncthreads();
   const uint32_t n = T.in_list ? *T.in_count : Q.n_queries;
   for (uint32_t x = blockIdx.x; x < n; x += gridDim.x)
-    process_query<kThreads, kEmitAll, kPacked, uint16_t>(T.in_list ? T.in_list[x] : x, P, Q, O, T, err, tb, c_post,
+    process_query<kThreads, kEmitAll, kPacked, kFilter, uint16_t>(T.in_list ? T.in_list[x] : x, P, Q, O, T, err, tb, c_post,
                                                          c_off, c_cnt, best, &sh);
 }
 
 // ---- global-memory tier: table, used list and hit list of each block in scratch
-template <bool kEmitAll>
+template <bool kEmitAll, bool kFilter = false>
 __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet Q, HitsOut O, TierIO T,
                                                        BigScratch B, DevErr* err) {
   constexpr int kThreads = 256;
@@ -455,6 +499,8 @@ __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet 
   Table<uint32_t> tb;
   tb.keys = B.keys + (size_t)blockIdx.x * B.cap;
   tb.vals = B.vals + (size_t)blockIdx.x * B.cap;
+  tb.vpa = kFilter ? B.vpa + (size_t)blockIdx.x * B.cap : nullptr;
+  tb.vpb = kFilter ? B.vpb + (size_t)blockIdx.x * B.cap : nullptr;
   tb.used = B.used + (size_t)blockIdx.x * B.cap;
   tb.out = B.out + (size_t)blockIdx.x * B.out_cap;
   tb.cap = B.cap;
@@ -466,11 +512,15 @@ __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet 
   for (uint32_t h = threadIdx.x; h < B.cap; h += kThreads) {
     tb.keys[h] = kEmpty;
     tb.vals[h] = 0;
+    if (kFilter) {
+      tb.vpa[h] = 0;
+      tb.vpb[h] = 0;
+    }
   }
   __syncthreads();
   const uint32_t n = *T.in_count;
   for (uint32_t x = blockIdx.x; x < n; x += gridDim.x)
-    process_query<kThreads, kEmitAll, false, uint32_t>(T.in_list[x], P, Q, O, T, err, tb, c_post, c_off, c_cnt, best,
+    process_query<kThreads, kEmitAll, false, kFilter, uint32_t>(T.in_list[x], P, Q, O, T, err, tb, c_post, c_off, c_cnt, best,
                                                        &sh);
 }
 
@@ -487,6 +537,12 @@ using T2E = SmemTier<kT2Threads, kT2Cap, kT2OutEmit, false>;
 static_assert(T1::kTable + T1::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 1 shared memory");
 static_assert(T2::kTable + T2::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 2 shared memory");
 static_assert(T2E::kTable + T2E::kUnion + 8 <= 227 * 1024, "tier 2 (emit-all, one target genome) shared memory");
+// Filtered queries (Eqs. (6)-(7)): split 4096-slot table with the two
+// directional sums; what does not fit goes straight to the global tier.
+constexpr int kFThreads = 256, kFMinBlocks = 2;
+constexpr uint32_t kFCap = 4096, kFOut = 512;
+using TF = SmemTier<kFThreads, kFCap, kFOut, false, true>;
+static_assert(TF::kTable + TF::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "filtered tier shared memory");
 
 template <typename K>
 cudaError_t launch_smem(K kernel, Launcher* L, const char* name, int threads, size_t smem, uint32_t max_grid,
@@ -514,6 +570,12 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
                              bool emit_all, cudaStream_t s) {
   if (Q.n_queries == 0) return cudaSuccess;
   const uint32_t n_best = Q.all_pairs ? P.n_genomes : 1u;
+  if (Q.filter) {
+    if (emit_all) return cudaErrorInvalidValue;
+    TierIO tf{nullptr, nullptr, O.def2, O.n_def2};
+    return launch_smem(k_summin_smem<kFThreads, kFMinBlocks, kFCap, kFOut, false, false, true>, L, "summin_bh_f",
+                       kFThreads, TF::bytes(n_best), Q.n_queries, P, Q, O, tf, err, s);
+  }
   TierIO t1{nullptr, nullptr, O.def1, O.n_def1};
   TierIO t2{O.def1, O.n_def1, O.def2, O.n_def2};
   cudaError_t e;
@@ -543,8 +605,16 @@ cudaError_t run_summin_global(Launcher* L, const ProfilesView& P, const QuerySet
                               const BigScratch& B, uint32_t n_ctas, DevErr* err, bool emit_all, cudaStream_t s) {
   const size_t smem = summin_global_smem_bytes(Q.all_pairs ? P.n_genomes : 1u);
   TierIO t3{O.def2, O.n_def2, nullptr, nullptr};
-  const char* name = emit_all ? "summin_pairs_t3" : "summin_bh_t3";
+  const char* name = Q.filter ? "summin_bh_f_t3" : (emit_all ? "summin_pairs_t3" : "summin_bh_t3");
   cudaError_t e;
+  if (Q.filter) {
+    if (emit_all || !B.vpa || !B.vpb) return cudaErrorInvalidValue;
+    e = cudaFuncSetAttribute(k_summin_global<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_begin(L, name)) != cudaSuccess) return e;
+    k_summin_global<false, true><<<n_ctas, 256, smem, s>>>(P, Q, O, t3, B, err);
+    return launch_end(L, name);
+  }
   if (emit_all)
     e = cudaFuncSetAttribute(k_summin_global<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   else

@@ -671,9 +671,15 @@ pd_status pdh::run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& Q,
       B.cap = std::max<uint32_t>(pdg::next_pow2(4 * targets), 256);  // load <= 1/4: short probe chains
       B.out_cap = pdg::next_pow2(targets);
       const uint32_t n_ctas = std::min<uint32_t>(n_def2, 64);
-      Buf bk, bv, bu, bo;
+      Buf bk, bv, bu, bo, bpa, bpb;
       ALLOC(bk, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
       ALLOC(bv, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
+      if (Q.filter) {
+        ALLOC(bpa, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
+        ALLOC(bpb, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
+        B.vpa = bpa.as<uint32_t>();
+        B.vpb = bpb.as<uint32_t>();
+      }
       ALLOC(bu, sizeof(uint32_t) * (size_t)B.cap * n_ctas);
       ALLOC(bo, sizeof(unsigned long long) * (size_t)B.out_cap * n_ctas);
       B.keys = bk.as<uint32_t>();
@@ -866,6 +872,77 @@ PD_API pd_status pd_bbh_all(pd_ctx* c, const pd_profiles* P, const pd_hits* H, p
     return fail(c, PD_ERR_OOM, "host allocation failed");
   } catch (...) {
     return fail(c, PD_ERR_INTERNAL, "exception in pd_bbh_all");
+  }
+}
+
+static pd_status set_filter(pd_ctx* c, const pd_filter* f, pdg::QuerySet* Q) {
+  if (!f) return fail(c, PD_ERR_ARG, "null filter");
+  if (f->theta_den == 0 || f->tau_den == 0 || f->theta_num > f->theta_den || f->tau_num > f->tau_den)
+    return fail(c, PD_ERR_ARG, "theta and tau must be fractions in [0, 1] with a denominator >= 1");
+  Q->filter = 1;
+  Q->theta_num = f->theta_num;
+  Q->theta_den = f->theta_den;
+  Q->tau_num = f->tau_num;
+  Q->tau_den = f->tau_den;
+  return PD_OK;
+}
+
+PD_API pd_status pd_best_hits_all_filtered(pd_ctx* c, const pd_profiles* P, const pd_filter* f, pd_hits** out) {
+  if (!c || !P || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    CK(cudaSetDevice(c->device));
+    std::unique_ptr<pd_hits> H(new pd_hits());
+    H->ctx = c;
+    H->all_pairs = 1;
+    pdg::QuerySet Q{};
+    Q.all_pairs = 1;
+    Q.order = P->view.order;
+    Q.n_queries = P->view.n_genes;
+    pd_status st = set_filter(c, f, &Q);
+    if (st != PD_OK) return st;
+    if ((st = run_hits(c, P, Q, false, H.get())) != PD_OK) return st;
+    *out = H.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_best_hits_all_filtered");
+  }
+}
+
+PD_API pd_status pd_best_hits_filtered(pd_ctx* c, const pd_profiles* P, uint32_t gi, uint32_t gj, const pd_filter* f,
+                                       pd_hits** out) {
+  if (!c || !P || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    CK(cudaSetDevice(c->device));
+    const auto& gp = P->h_genome_ptr;
+    if (gi >= P->view.n_genomes || gj >= P->view.n_genomes || gi == gj)
+      return fail(c, PD_ERR_ARG, "genome indices must be distinct and < n_genomes");
+    std::unique_ptr<pd_hits> H(new pd_hits());
+    pdg::QuerySet Q{};
+    pd_status st = set_filter(c, f, &Q);
+    if (st != PD_OK) return st;
+    Q.all_pairs = 0;
+    Q.qa0 = (uint32_t)gp[gi];
+    Q.nA = (uint32_t)(gp[gi + 1] - gp[gi]);
+    Q.ta0 = (uint32_t)gp[gj];
+    Q.ta1 = (uint32_t)gp[gj + 1];
+    Q.n_queries = Q.nA;
+    H->ctx = c;
+    H->all_pairs = 0;
+    H->row_base = Q.qa0;
+    H->col_base = Q.ta0;
+    H->nA = Q.nA;
+    H->qa0 = Q.qa0;
+    if ((st = run_hits(c, P, Q, false, H.get())) != PD_OK) return st;
+    *out = H.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_best_hits_filtered");
   }
 }
 

@@ -199,6 +199,11 @@ struct QuerySet {
   // Within-genome form (pair indexing, row = q0 + query): each query gene is
   // compared with the other genes of its own genome (not with itself).
   int paralog;
+  // Candidate filters (filter != 0): the length threshold theta = theta_num /
+  // theta_den of Eq. (6) and the directional threshold tau = tau_num /
+  // tau_den of Eq. (7); a numerator of 0 turns a filter off.
+  int filter;
+  uint32_t theta_num, theta_den, tau_num, tau_den;
 };
 
 struct HitsOut {
@@ -224,6 +229,8 @@ struct BigScratch {
   unsigned long long* out;  // n_ctas * out_cap
   uint32_t cap;          // power of two
   uint32_t out_cap;
+  uint32_t* vpa = nullptr;  // filtered queries: n_ctas * cap directional sums (query side)
+  uint32_t* vpb = nullptr;  // ... (target side)
 };
 
 // Queries of one sum-min launch: the range 0..n_queries-1 (first tier) or a

@@ -51,6 +51,11 @@ class HitsInfo(C.Structure):
                 ("col_base", C.c_uint32), ("n_deferred", C.c_uint32), ("postings_walked", C.c_uint64)]
 
 
+class Filter(C.Structure):
+    _fields_ = [("theta_num", C.c_uint32), ("theta_den", C.c_uint32), ("tau_num", C.c_uint32),
+                ("tau_den", C.c_uint32)]
+
+
 class BatchTuning(C.Structure):
     _fields_ = [("max_chunk_windows", C.c_uint64), ("max_chunk_jobs", C.c_uint32), ("reserved", C.c_uint32)]
 
@@ -118,6 +123,8 @@ _SIGNATURES = [
     ("pd_batch_copy_hits", C.c_int, [_P, _P, _P, _P, _P]),
     ("pd_batch_copy_bbh", C.c_int, [_P, _P, _P, _P, _P]),
     ("pd_batch_free", None, [_P]),
+    ("pd_best_hits_all_filtered", C.c_int, [_P, _P, C.POINTER(Filter), _PP]),
+    ("pd_best_hits_filtered", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, C.POINTER(Filter), _PP]),
     ("pd_paralog_hits", C.c_int, [_P, _P, _PP]),
     ("pd_paralog_bbh", C.c_int, [_P, _P, _P, _PP]),
     ("pd_components", C.c_int, [_P, _P, _P, C.c_uint64, C.c_uint32, _P, C.POINTER(C.c_uint32)]),
@@ -429,6 +436,28 @@ def pd_bbh(ctx: Ctx, prof: Profiles, gi: int, gj: int) -> BbhSet:
     h = C.c_void_p()
     _check(ctx, _lib.pd_bbh(ctx.handle, prof.handle, int(gi), int(gj), C.byref(h)), "pd_bbh")
     return BbhSet(ctx, h)
+
+
+def _filter(theta, tau):
+    return Filter(int(theta[0]), int(theta[1]), int(tau[0]), int(tau[1]))
+
+
+def pd_best_hits_all_filtered(ctx: Ctx, prof: Profiles, theta=(0, 1), tau=(0, 1)) -> Hits:
+    """pd_best_hits_all with the theta (Eq. (6)) and tau (Eq. (7)) candidate
+    filters, each a (numerator, denominator) fraction; numerator 0 = off."""
+    h = C.c_void_p()
+    f = _filter(theta, tau)
+    _check(ctx, _lib.pd_best_hits_all_filtered(ctx.handle, prof.handle, C.byref(f), C.byref(h)),
+           "pd_best_hits_all_filtered")
+    return Hits(ctx, h)
+
+
+def pd_best_hits_filtered(ctx: Ctx, prof: Profiles, gi: int, gj: int, theta=(0, 1), tau=(0, 1)) -> Hits:
+    h = C.c_void_p()
+    f = _filter(theta, tau)
+    _check(ctx, _lib.pd_best_hits_filtered(ctx.handle, prof.handle, int(gi), int(gj), C.byref(f), C.byref(h)),
+           "pd_best_hits_filtered")
+    return Hits(ctx, h)
 
 
 def pd_paralog_hits(ctx: Ctx, prof: Profiles) -> Hits:
