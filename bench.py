@@ -60,6 +60,32 @@ def dist_info():
         int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x, world):
+    """The largest x over all ranks (the slowest rank's time)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return int(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([int(x)], dtype=torch.int64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return int(t.item())
+
+
+def whole_job_rate(units, seconds, world):
+    """Units processed by all ranks together / the slowest rank's time."""
+    return sum_over_ranks(units, world) / max_over_ranks(seconds, world)
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -287,9 +313,12 @@ def run_batch(args):
         per_pair = {"ms_per_step": pp_ms, "value": pairs / (pp_ms / 1e3), "unit": "gene-pairs/s",
                     "steps": 1, "bbh_pairs": n_pp}
 
+    value = whole_job_rate(pairs, ms / 1e3, world)
+    jobs_rate = whole_job_rate(args.jobs, ms / 1e3, world)
+    ms = max_over_ranks(ms, world)
     if rank == 0:
         line = {
-            "metric": "gene-pair GJ evals/s", "value": pairs * world / (ms / 1e3), "unit": "gene-pairs/s",
+            "metric": "gene-pair GJ evals/s", "value": value, "unit": "gene-pairs/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "impl": "batched",
@@ -299,7 +328,7 @@ def run_batch(args):
                        "n_jobs": args.jobs, "n_genes": ds.n_genes, "n_residues": ds.n_residues,
                        "logical_pairs_per_step": pairs, "l2": "flushed between steps",
                        "generation_s": gen_s},
-            "genome_pairs_per_s": args.jobs * world / (ms / 1e3),
+            "genome_pairs_per_s": jobs_rate,
             "step_ms": step_ms,
             "per_pair_launch": per_pair,
             "speedup_vs_per_pair": (per_pair["ms_per_step"] / ms) if per_pair else None,
@@ -474,14 +503,11 @@ def main():
     step_ms = [a.elapsed_time(b) for a, b in ev]
     k_ms, k_n = pd.pd_ctx_kernel_time(ctx, "summin_bh")
     pd.pd_ctx_set_timing(ctx, False)
-    ms_per_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms_per_step])
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
+    ms_local = sum(step_ms) / len(step_ms)
     pairs = ds.logical_pairs()
-    value = pairs * world / (ms_per_step / 1e3)
+    value = whole_job_rate(pairs, ms_local / 1e3, world)
+    ms_per_step = max_over_ranks(ms_local, world)
+    genome_pairs_all = sum_over_ranks(ds.n_genomes * (ds.n_genomes - 1) // 2, world)
 
     prof, hits, bbh = keep
     pinfo = pd.pd_profiles_get_info(prof)
@@ -535,13 +561,10 @@ def main():
             step_e2e()
             torch.cuda.synchronize()
             times.append(time.perf_counter() - t0)
-        e2e_s = sum(times) / len(times)
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e2e_s])
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": pairs * world / e2e_s, "unit": "gene-pairs/s",
+        e2e_local = sum(times) / len(times)
+        e2e_value = whole_job_rate(pairs, e2e_local, world)
+        e2e_s = max_over_ranks(e2e_local, world)
+        e2e = {"value": e2e_value, "unit": "gene-pairs/s",
                "h2d_bytes_per_step": int(ds.residues.nbytes + ds.gene_ptr.nbytes + ds.genome_ptr.nbytes),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
 
@@ -559,7 +582,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": config_of(ds, args.workload, k, f"flushed ({L2_FLUSH_BYTES >> 20} MB write) between steps"),
-            "genome_pairs_per_s": ds.n_genomes * (ds.n_genomes - 1) / 2 * world / (ms_per_step / 1e3),
+            "genome_pairs_per_s": genome_pairs_all / (ms_per_step / 1e3),
             "step_ms": step_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
