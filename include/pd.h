@@ -76,7 +76,8 @@ typedef struct pd_bbh_set pd_bbh_set;
 
 /* Device allocator hooks.  alloc returns a device pointer usable on `stream`
  * (aligned to at least 256 bytes) or NULL; free releases it.  Passing NULL
- * hooks selects cudaMallocAsync / cudaFreeAsync on the context's stream. */
+ * hooks gives the context a CUDA memory pool of its own (stream-ordered
+ * allocation, freed memory kept for reuse until the context is destroyed). */
 typedef void* (*pd_alloc_fn)(size_t bytes, void* stream, void* user);
 typedef void (*pd_free_fn)(void* ptr, size_t bytes, void* stream, void* user);
 

@@ -113,10 +113,25 @@ PD_API pd_status pd_ctx_create(int device, void* cuda_stream, pd_alloc_fn alloc,
   if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(DevErr));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(DevErr));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(DevErr));
+  if (e == cudaSuccess && !alloc) {
+    // Without hooks the context allocates from a pool of its own that keeps
+    // freed memory for reuse (no release back to the driver between calls).
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    e = cudaMemPoolCreate(&c->pool, &props);
+    if (e == cudaSuccess) {
+      c->own_pool = true;
+      uint64_t keep = ~0ull;
+      e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     if (c->d_err) cudaFree(c->d_err);
     if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->own_pool) cudaMemPoolDestroy(c->pool);
     delete c;
     return PD_ERR_CUDA;
   }
@@ -134,6 +149,8 @@ PD_API void pd_ctx_destroy(pd_ctx* c) {
   for (auto e : c->event_pool) cudaEventDestroy(e);
   cudaFree(c->d_err);
   cudaFreeHost(c->h_err);
+  // allocations still held by handles keep the pool alive until they are freed
+  if (c->own_pool) cudaMemPoolDestroy(c->pool);
   delete c;
 }
 

@@ -48,6 +48,7 @@ struct pd_ctx {
   pdg::DevErr* d_err = nullptr;  // device error block
   pdg::DevErr* h_err = nullptr;  // pinned host mirror
   cudaMemPool_t pool = nullptr;  // without hooks: allocate from this pool (null: the device's default pool)
+  bool own_pool = false;         // the pool was created by (and is destroyed with) this context
   uint64_t pool_bytes = 0;       // bytes currently allocated through this context (pool allocations only)
 };
 

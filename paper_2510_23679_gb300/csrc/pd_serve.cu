@@ -154,14 +154,12 @@ uint64_t windows_of(const std::vector<int64_t>& gp, size_t g0, size_t g1, int k)
 struct pd_index {
   pd_ctx* c = nullptr;  // worker context: own stream and memory pool
   cudaStream_t stream = nullptr;
-  cudaMemPool_t pool = nullptr;
   int device = 0, k = 0;
   uint64_t budget = 0;
   uint32_t max_tick = 64;
   // resident data (owned by the worker once it runs)
   Buf res;
   uint64_t res_used = 0;
-  uint64_t res_windows = 0;
   std::vector<int64_t> gene_ptr;
   std::vector<int32_t> genome_ptr;
   std::unique_ptr<pd_profiles> P;
@@ -195,7 +193,6 @@ struct pd_index {
       cudaStreamSynchronize(stream);
       pd_ctx_destroy(c);
     }
-    if (pool) cudaMemPoolDestroy(pool);
     if (stream) cudaStreamDestroy(stream);
   }
 };
@@ -448,17 +445,11 @@ pd_status index_create(pd_ctx* caller, const uint8_t* residues, uint64_t n_res, 
   I->budget = hbm_budget;
   CK(cudaSetDevice(I->device));
   CK(cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking));
-  cudaMemPoolProps props = {};
-  props.allocType = cudaMemAllocationTypePinned;
-  props.location.type = cudaMemLocationTypeDevice;
-  props.location.id = I->device;
-  CK(cudaMemPoolCreate(&I->pool, &props));
-  uint64_t keep = hbm_budget;
-  CK(cudaMemPoolSetAttribute(I->pool, cudaMemPoolAttrReleaseThreshold, &keep));
   pd_status st = pd_ctx_create(I->device, I->stream, nullptr, nullptr, nullptr, &I->c);
   if (st != PD_OK) return fail(caller, st, "could not create the index context");
-  I->c->pool = I->pool;
   c = I->c;
+  uint64_t keep = hbm_budget;  // the index's pool keeps up to the budget for reuse
+  CK(cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep));
   // resident offsets on the host
   I->gene_ptr.resize(n_genes + 1);
   I->genome_ptr.resize(n_genomes + 1);

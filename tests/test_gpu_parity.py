@@ -238,3 +238,32 @@ def test_saturated_posting_counts_and_long_genes(ctx):
     assert run.bbh(0, 1) == [(0, 0)]
     _, _, gen, cnt = pd.pd_profiles_copy_index(ctx, run.prof)
     assert sorted(cnt.tolist()) == [1, 17000, 20000]
+
+
+@pytest.mark.parametrize("n_genes", [40, 3000, 20000])
+def test_index_lists_of_every_length(ctx, n_genes):
+    """Posting lists from 1 to n_genes entries (short lists, block-sorted lists
+    and, past 8192 entries, lists sorted in global memory) come out in gene
+    order with the right counts."""
+    rng = np.random.default_rng(n_genes)
+    letters = np.frombuffer(b"ACDEFGHIKLMNPQRSTVWY", np.uint8)
+    genes = []
+    for g in range(n_genes):
+        tail = letters[rng.integers(0, 20, size=int(rng.integers(0, 12)))].tobytes()
+        genes.append(b"ACDEF" * int(1 + g % 3) + tail)  # every gene holds ACD, CDE, DEF
+    ds = synth.from_strings([genes[: n_genes // 2], genes[n_genes // 2:]])
+    k = 3
+    prof = pd.pd_build_profiles(ctx, ds.residues, ds.gene_ptr, ds.genome_ptr, k)
+    post_ptr, codes, g_out, c_out = pd.pd_profiles_copy_index(ctx, prof)
+    ref = oracle.Profiles(ds.residues, ds.gene_ptr, k)
+    expect = {}
+    for g in range(ds.n_genes):
+        kmers, cnt = ref.mv(g)
+        for km, c in zip(kmers, cnt):
+            expect.setdefault(km, []).append((g, int(c)))
+    from tests._gpu import decode_code
+    got = {decode_code(int(codes[w]), k): list(zip(g_out[post_ptr[w]:post_ptr[w + 1]].tolist(),
+                                                   c_out[post_ptr[w]:post_ptr[w + 1]].tolist()))
+           for w in range(len(codes))}
+    assert got == expect
+    assert max(len(v) for v in expect.values()) == n_genes
