@@ -262,8 +262,13 @@ def run_batch(args):
     gn_d = torch.from_numpy(gnm).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
+    # autotune on a sample of the jobs, then run the whole batch with the winner
+    t_tune = time.perf_counter()
+    tuning, tune_ms_per_job = pd.pd_batch_autotune(ctx, res_d, gp_d, gn_d, jobs, ks, n_sample=min(100, args.jobs))
+    tune_s = time.perf_counter() - t_tune
+
     def step_batch():
-        return pd.pd_bbh_batch(ctx, res_d, gp_d, gn_d, jobs, ks)
+        return pd.pd_bbh_batch(ctx, res_d, gp_d, gn_d, jobs, ks, **tuning)
 
     for _ in range(args.warmup):
         step_batch()
@@ -330,6 +335,8 @@ def run_batch(args):
                        "generation_s": gen_s},
             "genome_pairs_per_s": jobs_rate,
             "step_ms": step_ms,
+            "tuning": tuning, "autotune": {"sample_jobs": min(100, args.jobs), "seconds": tune_s,
+                                            "best_ms_per_sampled_job": tune_ms_per_job},
             "per_pair_launch": per_pair,
             "speedup_vs_per_pair": (per_pair["ms_per_step"] / ms) if per_pair else None,
             "gpu_launches": gpu_launches,

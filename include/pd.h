@@ -308,7 +308,8 @@ typedef struct {
   uint32_t max_chunk_jobs;    /* jobs per chunk (default: as many as the 256 MiB
                                  chunk dictionary bitmap holds at the job's k,
                                  at most PD_MAX_GENOMES / 2) */
-  uint32_t reserved;
+  uint32_t query_order;       /* sum-min work queue: 0 = length buckets (longest
+                                 first), min-hash inside a bucket; 1 = min-hash only */
 } pd_batch_tuning;
 
 typedef struct {
@@ -338,6 +339,17 @@ pd_status pd_bbh_batch(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res, con
                        uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* jobs,
                        const int32_t* job_k, uint32_t n_jobs, const pd_batch_tuning* tuning, pd_batch** out);
 pd_status pd_batch_get_info(const pd_batch* batch, pd_batch_info* info);
+/* Autotuner of pd_bbh_batch: runs the first n_sample jobs (0 = min(n_jobs,
+ * 100)) once with each candidate tuning (jobs per chunk 8 / 32 / bitmap
+ * default, windows per chunk 2^28 / 2^29, both query orders), timed with CUDA
+ * events on the context's stream after one warm-up, and writes the fastest to
+ * *best (and its time per sampled job, in milliseconds, to *ms_per_job if not
+ * NULL).  Results never depend on the tuning, only the time does.  Arguments
+ * as pd_bbh_batch. */
+pd_status pd_batch_autotune(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                            uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* jobs,
+                            const int32_t* job_k, uint32_t n_jobs, uint32_t n_sample, pd_batch_tuning* best,
+                            double* ms_per_job);
 /* Best Hits of every job as one CSR: the rows of job j are the genes of A then
  * the genes of B (jobs in order); row_ptr n_rows+1 int64; cols int32, the
  * column's index inside the partner genome (B for rows of A, A for rows of B);

@@ -23,9 +23,12 @@
 //   mv_post        each multiplicity-vector entry gets its posting range, so
 //                  the sum-min kernel reads list bounds from its own
 //                  (coalesced) vector instead of the id offset table.
-//   order          queries ordered by min-hash buckets: genes that share their
-//                  minimum hashed k-mer (likely homologs) run together and
-//                  share posting lists in L2.
+//   order          queries ordered by length bucket (at least 1024, 512, 256
+//                  distinct k-mers, then the rest: longest first, so the
+//                  persistent sum-min launch ends on short queries) and within
+//                  a bucket by min-hash: genes that share their minimum hashed
+//                  k-mer (likely homologs) run together and share posting
+//                  lists in L2.
 #include "pd_internal.cuh"
 
 namespace pdg {
@@ -162,7 +165,10 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
   __syncthreads();
   if (threadIdx.x == 0) {
     M.mv_n[g] = E;
-    M.minhash[g] = warp_tmp[0];
+    // query order key: optionally a length bucket (longest first) in the top
+    // two bits, then the min-hash
+    const uint32_t lb = E >= 1024u ? 0u : (E >= 512u ? 1u : (E >= 256u ? 2u : 3u));
+    M.minhash[g] = M.length_buckets ? (lb << 30) | (warp_tmp[0] >> 2) : warp_tmp[0];
   }
   __syncthreads();
 }

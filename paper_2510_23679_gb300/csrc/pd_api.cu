@@ -237,7 +237,7 @@ static constexpr uint64_t kMaxBitmapBytes = (uint64_t)4 << 30;
 pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                                      uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
                                      const uint32_t* genome_seg, pd_profiles** out, const int64_t* gene_src,
-                                     int alphabet) {
+                                     int alphabet, int length_buckets) {
   if (alphabet != PD_ALPHABET_AMINO && alphabet != PD_ALPHABET_NUCLEOTIDE)
     return fail(c, PD_ERR_ARG, "alphabet must be 20 (amino acids) or 4 (nucleotides)");
   const int max_k = alphabet == PD_ALPHABET_AMINO ? PD_MAX_K : PD_MAX_K_NUCLEOTIDE;
@@ -406,6 +406,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   M.genome_code_base = d_code_base.as<unsigned long long>();
   M.gene_src = gene_src;
   M.alpha = alphabet;
+  M.length_buckets = length_buckets;
   if (n_genes)
     CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
                          P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), M,

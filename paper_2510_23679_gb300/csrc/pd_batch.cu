@@ -257,8 +257,10 @@ pd_status batch_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const i
     if (!src.empty())
       CK(cudaMemcpyAsync(d_src.p, src.data(), sizeof(int64_t) * src.size(), cudaMemcpyHostToDevice, c->stream));
     pd_profiles* Praw = nullptr;
+    const int length_buckets = (tuning && tuning->query_order == 1) ? 0 : 1;
     pd_status st = build_profiles_impl(c, res_dev, (uint64_t)cg.back(), cg.data(), chunk_genes, cgn.data(),
-                                       (uint32_t)genomes.size(), k, seg.data(), &Praw, d_src.as<int64_t>());
+                                       (uint32_t)genomes.size(), k, seg.data(), &Praw, d_src.as<int64_t>(),
+                                       PD_ALPHABET_AMINO, length_buckets);
     if (st != PD_OK) return st;
     std::unique_ptr<pd_profiles> P(Praw);
 
@@ -360,6 +362,55 @@ PD_API pd_status pd_bbh_batch(pd_ctx* c, const uint8_t* residues, uint64_t n_res
     return fail(c, PD_ERR_OOM, "host allocation failed");
   } catch (...) {
     return fail(c, PD_ERR_INTERNAL, "exception in pd_bbh_batch");
+  }
+}
+
+PD_API pd_status pd_batch_autotune(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
+                                   uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes,
+                                   const uint32_t* jobs, const int32_t* job_k, uint32_t n_jobs, uint32_t n_sample,
+                                   pd_batch_tuning* best, double* ms_per_job) {
+  if (!c || !best) return PD_ERR_ARG;
+  try {
+    CK(cudaSetDevice(c->device));
+    const uint32_t ns = std::min<uint32_t>(n_jobs, n_sample ? n_sample : 100u);
+    if (ns == 0) return fail(c, PD_ERR_ARG, "no jobs to sample");
+    std::vector<pd_batch_tuning> cand;
+    for (uint32_t order : {0u, 1u})
+      for (uint64_t w : {1ull << 28, 1ull << 29})
+        for (uint32_t j : {8u, 32u, 0u}) cand.push_back(pd_batch_tuning{w, j, order});
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = -1.f;
+    pd_status st = PD_OK;
+    for (size_t x = 0; x < cand.size() && st == PD_OK; ++x) {
+      for (int rep = 0; rep < 2 && st == PD_OK; ++rep) {  // one warm-up, one timed run
+        pd_batch* B = nullptr;
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail_cuda(c, cudaGetLastError(), "event");
+        if (st == PD_OK)
+          st = batch_impl(c, residues, n_res, gene_ptr, n_genes, genome_ptr, n_genomes, jobs, job_k, ns, &cand[x],
+                          &B);
+        if (st == PD_OK && cudaEventRecord(e1, c->stream) != cudaSuccess)
+          st = fail_cuda(c, cudaGetLastError(), "event");
+        if (st == PD_OK && cudaEventSynchronize(e1) != cudaSuccess) st = fail_cuda(c, cudaGetLastError(), "event");
+        float ms = 0.f;
+        if (st == PD_OK && rep == 1 && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess &&
+            (best_ms < 0.f || ms < best_ms)) {
+          best_ms = ms;
+          *best = cand[x];
+        }
+        pd_batch_free(B);
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != PD_OK) return st;
+    if (ms_per_job) *ms_per_job = best_ms / ns;
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_batch_autotune");
   }
 }
 

@@ -225,7 +225,7 @@ namespace pdh {
 pd_status build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                               uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
                               const uint32_t* genome_seg, pd_profiles** out, const int64_t* gene_src = nullptr,
-                              int alphabet = PD_ALPHABET_AMINO);
+                              int alphabet = PD_ALPHABET_AMINO, int length_buckets = 1);
 // Sum-min + Best Hits of the query set Q into H (all tiers, output sized
 // exactly).  genomes_per_query (0 = n_genomes - 1) bounds the genomes one
 // query can hit; it only sizes the first output allocation.

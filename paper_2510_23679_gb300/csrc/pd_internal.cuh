@@ -275,6 +275,7 @@ struct MvOut {
   const unsigned long long* genome_code_base;  // per genome: segment * 20^k, or null (one segment)
   const int64_t* gene_src;                     // per gene: first residue, or null (gene_ptr[g])
   int alpha;                                   // alphabet size: 20 or 4
+  int length_buckets;                          // query order: length buckets first (1) or min-hash only (0)
 };
 // Table slots used for a gene with La windows (genes above 16384 slots use
 // global scratch of that many 64-bit slots, listed in long_genes).

@@ -57,7 +57,7 @@ class Filter(C.Structure):
 
 
 class BatchTuning(C.Structure):
-    _fields_ = [("max_chunk_windows", C.c_uint64), ("max_chunk_jobs", C.c_uint32), ("reserved", C.c_uint32)]
+    _fields_ = [("max_chunk_windows", C.c_uint64), ("max_chunk_jobs", C.c_uint32), ("query_order", C.c_uint32)]
 
 
 class BatchInfo(C.Structure):
@@ -120,6 +120,8 @@ _SIGNATURES = [
     ("pd_bbh_batch", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, _P, _P, C.c_uint32,
                                C.POINTER(BatchTuning), _PP]),
     ("pd_batch_get_info", C.c_int, [_P, C.POINTER(BatchInfo)]),
+    ("pd_batch_autotune", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, _P, _P, C.c_uint32,
+                                    C.c_uint32, C.POINTER(BatchTuning), C.POINTER(C.c_double)]),
     ("pd_batch_copy_hits", C.c_int, [_P, _P, _P, _P, _P]),
     ("pd_batch_copy_bbh", C.c_int, [_P, _P, _P, _P, _P]),
     ("pd_batch_free", None, [_P]),
@@ -518,7 +520,7 @@ def pd_best_hits_noalloc(ctx: Ctx, prof: Profiles, gi: int, gj: int, row_ptr, co
 
 
 def pd_bbh_batch(ctx: Ctx, residues, gene_ptr, genome_ptr, jobs, job_k, max_chunk_windows: int = 0,
-                 max_chunk_jobs: int = 0) -> Batch:
+                 max_chunk_jobs: int = 0, query_order: int = 0) -> Batch:
     """Best Hits (both directions) and BBH of many genome-pair jobs: jobs is a
     host array [n_jobs, 2] of genome indices, job_k the k of each job."""
     n_res = int(residues.shape[0])
@@ -528,13 +530,28 @@ def pd_bbh_batch(ctx: Ctx, residues, gene_ptr, genome_ptr, jobs, job_k, max_chun
     kk = np.ascontiguousarray(job_k, dtype=np.int32)
     if jb.shape[0] != 2 * kk.shape[0]:
         raise ValueError("jobs must have two genome indices per entry of job_k")
-    tun = BatchTuning(int(max_chunk_windows), int(max_chunk_jobs), 0)
+    tun = BatchTuning(int(max_chunk_windows), int(max_chunk_jobs), int(query_order))
     h = C.c_void_p()
     st = _lib.pd_bbh_batch(ctx.handle, _ptr(residues), n_res, _ptr(gene_ptr), n_genes, _ptr(genome_ptr), n_genomes,
                            _ptr(jb) if jb.size else None, _ptr(kk) if kk.size else None, int(kk.shape[0]),
                            C.byref(tun), C.byref(h))
     _check(ctx, st, "pd_bbh_batch")
     return Batch(ctx, h)
+
+
+def pd_batch_autotune(ctx: Ctx, residues, gene_ptr, genome_ptr, jobs, job_k, n_sample: int = 0):
+    """Time candidate tunings on the first n_sample jobs; returns (dict of the
+    fastest tuning, usable as pd_bbh_batch keywords, ms per sampled job)."""
+    jb = np.ascontiguousarray(jobs, dtype=np.uint32).reshape(-1)
+    kk = np.ascontiguousarray(job_k, dtype=np.int32)
+    best = BatchTuning()
+    ms = C.c_double(0)
+    _check(ctx, _lib.pd_batch_autotune(ctx.handle, _ptr(residues), int(residues.shape[0]), _ptr(gene_ptr),
+                                       int(gene_ptr.shape[0]) - 1, _ptr(genome_ptr), int(genome_ptr.shape[0]) - 1,
+                                       _ptr(jb), _ptr(kk), int(kk.shape[0]), int(n_sample), C.byref(best),
+                                       C.byref(ms)), "pd_batch_autotune")
+    return ({"max_chunk_windows": int(best.max_chunk_windows), "max_chunk_jobs": int(best.max_chunk_jobs),
+             "query_order": int(best.query_order)}, float(ms.value))
 
 
 def pd_batch_get_info(batch: Batch) -> BatchInfo:

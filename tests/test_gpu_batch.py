@@ -96,8 +96,8 @@ def test_sampled_jobs_against_oracle(ctx, batch_data, j):
 
 
 def test_mixed_k_and_shared_genomes(ctx, batch_data):
-    """Jobs in any genome order (reversed pairs, a genome in several jobs)
-    take the gather path; k differs between jobs."""
+    """Jobs in any genome order (reversed pairs, a genome in several jobs) are
+    read in place through per-gene offsets; k differs between jobs."""
     ds, _, _ = batch_data
     jobs = np.array([[1, 0], [3, 0], [5, 4], [0, 5], [9, 2], [2, 9]], np.uint32)
     ks = np.array([3, 4, 5, 4, 6, 3], np.int32)
@@ -150,3 +150,14 @@ def test_segmented_profiles_match_separate_builds(ctx, batch_data):
         b1 = pd.pd_bbh_copy(ctx, pd.pd_bbh_all(ctx, p1, pd.pd_best_hits_all(ctx, p1)))
         sel = (bbh[:, 0] >= g0) & (bbh[:, 0] < g1)
         assert (bbh[sel] - g0).tolist() == b1.tolist()
+
+
+def test_query_order_and_autotuner(ctx, batch_data):
+    ds, jobs, ks = batch_data
+    a, _ = _run_batch(ctx, ds, jobs, ks, query_order=0)
+    b, _ = _run_batch(ctx, ds, jobs, ks, query_order=1, max_chunk_jobs=4)
+    assert a == b
+    best, ms = pd.pd_batch_autotune(ctx, ds.residues, ds.gene_ptr, ds.genome_ptr, jobs, ks, n_sample=12)
+    assert best["query_order"] in (0, 1) and best["max_chunk_jobs"] in (0, 8, 32) and ms > 0
+    c, _ = _run_batch(ctx, ds, jobs, ks, **best)
+    assert c == a
