@@ -167,15 +167,14 @@ __device__ __forceinline__ uint32_t lower_bound_post(const uint32_t* __restrict_
   return lo;
 }
 
+// Exact multiplicity of k-mer id in gene g, for a saturated packed count.
+// A multiplicity vector is stored in hash order, so this is a linear scan
+// (rare: only counts at the cap of the packed field come here).
 __device__ __forceinline__ uint32_t mv_count_of(const ProfilesView& P, uint32_t g, uint32_t id) {
-  uint32_t lo = P.win_off[g];
-  const uint32_t end = lo + P.mv_n[g];
-  uint32_t hi = end;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) >> 1;
-    if (P.mv_id[mid] < id) lo = mid + 1; else hi = mid;
-  }
-  return (lo < end && P.mv_id[lo] == id) ? P.mv_cnt[lo] : 0u;
+  const uint32_t off = P.win_off[g], n = P.mv_n[g];
+  for (uint32_t e = 0; e < n; ++e)
+    if (P.mv_id[off + e] == id) return P.mv_cnt[off + e];
+  return 0u;
 }
 
 // Max of (s, den) pairs by cross-multiplication, packed as s << 32 | den.

@@ -240,6 +240,30 @@ def test_saturated_posting_counts_and_long_genes(ctx):
     assert sorted(cnt.tolist()) == [1, 17000, 20000]
 
 
+@pytest.mark.parametrize("letter", "AHMRWY")
+def test_saturated_count_in_a_gene_with_many_kmers(ctx, letter):
+    """The exact count behind a saturated posting is looked up in the target
+    gene's multiplicity vector, which is stored in hash order: a target with
+    many distinct k-mers besides the saturated one must still be found, for
+    small, middle and large k-mer ids."""
+    n_empty = 70000
+    sat = letter.encode()
+    other = b"W" if sat != b"W" else b"A"
+    tail = bytes(c for c in b"ACDEFGHIKLMNPQRSTVWY" if c != sat[0])
+    target = sat * 20000 + tail * 3
+    query = sat * 17000 + other
+    ds = synth.from_strings([[query] + [b""] * n_empty, [target] + [b""] * n_empty])
+    run = GpuRun(ctx, ds, 1)
+    assert run.info.count_bits == 14
+    pair = synth.from_strings([[query], [target]])
+    prof = oracle.Profiles(pair.residues, pair.gene_ptr, 1)
+    s, _ = prof.summin(0, 1)
+    assert s == 17001
+    assert run.summin(0, 1) == {(0, 0): s}
+    assert run.summin(1, 0) == {(0, 0): s}
+    assert run.bbh(0, 1) == [(0, 0)]
+
+
 @pytest.mark.parametrize("n_genes", [40, 3000, 20000])
 def test_index_lists_of_every_length(ctx, n_genes):
     """Posting lists from 1 to n_genes entries (short lists, block-sorted lists
