@@ -398,6 +398,10 @@ typedef struct {
  * its Bidirectional Best Hits (Eq. (9)) with those genomes; after answering,
  * the genome becomes resident (genome id = n_genomes at that moment, genes
  * appended in order).
+ * The resident genomes are indexed in two levels (a base, and a delta of the
+ * genomes inserted since the base was built, merged into a new base once it
+ * holds a quarter of the base's windows); a request's genes are profiled
+ * against each level's dictionary.
  * A worker thread of the library admits queued requests in arrival order while
  * its estimate of device memory (resident residues and index, the rebuild and
  * the tick's outputs) stays within hbm_budget bytes, and answers all admitted
@@ -410,7 +414,7 @@ pd_status pd_index_create(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res, 
                           uint64_t hbm_budget, pd_index** out);
 /* Queue one genome (HOST buffers, copied before return): residues and its
  * gene_ptr (n_genes+1 int64 from 0 to n_res).  *ticket identifies the request.
- * Errors: PD_ERR_ARG (malformed), PD_ERR_GENE_TOO_LONG, PD_ERR_BUDGET (this
+ * Errors: PD_ERR_ARG (malformed), PD_ERR_ALPHABET, PD_ERR_GENE_TOO_LONG, PD_ERR_BUDGET (this
  * genome cannot fit the budget next to the resident index), PD_ERR_BUSY (the
  * index would exceed PD_MAX_GENOMES). */
 pd_status pd_index_submit(pd_index* index, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,

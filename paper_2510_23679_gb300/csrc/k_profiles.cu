@@ -117,6 +117,7 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
       const uint32_t c = lut[s[p + t]];
       code = code * (unsigned long long)M.alpha + (c < (uint32_t)M.alpha ? c : 0u);
     }
+    if (M.frozen && !((bitmap[(code + base) >> 6] >> ((code + base) & 63u)) & 1ull)) continue;  // not in that dictionary
     const uint32_t id = code_rank(code + base, bitmap, word_rank);
     uint32_t h = mix32(id) & (cap - 1u);
     uint32_t probe = 0;
@@ -151,11 +152,12 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
     const uint32_t id = (uint32_t)(v >> 32), c = (uint32_t)v;
     M.mv_id[off + pos] = id;
     M.mv_cnt[off + pos] = (uint16_t)c;
-    M.rec[off + pos] = ((unsigned long long)id << 32) | (g << M.cnt_bits) | (c < M.cnt_cap ? c : M.cnt_cap);
+    if (M.rec) M.rec[off + pos] = ((unsigned long long)id << 32) | (g << M.cnt_bits) | (c < M.cnt_cap ? c : M.cnt_cap);
     mh = min(mh, mix32(id));
     ++pos;
   }
-  for (uint32_t p = E + threadIdx.x; p < La; p += blockDim.x) M.rec[off + p] = kFree;
+  if (M.rec)
+    for (uint32_t p = E + threadIdx.x; p < La; p += blockDim.x) M.rec[off + p] = kFree;
   // block minimum of the hashed ids (warp_tmp is free again after the scan)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) mh = min(mh, __shfl_xor_sync(0xffffffffu, mh, o));
@@ -168,7 +170,7 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
     // query order key: optionally a length bucket (longest first) in the top
     // two bits, then the min-hash
     const uint32_t lb = E >= 1024u ? 0u : (E >= 512u ? 1u : (E >= 256u ? 2u : 3u));
-    M.minhash[g] = M.length_buckets ? (lb << 30) | (warp_tmp[0] >> 2) : warp_tmp[0];
+    if (M.minhash) M.minhash[g] = M.length_buckets ? (lb << 30) | (warp_tmp[0] >> 2) : warp_tmp[0];
   }
   __syncthreads();
 }

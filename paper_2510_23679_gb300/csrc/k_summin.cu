@@ -226,11 +226,18 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
   if (Q.all_pairs) {
     a = Q.order ? Q.order[qi] : Q.q0 + qi;
     row = a;
-    const uint32_t gg = P.gene_genome[a];
-    own0 = (uint32_t)P.genome_ptr[gg];
-    own1 = (uint32_t)P.genome_ptr[gg + 1];
-    if (Q.tgt_end) tend = Q.tgt_end[gg];
-    col = gg - Q.col_genome0;
+    if (Q.q_genome) {  // external query: no own genome among the targets
+      const uint32_t x = Q.q_genome[a];
+      own0 = own1 = kEmpty;
+      if (Q.tgt_end) tend = Q.tgt_end[x];
+      col = x;
+    } else {
+      const uint32_t gg = P.gene_genome[a];
+      own0 = (uint32_t)P.genome_ptr[gg];
+      own1 = (uint32_t)P.genome_ptr[gg + 1];
+      if (Q.tgt_end) tend = Q.tgt_end[gg];
+      col = gg - Q.col_genome0;
+    }
   } else {
     uint32_t tlo, thi;
     if (Q.paralog) {
@@ -252,7 +259,14 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
     key_lo = (unsigned long long)tlo << P.cnt_bits;
     key_hi = (unsigned long long)thi << P.cnt_bits;
   }
-  const uint32_t m0 = P.win_off[a], E = P.mv_n[a], La_a = P.La[a];
+  // the query's own vector (its dataset's, or the external query arrays)
+  const bool ext = P.q_win_off != nullptr;
+  const uint32_t* __restrict__ q_mv_id = ext ? P.q_mv_id : P.mv_id;
+  const uint16_t* __restrict__ q_mv_cnt = ext ? P.q_mv_cnt : P.mv_cnt;
+  const uint32_t* __restrict__ q_mv_post = ext ? P.q_mv_post : P.mv_post;
+  const uint32_t* __restrict__ q_mv_plen = ext ? P.q_mv_plen : P.mv_plen;
+  const uint32_t m0 = (ext ? P.q_win_off : P.win_off)[a], E = (ext ? P.q_mv_n : P.mv_n)[a];
+  const uint32_t La_a = (ext ? P.q_La : P.La)[a];
   const uint32_t cnt_mask = (1u << P.cnt_bits) - 1u;
   const uint32_t tid = threadIdx.x;
   if (tid == 0) {
@@ -272,14 +286,14 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
       const uint32_t e = tid * kItems + r;
       uint32_t len = 0;
       if (e < n_c) {
-        uint32_t lo = P.mv_post[m0 + c0 + e];
-        uint32_t hi = lo + P.mv_plen[m0 + c0 + e];
+        uint32_t lo = q_mv_post[m0 + c0 + e];
+        uint32_t hi = lo + q_mv_plen[m0 + c0 + e];
         if (!Q.all_pairs) {
           lo = lower_bound_post(P.post, lo, hi, key_lo);
           hi = lower_bound_post(P.post, lo, hi, key_hi);
         }
         c_post[e] = lo;
-        c_cnt[e] = P.mv_cnt[m0 + c0 + e];
+        c_cnt[e] = q_mv_cnt[m0 + c0 + e];
         len = hi - lo;
       }
       len_loc[r] = len;
@@ -334,7 +348,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
           if (j < nb) {
             const uint32_t p = pv[j];
             uint32_t cb = p & cnt_mask;
-            if (cb == P.cnt_cap && cav[j] > cb) cb = mv_count_of(P, p >> P.cnt_bits, P.mv_id[m0 + c0 + ev[j]]);
+            if (cb == P.cnt_cap && cav[j] > cb) cb = mv_count_of(P, p >> P.cnt_bits, q_mv_id[m0 + c0 + ev[j]]);
             const uint32_t key = kPacked ? (p & ~cnt_mask) : (p >> P.cnt_bits);
             if (!acc.add(mask, key, min(cav[j], cb), cav[j], cb)) sh->overflow = 1;
           }

@@ -407,6 +407,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   M.gene_src = gene_src;
   M.alpha = alphabet;
   M.length_buckets = length_buckets;
+  M.frozen = 0;
   if (n_genes)
     CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
                          P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), M,
@@ -640,12 +641,25 @@ PD_API pd_status pd_profiles_copy_index(pd_ctx* c, const pd_profiles* P, int64_t
 // ------------------------------------------------------------------ sum-min + Best Hits
 // Runs the shared-memory tiers, then (only if needed) the global-memory tier
 // for the queries they deferred, growing the output until every row fits.
+static pd_status run_hits_on(pd_ctx* c, const pdg::ProfilesView& v, const pdg::QuerySet& Q, bool emit_all,
+                             pd_hits* H, uint32_t genomes_per_query);
+
 pd_status pdh::run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& Q, bool emit_all, pd_hits* H,
                         uint32_t genomes_per_query) {
-  const pdg::ProfilesView& v = P->view;
+  return run_hits_on(c, P->view, Q, emit_all, H, genomes_per_query);
+}
+
+pd_status pdh::run_hits_view(pd_ctx* c, const pdg::ProfilesView& v, const pdg::QuerySet& Q, pd_hits* H,
+                             uint32_t genomes_per_query) {
+  return run_hits_on(c, v, Q, false, H, genomes_per_query);
+}
+
+static pd_status run_hits_on(pd_ctx* c, const pdg::ProfilesView& v, const pdg::QuerySet& Q, bool emit_all,
+                             pd_hits* H, uint32_t genomes_per_query) {
   pdg::Launcher* L = &c->L;
   const uint32_t nq = Q.n_queries;
-  const uint32_t n_rows = Q.all_pairs ? v.n_genes : nq;
+  // rows: the dataset's genes (all-pairs), or one per query (pair form, external queries)
+  const uint32_t n_rows = (Q.all_pairs && !Q.q_genome) ? v.n_genes : nq;
   uint64_t cap;
   if (Q.all_pairs)
     cap = (uint64_t)nq * std::max<uint32_t>(genomes_per_query ? genomes_per_query : v.n_genomes - 1, 1) * 3 / 2 +
@@ -719,6 +733,101 @@ pd_status pdh::run_hits(pd_ctx* c, const pd_profiles* P, const pdg::QuerySet& Q,
     cap = h[0] + 4096;  // output did not fit: rerun with the exact size
   }
   return fail(c, PD_ERR_INTERNAL, "Best Hit output did not converge");
+}
+
+pdg::ProfilesView pdh::external_view(const pd_profiles* P, const QueryProfiles& Qp) {
+  pdg::ProfilesView v = P->view;
+  v.q_win_off = Qp.win_off.as<uint32_t>();
+  v.q_mv_n = Qp.mv_n.as<uint32_t>();
+  v.q_mv_id = Qp.mv_id.as<uint32_t>();
+  v.q_mv_cnt = Qp.mv_cnt.as<uint16_t>();
+  v.q_mv_post = Qp.mv_post.as<uint32_t>();
+  v.q_mv_plen = Qp.mv_plen.as<uint32_t>();
+  v.q_La = Qp.La.as<uint32_t>();
+  return v;
+}
+
+pd_status pdh::query_profiles_impl(pd_ctx* c, const pd_profiles* P, const uint8_t* residues_dev,
+                                   const int64_t* gene_ptr, uint32_t n_genes, QueryProfiles* Qp) {
+  const pdg::ProfilesView& v = P->view;
+  const int k = v.k;
+  pdg::Launcher* L = &c->L;
+  std::vector<uint32_t> La(n_genes), win_off(n_genes + 1);
+  std::vector<uint32_t> mid, lng;
+  std::vector<unsigned long long> lng_off;
+  uint64_t W = 0, lng_total = 0;
+  for (uint32_t g = 0; g < n_genes; ++g) {
+    const int64_t len = gene_ptr[g + 1] - gene_ptr[g];
+    if (len < 0) return fail(c, PD_ERR_ARG, "gene_ptr is decreasing");
+    const uint64_t w = len >= k ? (uint64_t)(len - k + 1) : 0;
+    if (w > PD_MAX_WINDOWS) return fail(c, PD_ERR_GENE_TOO_LONG, "a query gene has too many windows");
+    La[g] = (uint32_t)w;
+    win_off[g] = (uint32_t)W;
+    W += w;
+    if (W > 0xFFFFFFF0ull) return fail(c, PD_ERR_ARG, "more than 2^32 query windows");
+    const uint32_t cap = pdg::mv_build_table_cap((uint32_t)w);
+    if (cap > 16384) {
+      lng.push_back(g);
+      lng_off.push_back(lng_total);
+      lng_total += cap;
+    } else if (cap > 2048) {
+      mid.push_back(g);
+    }
+  }
+  win_off[n_genes] = (uint32_t)W;
+  const size_t G1 = std::max<uint32_t>(n_genes, 1), W1 = std::max<uint64_t>(W, 1);
+  Qp->n_genes = n_genes;
+  Buf d_gp, d_mid, d_long, d_long_off, d_long_scratch, dummy;
+  ALLOC(d_gp, sizeof(int64_t) * (n_genes + 1));
+  ALLOC(Qp->win_off, sizeof(uint32_t) * (n_genes + 1));
+  ALLOC(Qp->La, sizeof(uint32_t) * G1);
+  ALLOC(Qp->mv_n, sizeof(uint32_t) * G1);
+  ALLOC(Qp->mv_id, sizeof(uint32_t) * W1);
+  ALLOC(Qp->mv_cnt, sizeof(uint16_t) * W1);
+  ALLOC(Qp->mv_post, sizeof(uint32_t) * W1);
+  ALLOC(Qp->mv_plen, sizeof(uint32_t) * W1);
+  ALLOC(dummy, 16);
+  CK(cudaMemcpyAsync(d_gp.p, gene_ptr, sizeof(int64_t) * (n_genes + 1), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(Qp->win_off.p, win_off.data(), sizeof(uint32_t) * (n_genes + 1), cudaMemcpyHostToDevice,
+                     c->stream));
+  if (n_genes) CK(cudaMemcpyAsync(Qp->La.p, La.data(), sizeof(uint32_t) * n_genes, cudaMemcpyHostToDevice, c->stream));
+  if (!mid.empty()) {
+    ALLOC(d_mid, sizeof(uint32_t) * mid.size());
+    CK(cudaMemcpyAsync(d_mid.p, mid.data(), sizeof(uint32_t) * mid.size(), cudaMemcpyHostToDevice, c->stream));
+  }
+  if (!lng.empty()) {
+    ALLOC(d_long, sizeof(uint32_t) * lng.size());
+    ALLOC(d_long_off, sizeof(unsigned long long) * lng_off.size());
+    ALLOC(d_long_scratch, sizeof(unsigned long long) * lng_total);
+    CK(cudaMemcpyAsync(d_long.p, lng.data(), sizeof(uint32_t) * lng.size(), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d_long_off.p, lng_off.data(), sizeof(unsigned long long) * lng_off.size(),
+                       cudaMemcpyHostToDevice, c->stream));
+  }
+  pdg::MvOut M{};
+  M.mv_id = Qp->mv_id.as<uint32_t>();
+  M.mv_cnt = Qp->mv_cnt.as<uint16_t>();
+  M.mv_n = Qp->mv_n.as<uint32_t>();
+  M.rec = nullptr;
+  M.minhash = nullptr;
+  M.cnt_bits = v.cnt_bits;
+  M.cnt_cap = v.cnt_cap;
+  M.err = c->d_err;
+  M.gene_genome = nullptr;
+  M.genome_code_base = nullptr;
+  M.gene_src = nullptr;
+  M.alpha = P->info.alphabet;
+  M.length_buckets = 0;
+  M.frozen = 1;
+  if (n_genes) {
+    CK(pdg::run_mv_build(L, residues_dev, d_gp.as<int64_t>(), Qp->win_off.as<uint32_t>(), n_genes, k, v.bitmap,
+                         v.word_rank, M, d_mid.as<uint32_t>(), (uint32_t)mid.size(), d_long.as<uint32_t>(),
+                         (uint32_t)lng.size(), d_long_scratch.as<unsigned long long>(),
+                         d_long_off.as<unsigned long long>(), c->stream));
+    CK(pdg::run_mv_post(L, Qp->win_off.as<uint32_t>(), Qp->mv_n.as<uint32_t>(), Qp->mv_id.as<uint32_t>(), n_genes,
+                        v.post_ptr, Qp->mv_post.as<uint32_t>(), Qp->mv_plen.as<uint32_t>(), dummy.as<uint32_t>(),
+                        c->stream));
+  }
+  return check_dev_err(c);  // synchronizes: the host offsets and temporaries end here
 }
 
 static pd_status hits_pair_impl(pd_ctx* c, const pd_profiles* P, uint32_t gi, uint32_t gj, bool both, bool emit_all,

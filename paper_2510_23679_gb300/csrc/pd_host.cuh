@@ -215,8 +215,27 @@ struct pd_bbh_set {
 };
 
 
+// Genes profiled against another dataset's dictionary (external queries):
+// their vectors hold only k-mers that dataset contains, with posting ranges
+// into its index, while La counts every window.
+struct QueryProfiles {
+  uint32_t n_genes = 0;
+  Buf win_off, mv_n, mv_id, mv_cnt, mv_post, mv_plen, La;
+};
+
 // ------------------------------------------------------------------ internal entry points (pd_api.cu)
 namespace pdh {
+
+// Profiles of n_genes genes (residues on the device, gene_ptr on the host from
+// 0) against the dictionary and index of P; windows with letters outside the
+// alphabet must have been rejected by the caller.
+pd_status query_profiles_impl(pd_ctx* c, const pd_profiles* P, const uint8_t* residues_dev, const int64_t* gene_ptr,
+                              uint32_t n_genes, QueryProfiles* out);
+// P's view with the external query arrays of Qp.
+pdg::ProfilesView external_view(const pd_profiles* P, const QueryProfiles& Qp);
+// run_hits on an explicit view (external queries).
+pd_status run_hits_view(pd_ctx* c, const pdg::ProfilesView& v, const pdg::QuerySet& Q, pd_hits* H,
+                        uint32_t genomes_per_query);
 
 // Profiles of a dataset; genome_seg (host, per genome, or null) gives each
 // segment its own k-mer namespace.  gene_src (device, per gene, or null):

@@ -173,6 +173,17 @@ struct ProfilesView {
   const uint32_t* post_ptr;     // [D+1]
   const uint32_t* post;         // [E]   packed postings
   const uint32_t* order;        // [G]   all-pairs query order (min-hash buckets)
+  // External queries (null = queries are genes of this dataset): genes
+  // profiled against this dataset's dictionary but not part of it; query a
+  // reads its vector from these arrays (indexed like the ones above, by the
+  // query's own numbering) while targets stay this dataset's genes.
+  const uint32_t* q_win_off;
+  const uint32_t* q_mv_n;
+  const uint32_t* q_mv_id;
+  const uint16_t* q_mv_cnt;
+  const uint32_t* q_mv_post;
+  const uint32_t* q_mv_plen;
+  const uint32_t* q_La;
 };
 
 // Target selection of one sum-min launch.
@@ -199,6 +210,10 @@ struct QuerySet {
   // Within-genome form (pair indexing, row = q0 + query): each query gene is
   // compared with the other genes of its own genome (not with itself).
   int paralog;
+  // External queries (with the q_* arrays of the view): the genome of each
+  // query gene among the queries' own genomes; it has no own-genome targets,
+  // tgt_end and the colbest column are indexed by it.
+  const uint32_t* q_genome;
   // Candidate filters (filter != 0): the length threshold theta = theta_num /
   // theta_den of Eq. (6) and the directional threshold tau = tau_num /
   // tau_den of Eq. (7); a numerator of 0 turns a filter off.
@@ -276,6 +291,8 @@ struct MvOut {
   const int64_t* gene_src;                     // per gene: first residue, or null (gene_ptr[g])
   int alpha;                                   // alphabet size: 20 or 4
   int length_buckets;                          // query order: length buckets first (1) or min-hash only (0)
+  int frozen;                                  // 1: the bitmap is another dataset's dictionary; windows
+                                               // whose code it lacks are left out of the vector
 };
 // Table slots used for a gene with La windows (genes above 16384 slots use
 // global scratch of that many 64-bit slots, listed in long_genes).

@@ -9,14 +9,21 @@
 //   * submit copies the genome to the host queue and stamps it with the
 //     resident set it will be compared with (its snapshot: the genomes
 //     resident at submission);
+//   * the resident genomes are indexed in two levels: a base index and a
+//     delta index of the genomes inserted since the base was built.  After
+//     each tick the delta is rebuilt over the new residents, or, once its
+//     windows pass a quarter of the base's, everything is merged into a new
+//     base -- so a tick never rebuilds the whole resident set;
 //   * continuous batching: whenever the GPU is free the worker admits queued
 //     requests in arrival order while the HBM estimate of the tick stays within
-//     the budget, and runs them together -- one profile build over the resident
-//     genomes plus the tick's genomes (this build is also the insertion: the
-//     tick's genomes are resident afterwards), ONE sum-min / Best Hit launch
-//     sequence over the genes of every admitted genome, one mutual-check pass;
+//     the budget, and runs them together: per level, the tick's genes are
+//     profiled against the level's dictionary (k-mers the level does not hold
+//     are left out of the walk but count in La) and ONE sum-min / Best Hit
+//     launch sequence answers every gene of every admitted genome against it;
 //   * each query is limited to the genes of its snapshot, so a result does not
 //     depend on which other requests shared its tick;
+//   * every resident genome lies in exactly one level, so the Best Hits of a
+//     row are the union of the levels' rows (base genes first);
 //   * the reverse direction of Eq. (9) -- is a among the Best Hits of b in X?
 //     -- needs, for every resident gene b, its best ratio over the genes of X.
 //     The sum-min kernel keeps that maximum per (b, X) in global memory while
@@ -75,23 +82,22 @@ uint64_t tick_bytes(uint64_t W, uint64_t G, uint64_t tick_genes, uint64_t res_ge
 }
 
 // Mutual check of the served Best Hits: warp per row of the tick.
-__global__ void k_serve_bbh_count(uint32_t n_rows, uint32_t g0, const unsigned long long* __restrict__ row_ptr,
+__global__ void k_serve_bbh_count(uint32_t n_rows, const unsigned long long* __restrict__ row_ptr,
                                   const int32_t* __restrict__ cols, const uint32_t* __restrict__ s,
-                                  const uint32_t* __restrict__ La, const uint16_t* __restrict__ gene_genome,
-                                  uint32_t col_genome0, uint32_t stride,
+                                  const uint32_t* __restrict__ La_q, const uint32_t* __restrict__ La_t,
+                                  const uint32_t* __restrict__ q_genome, uint32_t stride,
                                   const unsigned long long* __restrict__ colbest, uint8_t* __restrict__ flag,
                                   uint32_t* __restrict__ cnt) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += warps) {
-    const uint32_t a = g0 + r;
-    const uint32_t x = gene_genome[a] - col_genome0;
+    const uint32_t x = q_genome[r];
     const unsigned long long lo = row_ptr[r], hi = row_ptr[r + 1];
     uint32_t n = 0;
     for (unsigned long long i = lo + lane; i < hi; i += 32) {
       const uint32_t b = (uint32_t)cols[i], sv = s[i];
       const unsigned long long cb = colbest[(size_t)b * stride + x];
-      const bool f = pdg::ratio_equal(sv, La[a] + La[b] - sv, (uint32_t)(cb >> 32), (uint32_t)cb);
+      const bool f = pdg::ratio_equal(sv, La_q[r] + La_t[b] - sv, (uint32_t)(cb >> 32), (uint32_t)cb);
       flag[i] = f ? 1 : 0;
       n += f ? 1u : 0u;
     }
@@ -151,6 +157,16 @@ uint64_t windows_of(const std::vector<int64_t>& gp, size_t g0, size_t g1, int k)
 
 }  // namespace
 
+// One level of the resident index: the profiles of resident genomes
+// [genome0, genome1) (genes [gene0, gene1), global numbering).
+struct Level {
+  std::unique_ptr<pd_profiles> P;
+  uint32_t genome0 = 0, genome1 = 0, gene0 = 0, gene1 = 0;
+  uint64_t windows = 0;
+  bool empty() const { return !P || gene1 == gene0; }
+  uint64_t bytes() const { return P ? P->info.device_bytes : 0; }
+};
+
 struct pd_index {
   pd_ctx* c = nullptr;  // worker context: own stream and memory pool
   cudaStream_t stream = nullptr;
@@ -162,7 +178,8 @@ struct pd_index {
   uint64_t res_used = 0;
   std::vector<int64_t> gene_ptr;
   std::vector<int32_t> genome_ptr;
-  std::unique_ptr<pd_profiles> P;
+  std::vector<uint64_t> genome_windows;  // windows of each resident genome at k
+  Level base, delta;
   // shared with the API threads
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
@@ -188,7 +205,8 @@ struct pd_index {
     if (worker.joinable()) worker.join();
     if (c) {
       cudaSetDevice(device);
-      P.reset();
+      base.P.reset();
+      delta.P.reset();
       res.release();
       cudaStreamSynchronize(stream);
       pd_ctx_destroy(c);
@@ -199,13 +217,158 @@ struct pd_index {
 
 namespace {
 
-// Appends the genomes of `tick` to the resident data, rebuilds the index over
-// all of them and answers every request of the tick.
+// Profiles of resident genomes [g0, g1) as one level.
+pd_status build_level(pd_index* I, uint32_t g0, uint32_t g1, Level* L) {
+  pd_ctx* c = I->c;
+  L->P.reset();
+  L->genome0 = g0;
+  L->genome1 = g1;
+  L->gene0 = (uint32_t)I->genome_ptr[g0];
+  L->gene1 = (uint32_t)I->genome_ptr[g1];
+  L->windows = 0;
+  for (uint32_t i = g0; i < g1; ++i) L->windows += I->genome_windows[i];
+  if (g1 == g0 || L->gene1 == L->gene0) return PD_OK;
+  const int64_t r0 = I->gene_ptr[L->gene0];
+  std::vector<int64_t> gp(I->gene_ptr.begin() + L->gene0, I->gene_ptr.begin() + L->gene1 + 1);
+  for (auto& x : gp) x -= r0;
+  std::vector<int32_t> gn(I->genome_ptr.begin() + g0, I->genome_ptr.begin() + g1 + 1);
+  for (auto& x : gn) x -= (int32_t)L->gene0;
+  pd_profiles* P = nullptr;
+  pd_status st = build_profiles_impl(c, I->res.as<uint8_t>() + r0, (uint64_t)gp.back(), gp.data(),
+                                     L->gene1 - L->gene0, gn.data(), g1 - g0, I->k, nullptr, &P);
+  if (st != PD_OK) return st;
+  L->P.reset(P);
+  return PD_OK;
+}
+
+// Brings the levels up to the committed genomes: rebuild the delta over the
+// genomes after the base, or merge everything into a new base once the delta
+// holds more than a quarter of the base's windows.
+pd_status refresh_levels(pd_index* I) {
+  const uint32_t n = (uint32_t)I->genome_ptr.size() - 1;
+  const uint32_t nb = I->base.genome1;
+  if (I->delta.genome0 == nb && I->delta.genome1 == n && (I->delta.P || nb == n)) return PD_OK;
+  uint64_t dw = 0;
+  for (uint32_t i = nb; i < n; ++i) dw += I->genome_windows[i];
+  I->delta.P.reset();
+  if (4 * dw > I->base.windows) {
+    I->base.P.reset();
+    pd_status st = build_level(I, 0, n, &I->base);
+    if (st != PD_OK) return st;
+    I->delta = Level();
+    I->delta.genome0 = I->delta.genome1 = n;
+    I->delta.gene0 = I->delta.gene1 = (uint32_t)I->genome_ptr[n];
+    return PD_OK;
+  }
+  return build_level(I, nb, n, &I->delta);
+}
+
+// One level's answer for the tick's genes: rows in CSR (level-local target
+// ids) and the BBH pairs (tick row, level-local target), on the host.
+struct LevelAnswer {
+  std::vector<unsigned long long> rp;
+  std::vector<int32_t> cols, pa, pb;
+  std::vector<uint32_t> s;
+};
+
+pd_status answer_level(pd_index* I, const Level& L, const uint8_t* tick_res, const std::vector<int64_t>& tick_gp,
+                       const std::vector<uint32_t>& q_genome, const std::vector<uint32_t>& snap_gene_end,
+                       LevelAnswer* out) {
+  pd_ctx* c = I->c;
+  const uint32_t n_q = (uint32_t)tick_gp.size() - 1, n_tick = (uint32_t)snap_gene_end.size();
+  out->rp.assign(n_q + 1, 0);
+  if (L.empty() || n_q == 0) return PD_OK;
+  const uint32_t nL = L.gene1 - L.gene0;
+  QueryProfiles Qp;
+  pd_status st = query_profiles_impl(c, L.P.get(), tick_res, tick_gp.data(), n_q, &Qp);
+  if (st != PD_OK) return st;
+  const pdg::ProfilesView V = external_view(L.P.get(), Qp);
+  std::vector<uint32_t> tgt_end(n_tick);
+  for (uint32_t x = 0; x < n_tick; ++x)
+    tgt_end[x] = snap_gene_end[x] <= L.gene0 ? 0u : std::min<uint32_t>(snap_gene_end[x], L.gene1) - L.gene0;
+  Buf order, d_qg, d_tgt, colbest;
+  ALLOC(order, sizeof(uint32_t) * n_q);
+  ALLOC(d_qg, sizeof(uint32_t) * n_q);
+  ALLOC(d_tgt, sizeof(uint32_t) * n_tick);
+  ALLOC(colbest, sizeof(unsigned long long) * (size_t)nL * n_tick);
+  CK(cudaMemcpyAsync(d_qg.p, q_genome.data(), sizeof(uint32_t) * n_q, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(d_tgt.p, tgt_end.data(), sizeof(uint32_t) * n_tick, cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemsetAsync(colbest.p, 0, sizeof(unsigned long long) * (size_t)nL * n_tick, c->stream));
+  PD_KLAUNCH("serve_iota", (k_iota<<<grid_of(n_q, 256, 152u * 4u), 256, 0, c->stream>>>(order.as<uint32_t>(), n_q,
+                                                                                         0u)));
+  pdg::QuerySet Q{};
+  Q.all_pairs = 1;
+  Q.order = order.as<uint32_t>();
+  Q.n_queries = n_q;
+  Q.q_genome = d_qg.as<uint32_t>();
+  Q.tgt_end = d_tgt.as<uint32_t>();
+  Q.colbest = colbest.as<unsigned long long>();
+  Q.col_genome0 = 0;
+  Q.col_stride = n_tick;
+  pd_hits H;
+  H.ctx = c;
+  if ((st = run_hits_view(c, V, Q, &H, std::max<uint32_t>(L.genome1 - L.genome0, 1))) != PD_OK) return st;
+
+  Buf row_ptr, cols, sv, tmp, flag, cnt, start, pa, pb;
+  ALLOC(row_ptr, sizeof(unsigned long long) * (n_q + 1));
+  ALLOC(tmp, pdg::scan_temp_bytes(n_q + 1) + 64);
+  CK(pdg::scan_u32_to_u64(&c->L, H.row_len.as<uint32_t>(), n_q, row_ptr.as<unsigned long long>(), tmp.p,
+                          c->stream));
+  unsigned long long n_hits = 0;
+  CK(cudaMemcpyAsync(&n_hits, row_ptr.as<unsigned long long>() + n_q, sizeof(n_hits), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  ALLOC(cols, sizeof(int32_t) * std::max<unsigned long long>(n_hits, 1));
+  ALLOC(sv, sizeof(uint32_t) * std::max<unsigned long long>(n_hits, 1));
+  CK(pdg::run_gather_rows(&c->L, n_q, H.row_off.as<unsigned long long>(), H.row_len.as<uint32_t>(),
+                          row_ptr.as<unsigned long long>(), H.out_b.as<uint32_t>(), H.out_s.as<uint32_t>(), 0,
+                          cols.as<int32_t>(), sv.as<uint32_t>(), c->stream));
+  ALLOC(flag, std::max<unsigned long long>(n_hits, 1));
+  ALLOC(cnt, sizeof(uint32_t) * n_q);
+  ALLOC(start, sizeof(uint32_t) * (n_q + 1));
+  PD_KLAUNCH("serve_bbh_count",
+             (k_serve_bbh_count<<<grid_of((uint64_t)n_q * 32, 256, 152u * 16u), 256, 0, c->stream>>>(
+                 n_q, row_ptr.as<unsigned long long>(), cols.as<int32_t>(), sv.as<uint32_t>(), Qp.La.as<uint32_t>(),
+                 L.P->view.La, d_qg.as<uint32_t>(), n_tick, colbest.as<unsigned long long>(), flag.as<uint8_t>(),
+                 cnt.as<uint32_t>())));
+  CK(pdg::scan_u32(&c->L, cnt.as<uint32_t>(), n_q, start.as<uint32_t>(), tmp.p, c->stream));
+  uint32_t n_bbh = 0;
+  CK(cudaMemcpyAsync(&n_bbh, start.as<uint32_t>() + n_q, sizeof(n_bbh), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  ALLOC(pa, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
+  ALLOC(pb, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
+  if (n_bbh)
+    PD_KLAUNCH("serve_bbh_write", (k_serve_bbh_write<<<grid_of((uint64_t)n_q * 32, 256, 152u * 16u), 256, 0,
+                                                       c->stream>>>(n_q, row_ptr.as<unsigned long long>(),
+                                                                    cols.as<int32_t>(), flag.as<uint8_t>(),
+                                                                    start.as<uint32_t>(), pa.as<int32_t>(),
+                                                                    pb.as<int32_t>())));
+  out->cols.resize(n_hits);
+  out->s.resize(n_hits);
+  out->pa.resize(n_bbh);
+  out->pb.resize(n_bbh);
+  CK(cudaMemcpyAsync(out->rp.data(), row_ptr.p, sizeof(unsigned long long) * (n_q + 1), cudaMemcpyDeviceToHost,
+                     c->stream));
+  if (n_hits) {
+    CK(cudaMemcpyAsync(out->cols.data(), cols.p, sizeof(int32_t) * n_hits, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(out->s.data(), sv.p, sizeof(uint32_t) * n_hits, cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (n_bbh) {
+    CK(cudaMemcpyAsync(out->pa.data(), pa.p, sizeof(int32_t) * n_bbh, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaMemcpyAsync(out->pb.data(), pb.p, sizeof(int32_t) * n_bbh, cudaMemcpyDeviceToHost, c->stream));
+  }
+  return check_dev_err(c);  // synchronizes
+}
+
+// Appends the genomes of `tick` to the resident data and answers every
+// request of the tick against both levels (the levels hold the committed
+// genomes; the tick's genomes join them when the levels are next refreshed).
 pd_status run_tick(pd_index* I, std::vector<Request>& tick, std::vector<std::unique_ptr<pd_reply>>& replies) {
   pd_ctx* c = I->c;
+  pd_status st0 = refresh_levels(I);  // no-op unless an earlier refresh failed
+  if (st0 != PD_OK) return st0;
   const uint32_t n_tick = (uint32_t)tick.size();
-  const uint32_t g_res = (uint32_t)I->genome_ptr.size() - 1;       // resident genomes
-  const uint32_t G_res = (uint32_t)I->gene_ptr.size() - 1;         // resident genes
+  const uint32_t g_res = (uint32_t)I->genome_ptr.size() - 1;
   if (g_res + n_tick > PD_MAX_GENOMES) return fail(c, PD_ERR_BUDGET, "the index holds at most PD_MAX_GENOMES genomes");
   uint64_t add = 0;
   for (auto& r : tick) add += r.res.size();
@@ -215,132 +378,75 @@ pd_status run_tick(pd_index* I, std::vector<Request>& tick, std::vector<std::uni
     const uint64_t want = std::max<uint64_t>(I->res_used + add, std::max<uint64_t>(2 * I->res.n, 1 << 20));
     ALLOC(bigger, want);
     if (I->res_used) CK(cudaMemcpyAsync(bigger.p, I->res.p, I->res_used, cudaMemcpyDeviceToDevice, c->stream));
+    // the levels' profiles do not point into the residues, so moving them is safe
     I->res = std::move(bigger);
   }
-  uint64_t off = I->res_used;
-  for (auto& r : tick) {
+  const uint64_t tick_r0 = I->res_used;
+  uint64_t off = tick_r0;
+  std::vector<int64_t> tick_gp(1, 0);
+  std::vector<uint32_t> q_genome, snap_gene_end(n_tick);
+  for (uint32_t x = 0; x < n_tick; ++x) {
+    const Request& r = tick[x];
     if (!r.res.empty())
       CK(cudaMemcpyAsync(I->res.as<uint8_t>() + off, r.res.data(), r.res.size(), cudaMemcpyHostToDevice, c->stream));
-    for (size_t g = 1; g < r.gene_ptr.size(); ++g) I->gene_ptr.push_back((int64_t)off + r.gene_ptr[g]);
+    for (size_t g = 1; g < r.gene_ptr.size(); ++g) {
+      I->gene_ptr.push_back((int64_t)off + r.gene_ptr[g]);
+      tick_gp.push_back((int64_t)(off - tick_r0) + r.gene_ptr[g]);
+      q_genome.push_back(x);
+    }
     I->genome_ptr.push_back((int32_t)(I->gene_ptr.size() - 1));
+    I->genome_windows.push_back(r.windows);
+    snap_gene_end[x] = (uint32_t)I->genome_ptr[r.snapshot];
     off += r.res.size();
   }
   I->res_used = off;
-  const uint32_t G = (uint32_t)I->gene_ptr.size() - 1, n_genomes = g_res + n_tick;
-  const uint32_t n_q = G - G_res;
 
-  // ---- the index over resident + tick genomes (the insertion)
-  I->P.reset();
-  pd_profiles* Praw = nullptr;
-  pd_status st = build_profiles_impl(c, I->res.as<uint8_t>(), I->res_used, I->gene_ptr.data(), G,
-                                     I->genome_ptr.data(), n_genomes, I->k, nullptr, &Praw);
-  if (st != PD_OK) return st;
-  std::unique_ptr<pd_profiles> P(Praw);
-
-  // ---- queries: every gene of the tick against its snapshot
-  std::vector<uint32_t> tgt_end(n_genomes, 0);
-  for (uint32_t x = 0; x < n_tick; ++x) tgt_end[g_res + x] = (uint32_t)I->genome_ptr[tick[x].snapshot];
-  Buf order, d_tgt, colbest;
-  ALLOC(order, sizeof(uint32_t) * std::max<uint32_t>(n_q, 1));
-  ALLOC(d_tgt, sizeof(uint32_t) * n_genomes);
-  ALLOC(colbest, sizeof(unsigned long long) * std::max<uint64_t>((uint64_t)G_res * n_tick, 1));
-  CK(cudaMemcpyAsync(d_tgt.p, tgt_end.data(), sizeof(uint32_t) * n_genomes, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemsetAsync(colbest.p, 0, sizeof(unsigned long long) * std::max<uint64_t>((uint64_t)G_res * n_tick, 1),
-                     c->stream));
-  if (n_q) PD_KLAUNCH("serve_iota", (k_iota<<<grid_of(n_q, 256, 152u * 4u), 256, 0, c->stream>>>(
-                                        order.as<uint32_t>(), n_q, G_res)));
-  pdg::QuerySet Q{};
-  Q.all_pairs = 1;
-  Q.order = order.as<uint32_t>();
-  Q.n_queries = n_q;
-  Q.tgt_end = d_tgt.as<uint32_t>();
-  Q.colbest = colbest.as<unsigned long long>();
-  Q.col_genome0 = g_res;
-  Q.col_stride = n_tick;
-  pd_hits H;
-  H.ctx = c;
-  H.all_pairs = 1;
-  if ((st = run_hits(c, P.get(), Q, false, &H, std::max<uint32_t>(g_res, 1))) != PD_OK) return st;
-
-  // ---- the tick's rows as one CSR (global resident gene ids as columns)
-  Buf row_ptr, cols, sv, tmp, flag, cnt, start, pa, pb;
-  ALLOC(row_ptr, sizeof(unsigned long long) * (n_q + 1));
-  ALLOC(tmp, pdg::scan_temp_bytes(n_q + 1) + 64);
-  CK(pdg::scan_u32_to_u64(&c->L, H.row_len.as<uint32_t>() + G_res, n_q, row_ptr.as<unsigned long long>(), tmp.p,
-                          c->stream));
-  unsigned long long n_hits = 0;
-  CK(cudaMemcpyAsync(&n_hits, row_ptr.as<unsigned long long>() + n_q, sizeof(n_hits), cudaMemcpyDeviceToHost,
-                     c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  ALLOC(cols, sizeof(int32_t) * std::max<unsigned long long>(n_hits, 1));
-  ALLOC(sv, sizeof(uint32_t) * std::max<unsigned long long>(n_hits, 1));
-  if (n_q)
-    CK(pdg::run_gather_rows(&c->L, n_q, H.row_off.as<unsigned long long>() + G_res, H.row_len.as<uint32_t>() + G_res,
-                            row_ptr.as<unsigned long long>(), H.out_b.as<uint32_t>(), H.out_s.as<uint32_t>(), 0,
-                            cols.as<int32_t>(), sv.as<uint32_t>(), c->stream));
-  // ---- mutual check against the reverse maxima
-  ALLOC(flag, std::max<unsigned long long>(n_hits, 1));
-  ALLOC(cnt, sizeof(uint32_t) * std::max<uint32_t>(n_q, 1));
-  ALLOC(start, sizeof(uint32_t) * (n_q + 1));
-  if (n_q)
-    PD_KLAUNCH("serve_bbh_count",
-               (k_serve_bbh_count<<<grid_of((uint64_t)n_q * 32, 256, 152u * 16u), 256, 0, c->stream>>>(
-                   n_q, G_res, row_ptr.as<unsigned long long>(), cols.as<int32_t>(), sv.as<uint32_t>(),
-                   P->view.La, P->view.gene_genome, g_res, n_tick, colbest.as<unsigned long long>(),
-                   flag.as<uint8_t>(), cnt.as<uint32_t>())));
-  CK(pdg::scan_u32(&c->L, cnt.as<uint32_t>(), n_q, start.as<uint32_t>(), tmp.p, c->stream));
-  uint32_t n_bbh = 0;
-  CK(cudaMemcpyAsync(&n_bbh, start.as<uint32_t>() + n_q, sizeof(n_bbh), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-  ALLOC(pa, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
-  ALLOC(pb, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
-  if (n_q && n_bbh)
-    PD_KLAUNCH("serve_bbh_write", (k_serve_bbh_write<<<grid_of((uint64_t)n_q * 32, 256, 152u * 16u), 256, 0,
-                                                       c->stream>>>(n_q, row_ptr.as<unsigned long long>(),
-                                                                    cols.as<int32_t>(), flag.as<uint8_t>(),
-                                                                    start.as<uint32_t>(), pa.as<int32_t>(),
-                                                                    pb.as<int32_t>())));
-  // ---- to the host, split per request
-  std::vector<unsigned long long> h_rp(n_q + 1);
-  std::vector<int32_t> h_cols(n_hits), h_a(n_bbh), h_b(n_bbh);
-  std::vector<uint32_t> h_s(n_hits);
-  CK(cudaMemcpyAsync(h_rp.data(), row_ptr.p, sizeof(unsigned long long) * (n_q + 1), cudaMemcpyDeviceToHost,
-                     c->stream));
-  if (n_hits) {
-    CK(cudaMemcpyAsync(h_cols.data(), cols.p, sizeof(int32_t) * n_hits, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(h_s.data(), sv.p, sizeof(uint32_t) * n_hits, cudaMemcpyDeviceToHost, c->stream));
+  // ---- every level answers every gene of the tick
+  LevelAnswer A[2];
+  const Level* levels[2] = {&I->base, &I->delta};
+  for (int l = 0; l < 2; ++l) {
+    pd_status st = answer_level(I, *levels[l], I->res.as<uint8_t>() + tick_r0, tick_gp, q_genome, snap_gene_end,
+                                &A[l]);
+    if (st != PD_OK) return st;
   }
-  if (n_bbh) {
-    CK(cudaMemcpyAsync(h_a.data(), pa.p, sizeof(int32_t) * n_bbh, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaMemcpyAsync(h_b.data(), pb.p, sizeof(int32_t) * n_bbh, cudaMemcpyDeviceToHost, c->stream));
-  }
-  if ((st = check_dev_err(c)) != PD_OK) return st;  // synchronizes
+
+  // ---- per request: rows = base part then delta part (global resident ids)
   uint32_t r0 = 0;
-  size_t p = 0;
+  size_t p[2] = {0, 0};
   for (uint32_t x = 0; x < n_tick; ++x) {
     const uint32_t nx = (uint32_t)tick[x].gene_ptr.size() - 1;
     std::unique_ptr<pd_reply> R(new pd_reply());
-    const unsigned long long h0 = h_rp[r0], h1 = h_rp[r0 + nx];
-    R->row_ptr.resize(nx + 1);
-    for (uint32_t i = 0; i <= nx; ++i) R->row_ptr[i] = (int64_t)(h_rp[r0 + i] - h0);
-    R->cols.assign(h_cols.begin() + h0, h_cols.begin() + h1);
-    R->s.assign(h_s.begin() + h0, h_s.begin() + h1);
-    while (p < n_bbh && (uint32_t)h_a[p] < r0 + nx) {
-      R->bbh_a.push_back(h_a[p] - (int32_t)r0);
-      R->bbh_b.push_back(h_b[p]);
-      ++p;
+    R->row_ptr.resize(nx + 1, 0);
+    for (uint32_t i = 0; i < nx; ++i) {
+      const uint32_t r = r0 + i;
+      for (int l = 0; l < 2; ++l) {
+        if (A[l].cols.empty()) continue;
+        const int32_t g0 = (int32_t)levels[l]->gene0;
+        for (unsigned long long e = A[l].rp[r]; e < A[l].rp[r + 1]; ++e) {
+          R->cols.push_back(A[l].cols[e] + g0);
+          R->s.push_back(A[l].s[e]);
+        }
+      }
+      R->row_ptr[i + 1] = (int64_t)R->cols.size();
+      for (int l = 0; l < 2; ++l) {
+        const int32_t g0 = (int32_t)levels[l]->gene0;
+        while (p[l] < A[l].pa.size() && (uint32_t)A[l].pa[p[l]] == r) {
+          R->bbh_a.push_back((int32_t)i);
+          R->bbh_b.push_back(A[l].pb[p[l]] + g0);
+          ++p[l];
+        }
+      }
     }
     R->info.ticket = tick[x].ticket;
     R->info.status = PD_OK;
     R->info.snapshot_genomes = tick[x].snapshot;
     R->info.n_genes = nx;
-    R->info.n_hits = h1 - h0;
+    R->info.n_hits = R->cols.size();
     R->info.n_bbh = R->bbh_a.size();
     R->info.tick_requests = n_tick;
     replies.push_back(std::move(R));
     r0 += nx;
   }
-  I->P = std::move(P);
   return PD_OK;
 }
 
@@ -384,7 +490,7 @@ void worker_main(pd_index* I) {
     const int64_t t_start = now_ns();
     std::vector<std::unique_ptr<pd_reply>> replies;
     const uint64_t res_used0 = I->res_used;
-    const size_t gp0 = I->gene_ptr.size(), gn0 = I->genome_ptr.size();
+    const size_t gp0 = I->gene_ptr.size(), gn0 = I->genome_ptr.size(), gw0 = I->genome_windows.size();
     pd_status st;
     try {
       st = run_tick(I, tick, replies);
@@ -393,14 +499,13 @@ void worker_main(pd_index* I) {
       I->c->err = "exception in the request loop";
     }
     const int64_t t_done = now_ns();
-    std::lock_guard<std::mutex> lk(I->mu);
+    std::unique_lock<std::mutex> lk(I->mu);
     if (st == PD_OK) {
       I->committed += (uint32_t)tick.size();
       I->committed_genes = I->gene_ptr.size() - 1;
       I->committed_res = I->res_used;
       for (auto& r : tick) I->committed_windows += r.windows;
       I->committed_genome_ptr = I->genome_ptr;
-      I->resident_bytes = I->res.n + (I->P ? I->P->info.device_bytes : 0);
       I->stats.ticks += 1;
       I->stats.max_tick_requests = std::max<uint32_t>(I->stats.max_tick_requests, (uint32_t)tick.size());
       for (auto& R : replies) {
@@ -417,6 +522,7 @@ void worker_main(pd_index* I) {
       I->res_used = res_used0;
       I->gene_ptr.resize(gp0);
       I->genome_ptr.resize(gn0);
+      I->genome_windows.resize(gw0);
       for (auto& r : tick) {
         std::unique_ptr<pd_reply> R(new pd_reply());
         R->info.ticket = r.ticket;
@@ -429,6 +535,19 @@ void worker_main(pd_index* I) {
       }
     }
     I->cv_done.notify_all();
+    lk.unlock();
+    // take the new residents into the index before the next tick
+    if (st == PD_OK) {
+      pd_status rs;
+      try {
+        rs = refresh_levels(I);
+      } catch (...) {
+        rs = PD_ERR_INTERNAL;
+      }
+      (void)rs;  // a failed refresh is retried (and reported) by the next tick
+      std::lock_guard<std::mutex> lk2(I->mu);
+      I->resident_bytes = I->res.n + I->base.bytes() + I->delta.bytes();
+    }
   }
 }
 
@@ -464,17 +583,18 @@ pd_status index_create(pd_ctx* caller, const uint8_t* residues, uint64_t n_res, 
       return fail_cuda(caller, cudaGetLastError(), "copy of the resident residues");
   }
   I->res_used = n_res;
-  pd_profiles* Praw = nullptr;
-  st = build_profiles_impl(c, I->res.as<uint8_t>(), n_res, I->gene_ptr.data(), n_genes, I->genome_ptr.data(),
-                           n_genomes, k, nullptr, &Praw);
+  for (uint32_t i = 0; i < n_genomes; ++i)
+    I->genome_windows.push_back(windows_of(I->gene_ptr, I->genome_ptr[i], I->genome_ptr[i + 1], k));
+  st = build_level(I.get(), 0, n_genomes, &I->base);
   if (st != PD_OK) return fail(caller, st, c->err);
-  I->P.reset(Praw);
+  I->delta.genome0 = I->delta.genome1 = n_genomes;
+  I->delta.gene0 = I->delta.gene1 = n_genes;
   I->committed = n_genomes;
   I->committed_genes = n_genes;
   I->committed_windows = windows_of(I->gene_ptr, 0, n_genes, k);
   I->committed_genome_ptr = I->genome_ptr;
   I->committed_res = n_res;
-  I->resident_bytes = I->res.n + I->P->info.device_bytes;
+  I->resident_bytes = I->res.n + I->base.bytes();
   if (I->resident_bytes > hbm_budget) return fail(caller, PD_ERR_BUDGET, "the resident index exceeds the budget");
   I->worker = std::thread(worker_main, I.get());
   *out = I.release();
@@ -508,6 +628,13 @@ PD_API pd_status pd_index_submit(pd_index* I, const uint8_t* residues, uint64_t 
       if (r.gene_ptr[g + 1] < r.gene_ptr[g]) return PD_ERR_ARG;
       if (r.gene_ptr[g + 1] - r.gene_ptr[g] - I->k + 1 > (int64_t)PD_MAX_WINDOWS) return PD_ERR_GENE_TOO_LONG;
     }
+    // letters are checked here: the tick profiles the genome against the
+    // resident dictionary, which has no place for foreign letters
+    static const char kLetters[] = "ACDEFGHIKLMNPQRSTVWY";
+    bool valid[256] = {false};
+    for (const char* q = kLetters; *q; ++q) valid[(uint8_t)*q] = true;
+    for (uint64_t i = 0; i < n_res; ++i)
+      if (!valid[residues[i]]) return PD_ERR_ALPHABET;
     r.res.assign(residues, residues + n_res);
     r.windows = windows_of(r.gene_ptr, 0, n_genes, I->k);
     r.t_submit = now_ns();

@@ -131,3 +131,29 @@ def test_budget_and_arguments(ctx, stream):
     with pytest.raises(pd.PdError) as e:
         pd.pd_index_poll(index, 12345, 0)
     assert e.value.status == 1
+    with pytest.raises(pd.PdError) as e:
+        pd.pd_index_submit(index, np.frombuffer(b"ACDEFGXB", np.uint8), np.array([0, 8], np.int64))
+    assert e.value.status == 2
+
+
+def test_many_arrivals_cross_level_merges(ctx, stream):
+    """A longer stream, submitted in bursts: the delta level is rebuilt and
+    merged into the base several times; every answer still equals the plain
+    path at its snapshot."""
+    ds, res, k = stream
+    big = synth.served_stream(N_RES, 24, seed=9, resident_genes=("uniform", 200, 400), incoming_genes=(150, 500),
+                              n_families=500)
+    res = big.subset(list(range(N_RES)))
+    index = _index(ctx, res, k)
+    commit_order = list(range(big.n_genomes))  # answers commit in submission order
+    x = N_RES
+    while x < big.n_genomes:
+        burst = list(range(x, min(x + 5, big.n_genomes)))
+        tickets = [pd.pd_index_submit(index, *synth.genome_of(big, g)) for g in burst]
+        for t, g in zip(tickets, burst):
+            info, rows, bbh = _reply(index, t)
+            assert N_RES <= info.snapshot_genomes <= g
+            exp_rows, exp_bbh, _ = _expected(ctx, big, commit_order[:info.snapshot_genomes], g, k)
+            assert rows == exp_rows and bbh == exp_bbh, f"genome {g}"
+        x += len(burst)
+    assert pd.pd_index_get_info(index).n_genomes == big.n_genomes
