@@ -39,3 +39,26 @@ def test_choose_k_without_gpu():
     assert pd.pd_choose_k(50_000_000) == 6
     assert pd.pd_choose_k(20 ** 7) == 7
     assert pd.pd_choose_k(1) == 1
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    """No fallback: without the compiled library the binding raises."""
+    import pytest
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "absent.so"))
+    saved = pd._lib
+    try:
+        pd._lib = None
+        with pytest.raises(RuntimeError, match="not found"):
+            pd.load(build=False)
+    finally:
+        pd._lib = saved
+
+
+def test_product_sources_do_not_import_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2510_23679_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "pd_oracle" not in text, f
