@@ -40,13 +40,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pan50x3000", choices=sorted(synth.WORKLOADS) + ["jobs", "served"],
+    ap.add_argument("--workload", default="pan50x3000", choices=sorted(synth.WORKLOADS) + ["jobs", "served", "pairs"],
                     help="a plain pangenome, 'jobs': a batch of independent genome-pair jobs, or 'served': "
                          "genomes arriving at a resident index")
     ap.add_argument("--rates", default="2,5,10,20,50", help="arrival rates (genomes/s) of --workload served")
     ap.add_argument("--seconds-per-rate", type=float, default=20.0,
                     help="arrivals per rate: min(incoming, rate x this)")
     ap.add_argument("--incoming", type=int, default=500, help="incoming genomes of --workload served")
+    ap.add_argument("--pairs-of", default="pan200x4000", choices=sorted(synth.WORKLOADS),
+                    help="the pangenome whose genome pairs --workload pairs compares")
     ap.add_argument("--jobs", type=int, default=2000, help="jobs in the batch (--workload jobs)")
     ap.add_argument("--no-per-pair", action="store_true", help="skip the one-pair-per-launch comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -447,6 +449,67 @@ def run_served(args):
     return 0
 
 
+# --------------------------------------------------------------------------- genome pairs of one dataset
+def run_pairs(args):
+    """pd_bbh_pairs on --jobs random genome pairs of one profiled pangenome
+    (--pairs-of, default pan200x4000), next to the same pairs one pd_bbh call
+    each (its BBH only: the one-pair path's least work)."""
+    import torch
+    from paper_2510_23679_gb300 import pd
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    ds = synth.workload(args.pairs_of)
+    k = pd.pd_choose_k(ds.n_residues)
+    ctx = pd.pd_ctx_create(0)
+    prof = pd.pd_build_profiles(ctx, torch.from_numpy(ds.residues).to(dev), torch.from_numpy(ds.gene_ptr).to(dev),
+                                torch.from_numpy(ds.genome_ptr).to(dev), k)
+    rng = np.random.default_rng(12)
+    jobs = []
+    while len(jobs) < args.jobs:
+        a, b = rng.integers(0, ds.n_genomes, size=2)
+        if a != b:
+            jobs.append((int(a), int(b)))
+    jobs = np.array(jobs, np.uint32)
+    sizes = np.diff(ds.genome_ptr).astype(np.int64)
+    pairs = int(sum(sizes[a] * sizes[b] for a, b in jobs))
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, reps):
+        out = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            out.append(e0.elapsed_time(e1))
+        return sorted(out)[len(out) // 2], r
+
+    def batched():
+        return pd.pd_batch_get_info(pd.pd_bbh_pairs(ctx, prof, jobs)).n_bbh
+
+    def one_by_one():
+        return sum(pd.pd_bbh_count(pd.pd_bbh(ctx, prof, int(a), int(b))) for a, b in jobs)
+
+    for _ in range(args.warmup):
+        batched()
+    one_by_one()
+    with ClockSampler(0) as clk:
+        ms_b, n_b = timed(batched, args.steps)
+        ms_1, n_1 = timed(one_by_one, 1)
+    assert n_b == n_1, (n_b, n_1)
+    print(json.dumps({
+        "metric": "gene-pair GJ evals/s", "value": pairs / (ms_b / 1e3), "unit": "gene-pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_b, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic", "impl": "pairs",
+        "config": {"workload": f"{args.jobs} random genome pairs of {args.pairs_of} (k={k}), profiles resident",
+                   "logical_pairs_per_step": pairs},
+        "genome_pairs_per_s": args.jobs / (ms_b / 1e3),
+        "one_pair_per_call": {"ms": ms_1, "genome_pairs_per_s": args.jobs / (ms_1 / 1e3)},
+        "speedup_vs_one_pair_per_call": ms_1 / ms_b, "bbh_pairs": n_b, "clocks": clk.summary()}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -455,6 +518,8 @@ def main():
         return run_batch(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "pairs":
+        return run_pairs(args)
     import torch
     from paper_2510_23679_gb300 import pd
 

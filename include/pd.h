@@ -338,6 +338,16 @@ typedef struct {
 pd_status pd_bbh_batch(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                        uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* jobs,
                        const int32_t* job_k, uint32_t n_jobs, const pd_batch_tuning* tuning, pd_batch** out);
+/* Many genome pairs of ONE profiled dataset (Algorithms 2-3 for each pair),
+ * answered by one sum-min / Best Hit launch sequence over the genes of all
+ * pairs: jobs is a HOST array of 2*n_jobs genome indices of prof (A != B; a
+ * genome may appear in several jobs).  The result has the pd_bbh_batch layout
+ * (rows of A then B per job, partner-local columns; BBH pairs per job) and is
+ * read with pd_batch_get_info / pd_batch_copy_hits / pd_batch_copy_bbh.
+ * Each job equals pd_best_hits(gi=A, gj=B), pd_best_hits(B, A) and
+ * pd_bbh(A, B) on the same profiles. */
+pd_status pd_bbh_pairs(pd_ctx* ctx, const pd_profiles* prof, const uint32_t* jobs, uint32_t n_jobs,
+                       pd_batch** out);
 pd_status pd_batch_get_info(const pd_batch* batch, pd_batch_info* info);
 /* Autotuner of pd_bbh_batch: runs the first n_sample jobs (0 = min(n_jobs,
  * 100)) once with each candidate tuning (jobs per chunk 8 / 32 / bitmap

@@ -240,7 +240,11 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
     }
   } else {
     uint32_t tlo, thi;
-    if (Q.paralog) {
+    if (Q.q_gene) {
+      a = Q.q_gene[qi];
+      tlo = Q.q_t0[qi];
+      thi = Q.q_t1[qi];
+    } else if (Q.paralog) {
       a = Q.q0 + qi;
       const uint32_t gg = P.gene_genome[a];
       tlo = (uint32_t)P.genome_ptr[gg];

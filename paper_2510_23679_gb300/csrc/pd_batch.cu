@@ -348,7 +348,210 @@ pd_status batch_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const i
   return PD_OK;
 }
 
+// ---------------------------------------------------------------- genome pairs of one profile set
+// One pair job of pd_bbh_pairs: its rows are queries row0 .. row0+nA-1 (genes
+// of A, targets B) then row0+nA .. row0+nA+nB-1 (genes of B, targets A).
+struct PairJob {
+  uint32_t row0, nA, nB, A0, B0;
+};
+
+__device__ __forceinline__ bool row_has(const uint32_t* __restrict__ hit_b, unsigned long long off, uint32_t n,
+                                        uint32_t a) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (hit_b[off + mid] < a) lo = mid + 1; else hi = mid;
+  }
+  return lo < n && hit_b[off + lo] == a;
+}
+
+__device__ __forceinline__ uint32_t job_of_row(const PairJob* __restrict__ jobs, uint32_t n_jobs, uint32_t r) {
+  uint32_t lo = 0, hi = n_jobs;  // last job with row0 <= r
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (jobs[mid].row0 <= r) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Rows into the batch CSR (columns made local to the partner genome).
+__global__ void k_pairs_rows_fill(const PairJob* __restrict__ jobs, uint32_t n_jobs, uint32_t n_rows,
+                                  const unsigned long long* __restrict__ row_off, const uint32_t* __restrict__ row_len,
+                                  const uint32_t* __restrict__ hit_b, const uint32_t* __restrict__ hit_s,
+                                  const unsigned long long* __restrict__ batch_ptr, int32_t* __restrict__ cols,
+                                  uint32_t* __restrict__ s) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += warps) {
+    const PairJob J = jobs[job_of_row(jobs, n_jobs, r)];
+    const uint32_t partner0 = r < J.row0 + J.nA ? J.B0 : J.A0;
+    const unsigned long long src = row_off[r], dst = batch_ptr[r];
+    for (uint32_t i = lane; i < row_len[r]; i += 32) {
+      cols[dst + i] = (int32_t)(hit_b[src + i] - partner0);
+      s[dst + i] = hit_s[src + i];
+    }
+  }
+}
+
+// Mutual check, warp per row of an A genome: b's own row lists a?
+__global__ void k_pairs_bbh(const PairJob* __restrict__ jobs, uint32_t n_jobs, uint32_t n_rows,
+                            const unsigned long long* __restrict__ row_off, const uint32_t* __restrict__ row_len,
+                            const uint32_t* __restrict__ hit_b, const uint32_t* __restrict__ start,
+                            uint32_t* __restrict__ cnt, int32_t* __restrict__ pa, int32_t* __restrict__ pb) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < n_rows; r += warps) {
+    const PairJob J = jobs[job_of_row(jobs, n_jobs, r)];
+    uint32_t n = 0;
+    if (r < J.row0 + J.nA) {
+      const uint32_t a = J.A0 + (r - J.row0);
+      const unsigned long long off = row_off[r];
+      const uint32_t len = row_len[r];
+      uint32_t pos = start ? start[r] : 0u;
+      for (uint32_t e0 = 0; e0 < len; e0 += 32) {
+        const uint32_t e = e0 + lane;
+        bool f = false;
+        uint32_t b = 0;
+        if (e < len) {
+          b = hit_b[off + e];
+          const uint32_t rb = J.row0 + J.nA + (b - J.B0);
+          f = row_has(hit_b, row_off[rb], row_len[rb], a);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, f);
+        if (start && f) {
+          const uint32_t at = pos + (uint32_t)__popc(m & ((1u << lane) - 1u));
+          pa[at] = (int32_t)(a - J.A0);
+          pb[at] = (int32_t)(b - J.B0);
+        }
+        pos += (uint32_t)__popc(m);
+        n += (uint32_t)__popc(m);
+      }
+    }
+    if (!start && lane == 0) cnt[r] = n;
+  }
+}
+
+pd_status pairs_impl(pd_ctx* c, const pd_profiles* P, const uint32_t* jobs, uint32_t n_jobs, pd_batch** out) {
+  if (n_jobs && !jobs) return fail(c, PD_ERR_ARG, "null jobs");
+  if (n_jobs && is_device_ptr(jobs)) return fail(c, PD_ERR_ARG, "jobs must be a host array");
+  CK(cudaSetDevice(c->device));
+  const auto& gp = P->h_genome_ptr;
+  const uint32_t n_genomes = P->view.n_genomes;
+  std::vector<PairJob> pj(n_jobs);
+  std::vector<uint32_t> qg, qt0, qt1;
+  uint32_t row = 0;
+  for (uint32_t j = 0; j < n_jobs; ++j) {
+    const uint32_t A = jobs[2 * j], B = jobs[2 * j + 1];
+    if (A >= n_genomes || B >= n_genomes || A == B)
+      return fail(c, PD_ERR_ARG, "job " + std::to_string(j) + " needs two distinct genome indices < n_genomes");
+    PairJob J{row, (uint32_t)(gp[A + 1] - gp[A]), (uint32_t)(gp[B + 1] - gp[B]), (uint32_t)gp[A], (uint32_t)gp[B]};
+    pj[j] = J;
+    for (uint32_t i = 0; i < J.nA; ++i) {
+      qg.push_back(J.A0 + i);
+      qt0.push_back((uint32_t)gp[B]);
+      qt1.push_back((uint32_t)gp[B + 1]);
+    }
+    for (uint32_t i = 0; i < J.nB; ++i) {
+      qg.push_back(J.B0 + i);
+      qt0.push_back((uint32_t)gp[A]);
+      qt1.push_back((uint32_t)gp[A + 1]);
+    }
+    row += J.nA + J.nB;
+  }
+  const uint32_t n_q = row;
+  std::unique_ptr<pd_batch> Bt(new pd_batch());
+  Bt->ctx = c;
+  Buf d_jobs, d_qg, d_t0, d_t1, tmp, cnt, start;
+  ALLOC(d_jobs, sizeof(PairJob) * std::max<uint32_t>(n_jobs, 1));
+  ALLOC(d_qg, sizeof(uint32_t) * std::max<uint32_t>(n_q, 1));
+  ALLOC(d_t0, sizeof(uint32_t) * std::max<uint32_t>(n_q, 1));
+  ALLOC(d_t1, sizeof(uint32_t) * std::max<uint32_t>(n_q, 1));
+  ALLOC(Bt->row_ptr, sizeof(unsigned long long) * (n_q + 1));
+  ALLOC(Bt->job_ptr, sizeof(unsigned long long) * (n_jobs + 1));
+  ALLOC(tmp, pdg::scan_temp_bytes(n_q + 1) + 64);
+  ALLOC(cnt, sizeof(uint32_t) * std::max<uint32_t>(n_q, 1));
+  ALLOC(start, sizeof(uint32_t) * (n_q + 1));
+  if (n_jobs) CK(cudaMemcpyAsync(d_jobs.p, pj.data(), sizeof(PairJob) * n_jobs, cudaMemcpyHostToDevice, c->stream));
+  if (n_q) {
+    CK(cudaMemcpyAsync(d_qg.p, qg.data(), sizeof(uint32_t) * n_q, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d_t0.p, qt0.data(), sizeof(uint32_t) * n_q, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(d_t1.p, qt1.data(), sizeof(uint32_t) * n_q, cudaMemcpyHostToDevice, c->stream));
+  }
+  // one sum-min / Best Hit launch sequence over every query of every job
+  pd_hits H;
+  H.ctx = c;
+  pdg::QuerySet Q{};
+  Q.all_pairs = 0;
+  Q.n_queries = n_q;
+  Q.q_gene = d_qg.as<uint32_t>();
+  Q.q_t0 = d_t0.as<uint32_t>();
+  Q.q_t1 = d_t1.as<uint32_t>();
+  pd_status st = run_hits(c, P, Q, false, &H, 1);
+  if (st != PD_OK) return st;
+  CK(pdg::scan_u32_to_u64(&c->L, H.row_len.as<uint32_t>(), n_q, Bt->row_ptr.as<unsigned long long>(), tmp.p,
+                          c->stream));
+  if (n_q)
+    PD_KLAUNCH("pairs_bbh_count", (k_pairs_bbh<<<grid_of((uint64_t)n_q * 32, 256, 152u * 16u), 256, 0, c->stream>>>(
+                                       d_jobs.as<PairJob>(), n_jobs, n_q, H.row_off.as<unsigned long long>(),
+                                       H.row_len.as<uint32_t>(), H.out_b.as<uint32_t>(), nullptr,
+                                       cnt.as<uint32_t>(), nullptr, nullptr)));
+  CK(pdg::scan_u32(&c->L, cnt.as<uint32_t>(), n_q, start.as<uint32_t>(), tmp.p, c->stream));
+  unsigned long long n_hits = 0;
+  uint32_t n_bbh = 0;
+  std::vector<uint32_t> h_start(n_q + 1);
+  CK(cudaMemcpyAsync(&n_hits, Bt->row_ptr.as<unsigned long long>() + n_q, sizeof(n_hits), cudaMemcpyDeviceToHost,
+                     c->stream));
+  CK(cudaMemcpyAsync(h_start.data(), start.p, sizeof(uint32_t) * (n_q + 1), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  n_bbh = h_start[n_q];
+  std::vector<unsigned long long> job_ptr(n_jobs + 1);
+  for (uint32_t j = 0; j < n_jobs; ++j) job_ptr[j] = h_start[pj[j].row0];
+  job_ptr[n_jobs] = n_bbh;
+  CK(cudaMemcpyAsync(Bt->job_ptr.p, job_ptr.data(), sizeof(unsigned long long) * (n_jobs + 1),
+                     cudaMemcpyHostToDevice, c->stream));
+  ALLOC(Bt->cols, sizeof(int32_t) * std::max<unsigned long long>(n_hits, 1));
+  ALLOC(Bt->s, sizeof(uint32_t) * std::max<unsigned long long>(n_hits, 1));
+  ALLOC(Bt->a, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
+  ALLOC(Bt->b, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
+  if (n_q) {
+    PD_KLAUNCH("pairs_rows_fill",
+               (k_pairs_rows_fill<<<grid_of((uint64_t)n_q * 32, 256, 152u * 16u), 256, 0, c->stream>>>(
+                   d_jobs.as<PairJob>(), n_jobs, n_q, H.row_off.as<unsigned long long>(), H.row_len.as<uint32_t>(),
+                   H.out_b.as<uint32_t>(), H.out_s.as<uint32_t>(), Bt->row_ptr.as<unsigned long long>(),
+                   Bt->cols.as<int32_t>(), Bt->s.as<uint32_t>())));
+    if (n_bbh)
+      PD_KLAUNCH("pairs_bbh_write",
+                 (k_pairs_bbh<<<grid_of((uint64_t)n_q * 32, 256, 152u * 16u), 256, 0, c->stream>>>(
+                     d_jobs.as<PairJob>(), n_jobs, n_q, H.row_off.as<unsigned long long>(), H.row_len.as<uint32_t>(),
+                     H.out_b.as<uint32_t>(), start.as<uint32_t>(), nullptr, Bt->a.as<int32_t>(),
+                     Bt->b.as<int32_t>())));
+  }
+  CK(cudaStreamSynchronize(c->stream));  // temporaries and the hits are released on return
+  pd_batch_info& in = Bt->info;
+  in.n_jobs = n_jobs;
+  in.n_chunks = 1;
+  in.n_rows = n_q;
+  in.n_hits = n_hits;
+  in.n_bbh = n_bbh;
+  in.postings_walked = H.walked;
+  *out = Bt.release();
+  return PD_OK;
+}
+
 }  // namespace
+
+PD_API pd_status pd_bbh_pairs(pd_ctx* c, const pd_profiles* P, const uint32_t* jobs, uint32_t n_jobs,
+                              pd_batch** out) {
+  if (!c || !P || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    return pairs_impl(c, P, jobs, n_jobs, out);
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_bbh_pairs");
+  }
+}
 
 PD_API pd_status pd_bbh_batch(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                               uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* jobs,

@@ -210,6 +210,11 @@ struct QuerySet {
   // Within-genome form (pair indexing, row = q0 + query): each query gene is
   // compared with the other genes of its own genome (not with itself).
   int paralog;
+  // Listed form (pair indexing, row = query): query x is gene q_gene[x] and
+  // targets genes [q_t0[x], q_t1[x]) -- many genome pairs in one launch.
+  const uint32_t* q_gene;
+  const uint32_t* q_t0;
+  const uint32_t* q_t1;
   // External queries (with the q_* arrays of the view): the genome of each
   // query gene among the queries' own genomes; it has no own-genome targets,
   // tgt_end and the colbest column are indexed by it.

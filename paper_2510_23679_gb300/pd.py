@@ -119,6 +119,7 @@ _SIGNATURES = [
     ("pd_summin_pairs", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _P, _P, _P, C.POINTER(C.c_uint64)]),
     ("pd_bbh_batch", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, _P, _P, C.c_uint32,
                                C.POINTER(BatchTuning), _PP]),
+    ("pd_bbh_pairs", C.c_int, [_P, _P, _P, C.c_uint32, _PP]),
     ("pd_batch_get_info", C.c_int, [_P, C.POINTER(BatchInfo)]),
     ("pd_batch_autotune", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, _P, C.c_uint32, _P, _P, C.c_uint32,
                                     C.c_uint32, C.POINTER(BatchTuning), C.POINTER(C.c_double)]),
@@ -536,6 +537,16 @@ def pd_bbh_batch(ctx: Ctx, residues, gene_ptr, genome_ptr, jobs, job_k, max_chun
                            _ptr(jb) if jb.size else None, _ptr(kk) if kk.size else None, int(kk.shape[0]),
                            C.byref(tun), C.byref(h))
     _check(ctx, st, "pd_bbh_batch")
+    return Batch(ctx, h)
+
+
+def pd_bbh_pairs(ctx: Ctx, prof: Profiles, jobs) -> Batch:
+    """Best Hits both ways and BBH of many genome pairs [n_jobs, 2] of one
+    profiled dataset, in one launch sequence (pd_batch result layout)."""
+    jb = np.ascontiguousarray(jobs, dtype=np.uint32).reshape(-1)
+    h = C.c_void_p()
+    _check(ctx, _lib.pd_bbh_pairs(ctx.handle, prof.handle, _ptr(jb) if jb.size else None, jb.size // 2,
+                                  C.byref(h)), "pd_bbh_pairs")
     return Batch(ctx, h)
 
 
