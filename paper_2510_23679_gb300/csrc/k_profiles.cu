@@ -54,14 +54,17 @@ __global__ void __launch_bounds__(kEncThreads)
     k_encode_mark(const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr, uint32_t n_genes, int k,
                   unsigned long long* __restrict__ bitmap, const uint16_t* __restrict__ gene_genome,
                   const unsigned long long* __restrict__ genome_code_base, const int64_t* __restrict__ gene_src,
-                  int alpha, DevErr* err) {
+                  int alpha, uint64_t n_res, DevErr* err) {
   __shared__ uint8_t lut[256];
   init_letter_table(lut, alpha);
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_genes; g += warps) {
     const int64_t r0 = gene_src ? gene_src[g] : gene_ptr[g];
-    const uint32_t len = (uint32_t)(gene_ptr[g + 1] - gene_ptr[g]);
+    const int64_t glen = gene_ptr[g + 1] - gene_ptr[g];
+    // malformed offsets are reported by gene_windows; never read past them
+    if (glen < 0 || r0 < 0 || (!gene_src && (uint64_t)(r0 + glen) > n_res)) continue;
+    const uint32_t len = (uint32_t)glen;
     const uint8_t* s = res + r0;
     const unsigned long long base = genome_code_base ? genome_code_base[gene_genome[g]] : 0ull;
     for (uint32_t p = lane; p < len; p += 32) {
@@ -79,6 +82,44 @@ __global__ void __launch_bounds__(kEncThreads)
       if (ok) atomicOr(&bitmap[code >> 6], 1ull << (code & 63u));
     }
   }
+}
+
+// ------------------------------------------------------------ gene windows
+__host__ __device__ __forceinline__ uint32_t mv_table_cap(uint32_t La);
+
+__global__ void k_gene_windows(const int64_t* __restrict__ gene_ptr, uint32_t n_genes, uint64_t n_res, int check_end,
+                               int k, uint32_t* __restrict__ La, uint32_t* __restrict__ mid_list,
+                               uint32_t* __restrict__ long_list, unsigned long long* __restrict__ long_off,
+                               uint32_t* counts, unsigned long long* long_total, DevErr* err) {
+  for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n_genes; g += gridDim.x * blockDim.x) {
+    const int64_t r0 = gene_ptr[g], r1 = gene_ptr[g + 1];
+    const bool bad = r1 < r0 || (g == 0 && r0 != 0) || (check_end && g + 1 == n_genes && (uint64_t)r1 != n_res);
+    if (bad) {
+      raise_error(err, PD_ERR_ARG, g);
+      La[g] = 0;
+      continue;
+    }
+    const int64_t len = r1 - r0;
+    uint64_t w = len >= k ? (uint64_t)(len - k + 1) : 0;
+    if (w > PD_MAX_WINDOWS) {
+      raise_error(err, PD_ERR_GENE_TOO_LONG, g);
+      w = 0;
+    }
+    La[g] = (uint32_t)w;
+    const uint32_t cap = mv_table_cap((uint32_t)w);
+    if (cap > kMvMidCap) {
+      const uint32_t x = atomicAdd(&counts[1], 1u);
+      long_list[x] = g;
+      long_off[x] = atomicAdd(long_total, (unsigned long long)cap);
+    } else if (cap > kMvSmallCap) {
+      mid_list[atomicAdd(&counts[0], 1u)] = g;
+    }
+  }
+}
+
+__global__ void k_narrow_u64(const unsigned long long* __restrict__ in, uint64_t n, uint32_t* __restrict__ out) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+    out[i] = (uint32_t)in[i];
 }
 
 // ------------------------------------------------------------ mv_build
@@ -364,11 +405,27 @@ unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
                             unsigned long long* bitmap, const uint16_t* gene_genome,
                             const unsigned long long* genome_code_base, const int64_t* gene_src, int alpha,
-                            DevErr* err, cudaStream_t s) {
+                            uint64_t n_res, DevErr* err, cudaStream_t s) {
   const unsigned grid = grid_for((uint64_t)n_genes * 32, kEncThreads, 152u * 16u);
   PD_LAUNCH(L, "encode_mark", k_encode_mark<<<grid, kEncThreads, 0, s>>>(res, gene_ptr, n_genes, k, bitmap,
                                                                         gene_genome, genome_code_base, gene_src,
-                                                                        alpha, err));
+                                                                        alpha, n_res, err));
+  return cudaSuccess;
+}
+
+cudaError_t run_gene_windows(Launcher* L, const int64_t* gene_ptr, uint32_t n_genes, uint64_t n_res, int check_end,
+                             int k, uint32_t* La, uint32_t* mid_list, uint32_t* long_list,
+                             unsigned long long* long_off, uint32_t* counts, unsigned long long* long_total,
+                             DevErr* err, cudaStream_t s) {
+  PD_LAUNCH(L, "gene_windows",
+            k_gene_windows<<<grid_for(n_genes, 256, 152u * 8u), 256, 0, s>>>(gene_ptr, n_genes, n_res, check_end, k,
+                                                                            La, mid_list, long_list, long_off,
+                                                                            counts, long_total, err));
+  return cudaSuccess;
+}
+
+cudaError_t run_narrow_u64(Launcher* L, const unsigned long long* in, uint64_t n, uint32_t* out, cudaStream_t s) {
+  PD_LAUNCH(L, "narrow_u64", k_narrow_u64<<<grid_for(n, 256, 152u * 8u), 256, 0, s>>>(in, n, out));
   return cudaSuccess;
 }
 

@@ -112,6 +112,8 @@ PD_API pd_status pd_ctx_create(int device, void* cuda_stream, pd_alloc_fn alloc,
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaMalloc(&c->d_err, sizeof(DevErr));
   if (e == cudaSuccess) e = cudaMallocHost(&c->h_err, sizeof(DevErr));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_build, 8 * sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMallocHost(&c->h_genome_ptr, sizeof(int32_t) * (PD_MAX_GENOMES + 1));
   if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(DevErr));
   if (e == cudaSuccess && !alloc) {
     // Without hooks the context allocates from a pool of its own that keeps
@@ -131,6 +133,8 @@ PD_API pd_status pd_ctx_create(int device, void* cuda_stream, pd_alloc_fn alloc,
     cudaGetLastError();
     if (c->d_err) cudaFree(c->d_err);
     if (c->h_err) cudaFreeHost(c->h_err);
+    if (c->h_build) cudaFreeHost(c->h_build);
+    if (c->h_genome_ptr) cudaFreeHost(c->h_genome_ptr);
     if (c->own_pool) cudaMemPoolDestroy(c->pool);
     delete c;
     return PD_ERR_CUDA;
@@ -149,6 +153,8 @@ PD_API void pd_ctx_destroy(pd_ctx* c) {
   for (auto e : c->event_pool) cudaEventDestroy(e);
   cudaFree(c->d_err);
   cudaFreeHost(c->h_err);
+  cudaFreeHost(c->h_build);
+  cudaFreeHost(c->h_genome_ptr);
   // allocations still held by handles keep the pool alive until they are freed
   if (c->own_pool) cudaMemPoolDestroy(c->pool);
   delete c;
@@ -247,52 +253,37 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   if (n_genomes < 1 || n_genomes > PD_MAX_GENOMES)
     return fail(c, PD_ERR_ARG, "n_genomes must be in [1, " + std::to_string(PD_MAX_GENOMES) + "]");
   if (n_genes > 0x7FFFFFFFu) return fail(c, PD_ERR_ARG, "too many genes");
+  if (n_genes == 0 && n_res != 0 && !gene_src) return fail(c, PD_ERR_ARG, "residues without genes");
   CK(cudaSetDevice(c->device));
 
-  // ---- offsets on the host (validated; they size every buffer)
-  std::vector<int64_t> hg(n_genes + 1);
+  // ---- genome offsets on the host (small; checked before any kernel reads them,
+  // except on the non-segmented path with device offsets, where the checks
+  // come after the dictionary pass and before the first kernel that uses them)
   std::vector<int32_t> hgn(n_genomes + 1);
   const bool gp_dev = is_device_ptr(gene_ptr), gn_dev = is_device_ptr(genome_ptr);
-  CK(cudaMemcpyAsync(hg.data(), gene_ptr, sizeof(int64_t) * (n_genes + 1), cudaMemcpyDefault, c->stream));
-  CK(cudaMemcpyAsync(hgn.data(), genome_ptr, sizeof(int32_t) * (n_genomes + 1), cudaMemcpyDefault, c->stream));
-  if (gp_dev || gn_dev) CK(cudaStreamSynchronize(c->stream));
-  if (hg[0] != 0 || (!gene_src && (uint64_t)hg[n_genes] != n_res))
-    return fail(c, PD_ERR_ARG, "gene_ptr must run from 0 to n_res");
-  if (hgn[0] != 0 || (uint32_t)hgn[n_genomes] != n_genes)
-    return fail(c, PD_ERR_ARG, "genome_ptr must run from 0 to n_genes");
-  for (uint32_t i = 0; i < n_genomes; ++i)
-    if (hgn[i + 1] < hgn[i]) return fail(c, PD_ERR_ARG, "genome_ptr is decreasing at " + std::to_string(i));
-  std::vector<uint32_t> La(n_genes), win_off(n_genes + 1);
-  uint64_t W = 0;
-  std::vector<uint32_t> long_genes;
-  std::vector<unsigned long long> long_off;
-  uint64_t long_total = 0;
-  std::vector<uint32_t> mid_genes;
-  for (uint32_t g = 0; g < n_genes; ++g) {
-    const int64_t len = hg[g + 1] - hg[g];
-    if (len < 0) return fail(c, PD_ERR_ARG, "gene_ptr is decreasing at " + std::to_string(g));
-    const uint64_t w = (len >= k) ? (uint64_t)(len - k + 1) : 0;
-    if (w > PD_MAX_WINDOWS)
-      return fail(c, PD_ERR_GENE_TOO_LONG, "gene " + std::to_string(g) + " has " + std::to_string(w) +
-                                               " windows (max " + std::to_string(PD_MAX_WINDOWS) + ")");
-    La[g] = (uint32_t)w;
-    win_off[g] = (uint32_t)W;
-    W += w;
-    if (W > 0xFFFFFFF0ull) return fail(c, PD_ERR_ARG, "more than 2^32 k-mer windows in the dataset");
-    const uint32_t cap = pdg::mv_build_table_cap((uint32_t)w);
-    if (cap > 16384) {  // table beyond shared memory: global scratch
-      long_genes.push_back(g);
-      long_off.push_back(long_total);
-      long_total += cap;
-    } else if (cap > 2048) {  // table beyond the small shared-memory build
-      mid_genes.push_back(g);
-    }
+  const bool early_genomes = !gn_dev || genome_seg;
+  if (gn_dev) {
+    CK(cudaMemcpyAsync(c->h_genome_ptr, genome_ptr, sizeof(int32_t) * (n_genomes + 1), cudaMemcpyDeviceToHost,
+                       c->stream));
+    if (early_genomes) CK(cudaStreamSynchronize(c->stream));
+  } else {
+    std::copy(genome_ptr, genome_ptr + n_genomes + 1, c->h_genome_ptr);
   }
-  win_off[n_genes] = (uint32_t)W;
+  auto check_genomes = [&]() -> pd_status {
+    std::copy(c->h_genome_ptr, c->h_genome_ptr + n_genomes + 1, hgn.begin());
+    if (hgn[0] != 0 || (uint32_t)hgn[n_genomes] != n_genes)
+      return fail(c, PD_ERR_ARG, "genome_ptr must run from 0 to n_genes");
+    for (uint32_t i = 0; i < n_genomes; ++i)
+      if (hgn[i + 1] < hgn[i]) return fail(c, PD_ERR_ARG, "genome_ptr is decreasing at " + std::to_string(i));
+    return PD_OK;
+  };
+  if (early_genomes) {
+    pd_status st0 = check_genomes();
+    if (st0 != PD_OK) return st0;
+  }
 
   pd_profiles* P = new pd_profiles();
   P->ctx = c;
-  P->h_genome_ptr = hgn;
   std::unique_ptr<pd_profiles> guard(P);
   const uint64_t n_codes = pow_u64((uint64_t)alphabet, k);
   uint64_t n_seg = 1;
@@ -309,7 +300,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
                                         std::to_string(kMaxBitmapBytes >> 30) + " GiB)");
   }
   const uint64_t n_words = (n_seg * n_codes + 63) / 64;
-  const size_t G1 = std::max<uint32_t>(n_genes, 1), W1 = std::max<uint64_t>(W, 1);
+  const size_t G1 = std::max<uint32_t>(n_genes, 1);
   pdg::Launcher* L = &c->L;
 
   // ---- inputs on the device
@@ -323,7 +314,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   }
   if (!gp_dev) {
     ALLOC(d_gene_ptr, sizeof(int64_t) * (n_genes + 1));
-    CK(cudaMemcpyAsync(d_gene_ptr.p, hg.data(), sizeof(int64_t) * (n_genes + 1), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(d_gene_ptr.p, gene_ptr, sizeof(int64_t) * (n_genes + 1), cudaMemcpyHostToDevice,
                        c->stream));
     gp_devp = d_gene_ptr.as<int64_t>();
   }
@@ -332,13 +323,27 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   ALLOC(P->win_off, sizeof(uint32_t) * (n_genes + 1));
   ALLOC(P->gene_genome, sizeof(uint16_t) * G1);
   ALLOC(P->ginfo, sizeof(uint32_t) * G1);
-  CK(cudaMemcpyAsync(P->genome_ptr.p, hgn.data(), sizeof(int32_t) * (n_genomes + 1), cudaMemcpyHostToDevice,
-                     c->stream));
-  if (n_genes) CK(cudaMemcpyAsync(P->La.p, La.data(), sizeof(uint32_t) * n_genes, cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(P->win_off.p, win_off.data(), sizeof(uint32_t) * (n_genes + 1), cudaMemcpyHostToDevice,
-                     c->stream));
-  CK(pdg::run_gene_info(L, P->genome_ptr.as<int32_t>(), n_genomes, P->La.as<uint32_t>(),
-                        P->gene_genome.as<uint16_t>(), P->ginfo.as<uint32_t>(), c->stream));
+  CK(cudaMemcpyAsync(P->genome_ptr.p, genome_ptr, sizeof(int32_t) * (n_genomes + 1), cudaMemcpyDefault, c->stream));
+
+  // ---- window counts, window offsets and the gene classes, on the device
+  Buf d_win64, d_gtmp, d_wcount;
+  ALLOC(d_mid, sizeof(uint32_t) * G1);
+  ALLOC(d_long, sizeof(uint32_t) * G1);
+  ALLOC(d_long_off, sizeof(unsigned long long) * G1);
+  ALLOC(d_win64, sizeof(unsigned long long) * (n_genes + 1));
+  ALLOC(d_gtmp, pdg::scan_temp_bytes(n_genes + 1) + 64);
+  ALLOC(d_wcount, 4 * sizeof(unsigned long long));  // [n_mid, n_long] (u32), long_total (u64)
+  CK(cudaMemsetAsync(d_wcount.p, 0, 4 * sizeof(unsigned long long), c->stream));
+  unsigned long long* wcount64 = d_wcount.as<unsigned long long>();
+  if (n_genes)
+    CK(pdg::run_gene_windows(L, gp_devp, n_genes, n_res, gene_src ? 0 : 1, k, P->La.as<uint32_t>(),
+                             d_mid.as<uint32_t>(), d_long.as<uint32_t>(), d_long_off.as<unsigned long long>(),
+                             (uint32_t*)wcount64, wcount64 + 1, c->d_err, c->stream));
+  CK(pdg::scan_u32_to_u64(L, P->La.as<uint32_t>(), n_genes, d_win64.as<unsigned long long>(), d_gtmp.p, c->stream));
+  CK(pdg::run_narrow_u64(L, d_win64.as<unsigned long long>(), n_genes + 1, P->win_off.as<uint32_t>(), c->stream));
+  if (early_genomes)
+    CK(pdg::run_gene_info(L, P->genome_ptr.as<int32_t>(), n_genomes, P->La.as<uint32_t>(),
+                          P->gene_genome.as<uint16_t>(), P->ginfo.as<uint32_t>(), c->stream));
 
   if (genome_seg) {
     ALLOC(d_code_base, sizeof(unsigned long long) * n_genomes);
@@ -353,7 +358,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   if (n_genes)
     CK(pdg::run_encode_mark(L, res_dev, gp_devp, n_genes, k, P->bitmap.as<unsigned long long>(),
                             P->gene_genome.as<uint16_t>(), d_code_base.as<unsigned long long>(), gene_src,
-                            alphabet, c->d_err, c->stream));
+                            alphabet, n_res, c->d_err, c->stream));
   const uint32_t kOrderShift = 16;  // 65536 min-hash buckets
   const uint64_t n_order_b = (uint64_t)1 << (32 - kOrderShift);
   ALLOC(tmp, pdg::scan_temp_bytes(std::max<uint64_t>(std::max<uint64_t>(n_words, n_order_b), 24577)) + 64);
@@ -361,11 +366,27 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   CK(cudaMemsetAsync(d_counts.p, 0, 4 * sizeof(uint32_t), c->stream));
   CK(pdg::scan_popc_words(L, P->bitmap.as<unsigned long long>(), n_words, P->word_rank.as<uint32_t>(),
                           d_counts.as<uint32_t>(), tmp.p, c->stream));
-  uint32_t h_counts[4] = {0, 0, 0, 0};
-  CK(cudaMemcpyAsync(h_counts, d_counts.p, sizeof(h_counts), cudaMemcpyDeviceToHost, c->stream));
+  // one synchronisation: the dictionary size, the window total, the gene
+  // classes and any error found in the offsets or the letters
+  unsigned long long* hb = c->h_build;
+  CK(cudaMemcpyAsync(hb, d_counts.p, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hb + 2, d_win64.as<unsigned long long>() + n_genes, sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hb + 3, wcount64, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
   pd_status st = check_dev_err(c);  // synchronizes
   if (st != PD_OK) return st;
-  const uint64_t D = h_counts[0];
+  const uint64_t D = (uint32_t)hb[0];
+  const uint64_t W = hb[2];
+  const uint32_t n_mid = (uint32_t)hb[3], n_long = (uint32_t)(hb[3] >> 32);
+  const uint64_t long_total = hb[4];
+  if (W > 0xFFFFFFF0ull) return fail(c, PD_ERR_ARG, "more than 2^32 k-mer windows in the dataset");
+  if (!early_genomes) {
+    if ((st = check_genomes()) != PD_OK) return st;
+    CK(pdg::run_gene_info(L, P->genome_ptr.as<int32_t>(), n_genomes, P->La.as<uint32_t>(),
+                          P->gene_genome.as<uint16_t>(), P->ginfo.as<uint32_t>(), c->stream));
+  }
+  P->h_genome_ptr = hgn;
+  const size_t W1 = std::max<uint64_t>(W, 1);
 
   // ---- multiplicity vectors (and one index record per entry)
   // gene field wide enough to keep the all-ones id unused (see the packed
@@ -379,20 +400,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   ALLOC(P->mv_n, sizeof(uint32_t) * G1);
   ALLOC(minhash, sizeof(uint32_t) * G1);
   ALLOC(mvrec, sizeof(unsigned long long) * W1);
-  if (!mid_genes.empty()) {
-    ALLOC(d_mid, sizeof(uint32_t) * mid_genes.size());
-    CK(cudaMemcpyAsync(d_mid.p, mid_genes.data(), sizeof(uint32_t) * mid_genes.size(), cudaMemcpyHostToDevice,
-                       c->stream));
-  }
-  if (!long_genes.empty()) {
-    ALLOC(d_long, sizeof(uint32_t) * long_genes.size());
-    ALLOC(d_long_off, sizeof(unsigned long long) * long_off.size());
-    ALLOC(d_long_scratch, sizeof(unsigned long long) * long_total);
-    CK(cudaMemcpyAsync(d_long.p, long_genes.data(), sizeof(uint32_t) * long_genes.size(), cudaMemcpyHostToDevice,
-                       c->stream));
-    CK(cudaMemcpyAsync(d_long_off.p, long_off.data(), sizeof(unsigned long long) * long_off.size(),
-                       cudaMemcpyHostToDevice, c->stream));
-  }
+  if (n_long) ALLOC(d_long_scratch, sizeof(unsigned long long) * long_total);
   pdg::MvOut M;
   M.mv_id = P->mv_id.as<uint32_t>();
   M.mv_cnt = P->mv_cnt.as<uint16_t>();
@@ -411,8 +419,8 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   if (n_genes)
     CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
                          P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), M,
-                         d_mid.as<uint32_t>(), (uint32_t)mid_genes.size(), d_long.as<uint32_t>(), (uint32_t)long_genes.size(), d_long_scratch.as<unsigned long long>(),
-                         d_long_off.as<unsigned long long>(), c->stream));
+                         d_mid.as<uint32_t>(), n_mid, d_long.as<uint32_t>(), n_long,
+                         d_long_scratch.as<unsigned long long>(), d_long_off.as<unsigned long long>(), c->stream));
 
   // ---- inverted index: stable radix sort of the index records by k-mer id
   // (records arrive in gene order, so every posting list ends up gene-sorted)
@@ -443,13 +451,13 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
     CK(pdg::run_order(L, minhash.as<uint32_t>(), n_genes, kOrderShift, ocount.as<uint32_t>(),
                       P->order.as<uint32_t>(), tmp.p, c->stream));
 
-  uint32_t E32 = 0;
-  CK(cudaMemcpyAsync(&E32, P->post_ptr.as<uint32_t>() + D, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaMemcpyAsync(h_counts, d_counts.p, sizeof(h_counts), cudaMemcpyDeviceToHost, c->stream));
+  uint32_t* hb32 = (uint32_t*)c->h_build;  // [0] = E, [2..5] = d_counts
+  CK(cudaMemcpyAsync(hb32, P->post_ptr.as<uint32_t>() + D, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaMemcpyAsync(hb32 + 2, d_counts.p, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
   st = check_dev_err(c);  // synchronizes; temporaries are released after this
   if (st != PD_OK) return st;
-  const uint64_t E = E32;
-  const uint32_t max_posting = h_counts[1];
+  const uint64_t E = hb32[0];
+  const uint32_t max_posting = hb32[3];
 
   pdg::ProfilesView& v = P->view;
   v.k = k;

@@ -47,6 +47,9 @@ struct pd_ctx {
   pdg::Launcher L{nullptr};
   pdg::DevErr* d_err = nullptr;  // device error block
   pdg::DevErr* h_err = nullptr;  // pinned host mirror
+  // pinned host words the profile build reads back after its dictionary pass
+  unsigned long long* h_build = nullptr;  // [8]
+  int32_t* h_genome_ptr = nullptr;        // [PD_MAX_GENOMES + 1]
   cudaMemPool_t pool = nullptr;  // without hooks: allocate from this pool (null: the device's default pool)
   bool own_pool = false;         // the pool was created by (and is destroyed with) this context
   uint64_t pool_bytes = 0;       // bytes currently allocated through this context (pool allocations only)

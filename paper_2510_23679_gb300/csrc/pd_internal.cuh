@@ -278,10 +278,25 @@ cudaError_t scan_u32_to_u64(Launcher* L, const uint32_t* in, uint64_t n, unsigne
                             void* temp, cudaStream_t s);
 
 // profiles (k_profiles.cu)
+// Gene offsets -> window counts on the device.  Checks every gene (offsets
+// from 0, non-decreasing, ending at n_res unless check_end is 0; at most
+// PD_MAX_WINDOWS windows), recording PD_ERR_ARG / PD_ERR_GENE_TOO_LONG with
+// the gene as detail (such a gene gets La 0); lists the genes whose vector
+// table exceeds the small (mid) and the large (long) shared-memory build, with
+// a scratch offset for each long gene.  counts: [n_mid, n_long] (uint32) and
+// long_total (uint64, after them, 8-byte aligned).
+cudaError_t run_gene_windows(Launcher* L, const int64_t* gene_ptr, uint32_t n_genes, uint64_t n_res, int check_end,
+                             int k, uint32_t* La, uint32_t* mid_list, uint32_t* long_list,
+                             unsigned long long* long_off, uint32_t* counts, unsigned long long* long_total,
+                             DevErr* err, cudaStream_t s);
+// u64 -> u32 copy of n values.
+cudaError_t run_narrow_u64(Launcher* L, const unsigned long long* in, uint64_t n, uint32_t* out, cudaStream_t s);
+// n_res bounds the residues of every gene read through gene_ptr (genes read
+// through gene_src are trusted).
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
                             unsigned long long* bitmap, const uint16_t* gene_genome,
                             const unsigned long long* genome_code_base, const int64_t* gene_src, int alpha,
-                            DevErr* err, cudaStream_t s);
+                            uint64_t n_res, DevErr* err, cudaStream_t s);
 // Outputs of the multiplicity-vector build.
 struct MvOut {
   uint32_t* mv_id;

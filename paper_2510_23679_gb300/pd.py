@@ -228,10 +228,27 @@ class Ctx:
             raise PdError(st, "pd_ctx_create", "context creation failed")
         self.handle = h
 
-    def close(self):
-        if getattr(self, "handle", None):
+    # Every handle made with this context must be freed before pd_ctx_destroy.
+    # The garbage collector finalizes a reference cycle (a frame kept alive by
+    # a caught exception's traceback) in no fixed order, so the context counts
+    # its live handles and a close() that comes first waits for the last one.
+    def _retain(self):
+        self._live = getattr(self, "_live", 0) + 1
+
+    def _release(self):
+        self._live -= 1
+        if self._live == 0 and getattr(self, "_closing", False):
+            self._destroy()
+
+    def _destroy(self):
+        if getattr(self, "handle", None) and _lib is not None:
             _lib.pd_ctx_destroy(self.handle)
             self.handle = None
+
+    def close(self):
+        self._closing = True
+        if getattr(self, "_live", 0) == 0:
+            self._destroy()
 
     def __del__(self):
         self.close()
@@ -285,11 +302,13 @@ class _Handle:
     def __init__(self, ctx: Ctx, h: C.c_void_p):
         self.ctx = ctx
         self.handle = h
+        ctx._retain()
 
     def free(self):
         if getattr(self, "handle", None) and _lib is not None:
             getattr(_lib, self._free_name)(self.handle)
             self.handle = None
+            self.ctx._release()
 
     def __del__(self):
         self.free()

@@ -291,3 +291,31 @@ def test_index_lists_of_every_length(ctx, n_genes):
            for w in range(len(codes))}
     assert got == expect
     assert max(len(v) for v in expect.values()) == n_genes
+
+
+def test_malformed_offsets_are_errors(ctx):
+    """Offsets are checked on the device before any kernel reads past them:
+    decreasing, not starting at 0, not ending at n_res -- on host and device
+    inputs -- and a genome_ptr that does not cover the genes."""
+    import torch
+    res = np.frombuffer(b"ACDEFGHIKLMNPQRSTVWY" * 5, np.uint8).copy()
+    good_gp = np.array([0, 30, 60, 100], np.int64)
+    gn = np.array([0, 2, 3], np.int32)
+    bad_gps = [np.array([0, 30, 20, 100], np.int64), np.array([5, 30, 60, 100], np.int64),
+               np.array([0, 30, 60, 99], np.int64), np.array([0, 30, 60, 10_000], np.int64)]
+    for gp in bad_gps:
+        for dev in (False, True):
+            g = torch.from_numpy(gp).cuda() if dev else gp
+            r = torch.from_numpy(res).cuda() if dev else res
+            with pytest.raises(pd.PdError) as e:
+                pd.pd_build_profiles(ctx, r, g, gn, 3)
+            assert e.value.status == 1, (gp.tolist(), dev)
+    for bad_gn in (np.array([0, 4, 3], np.int32), np.array([0, 2, 4], np.int32), np.array([1, 2, 3], np.int32)):
+        for dev in (False, True):
+            n = torch.from_numpy(bad_gn).cuda() if dev else bad_gn
+            with pytest.raises(pd.PdError) as e:
+                pd.pd_build_profiles(ctx, res, good_gp, n, 3)
+            assert e.value.status == 1, (bad_gn.tolist(), dev)
+    # the context stays usable
+    prof = pd.pd_build_profiles(ctx, res, good_gp, gn, 3)
+    assert pd.pd_profiles_get_info(prof).n_genes == 3
