@@ -600,6 +600,41 @@ def main():
     peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
+    # ---- per-phase breakdown, after the timed region: each phase's wall time
+    # on the stream and the device time of its kernels (CUDA events around
+    # every launch), medians of three L2-flushed steps
+    def timed_phase(fn):
+        pd.pd_ctx_reset_timing(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        kms, kn = pd.pd_ctx_kernel_time(ctx, None)  # synchronizes the stream
+        return out, e0.elapsed_time(e1), kms, kn
+
+    ph = {"build": [], "best_hits": [], "bbh": []}
+    pd.pd_ctx_set_timing(ctx, True)
+    for i in range(3):
+        flush.fill_(i)
+        torch.cuda.synchronize()
+        p_, *t_b = timed_phase(lambda: pd.pd_build_profiles_alphabet(ctx, res_d, gp_d, gn_d, alpha, k))
+        h_, *t_h = timed_phase(lambda: pd.pd_best_hits_all(ctx, p_))
+        _, *t_x = timed_phase(lambda: pd.pd_bbh_all(ctx, p_, h_))
+        for name, t in (("build", t_b), ("best_hits", t_h), ("bbh", t_x)):
+            ph[name].append(t)
+    pd.pd_ctx_set_timing(ctx, False)
+    phases = {name: {"ms": statistics.median(t[0] for t in v), "kernel_ms": statistics.median(t[1] for t in v),
+                     "launches": int(v[0][2])} for name, v in ph.items()}
+    # encoder (profiles + inverted index) roofline: algorithmic bytes of one build
+    W, D = pinfo.n_windows, pinfo.n_distinct
+    passes = (max(1, int(D).bit_length()) + 8) // 9
+    enc_bytes = (2 * ds.n_residues + E * 6 + pinfo.n_genes * 4 + W * 8 + passes * W * 16
+                 + W * 8 + E * 4 + D * 4 + E * 12)
+    enc_ms = phases["build"]["kernel_ms"]
+    encoder = {"bound": "hbm", "alg_bytes": int(enc_bytes), "kernel_ms": enc_ms,
+               "achieved": enc_bytes / (enc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+               "frac": enc_bytes / (enc_ms / 1e3) / 1e9 / peak, "sort_passes": passes}
+
     # ---- end to end through the C ABI from pinned host buffers
     e2e = None
     if not args.no_e2e:
@@ -663,6 +698,8 @@ def main():
                          "kernel": "summin_bh",
                          "kernel_ms": k_avg_ms, "alg_bytes": alg_bytes, "peak_source": peak_src},
             "e2e": e2e,
+            "phases": phases,
+            "encoder_roofline": encoder,
             "gpu_launches": gpu_launches,
             "cpu_baseline": cpu,
             "clocks": clk.summary(),
