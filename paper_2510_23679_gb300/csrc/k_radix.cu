@@ -8,8 +8,9 @@
 //              counters), stored digit-major;
 //   (scan)     exclusive prefix over (digit, tile): the global start of each
 //              tile's run of each digit;
-//   downsweep  per tile: stable ranks within each warp from __match_any_sync
-//              groups, then per-digit offsets across the warps; the tile is
+//   downsweep  per tile: stable ranks within each warp from the lanes holding
+//              the same digit (one ballot per digit bit), then per-digit
+//              offsets across the warps; the tile is
 //              staged in shared memory in sorted order and written out, so
 //              consecutive threads store consecutive addresses of a digit run.
 // After the last pass `post_split` peels the low words into the posting array
@@ -21,8 +22,9 @@ namespace {
 
 constexpr int kRThreads = 256;
 constexpr int kRWarps = kRThreads / 32;
-constexpr int kRItems = 16;                       // records per lane
-constexpr uint32_t kTile = kRThreads * kRItems;   // 4096 records per tile
+constexpr int kRItems = 12;                       // records per lane
+constexpr uint32_t kTile = kRThreads * kRItems;   // 3072 records per tile
+constexpr int kRDownBlocks = 4;                   // resident downsweep blocks per SM (64 registers)
 constexpr int kMaxBins = 512;
 
 __device__ __forceinline__ uint32_t digit_of(unsigned long long r, uint32_t shift, uint32_t bins) {
@@ -50,7 +52,7 @@ __global__ void __launch_bounds__(kRThreads)
   for (uint32_t d = threadIdx.x; d < bins; d += kRThreads) counts[(uint64_t)d * n_tiles + blockIdx.x] = cnt[d];
 }
 
-__global__ void __launch_bounds__(kRThreads)
+__global__ void __launch_bounds__(kRThreads, kRDownBlocks)
     k_radix_downsweep(const unsigned long long* __restrict__ in, unsigned long long* __restrict__ out, uint64_t n,
                       uint32_t shift, uint32_t bins, uint32_t n_tiles, const uint32_t* __restrict__ goff) {
   __shared__ uint32_t wcnt[kRWarps][kMaxBins];  // per-warp counts, then per-warp offsets
@@ -74,7 +76,15 @@ __global__ void __launch_bounds__(kRThreads)
   for (int r = 0; r < kRItems; ++r) {
     const bool valid = t0 + (uint64_t)r * 32 + lane < n;
     const uint32_t d = valid ? digit_of(xr[r], shift, bins) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xffffffffu, d);
+    // lanes with the same digit: the AND over the digit's bits of each bit's
+    // ballot (or its complement); invalid lanes form a group of their own
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    if (!valid) peers = ~peers;
+    for (uint32_t b = 0; (1u << b) < bins; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? bal : ~bal;
+    }
     const uint32_t leader = (uint32_t)(__ffs(peers) - 1);
     uint32_t base = 0;
     if (valid && lane == leader) {
