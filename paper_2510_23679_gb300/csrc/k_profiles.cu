@@ -269,12 +269,27 @@ __global__ void __launch_bounds__(256)
   uint32_t m = 0;
   for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_genes; g += warps) {
     const uint32_t off = win_off[g], n = mv_n[g];
-    for (uint32_t e = lane; e < n; e += 32) {
-      const uint32_t id = mv_id[off + e];
-      const uint32_t lo = post_ptr[id], len = post_ptr[id + 1] - lo;
-      mv_post[off + e] = lo;
-      mv_plen[off + e] = len;
-      m = max(m, len);
+    // four entries per lane in flight: their ids, then their list bounds
+    for (uint32_t e0 = lane; e0 < n; e0 += 128) {
+      uint32_t id[4], lo[4], hi[4];
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) id[j] = e0 + 32 * j < n ? mv_id[off + e0 + 32 * j] : 0u;
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) {
+        lo[j] = hi[j] = 0;
+        if (e0 + 32 * j < n) {
+          lo[j] = post_ptr[id[j]];
+          hi[j] = post_ptr[id[j] + 1];
+        }
+      }
+#pragma unroll
+      for (uint32_t j = 0; j < 4; ++j) {
+        if (e0 + 32 * j < n) {
+          mv_post[off + e0 + 32 * j] = lo[j];
+          mv_plen[off + e0 + 32 * j] = hi[j] - lo[j];
+          m = max(m, hi[j] - lo[j]);
+        }
+      }
     }
   }
 #pragma unroll
