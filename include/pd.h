@@ -101,6 +101,10 @@ uint64_t pd_ctx_launch_count(const pd_ctx* ctx);
  * the stream and returns the summed milliseconds and launch count of kernel
  * `name` since the last reset (name = NULL: all kernels). */
 pd_status pd_ctx_set_timing(pd_ctx* ctx, int enable);
+/* Restrict the timing above to launches of kernel `name` (NULL or "": every
+ * kernel, the default), so that a timed region pays for the events of one
+ * kernel only.  The name is copied. */
+pd_status pd_ctx_set_timing_filter(pd_ctx* ctx, const char* name);
 pd_status pd_ctx_kernel_time(pd_ctx* ctx, const char* name, double* ms, uint64_t* launches);
 pd_status pd_ctx_reset_timing(pd_ctx* ctx);
 

@@ -37,7 +37,7 @@ static cudaEvent_t take_event(pd_ctx* c) {
 
 cudaError_t launch_begin(Launcher* L, const char* name) {
   pd_ctx* c = L->ctx;
-  if (c->timing) {
+  if (c->timing && (c->timing_filter.empty() || c->timing_filter == name)) {
     PendingTiming t{name, take_event(c), take_event(c)};
     if (!t.start || !t.stop) return cudaErrorMemoryAllocation;
     cudaError_t e = cudaEventRecord(t.start, c->stream);
@@ -173,6 +173,16 @@ PD_API uint64_t pd_ctx_launch_count(const pd_ctx* c) { return c ? c->launches : 
 PD_API pd_status pd_ctx_set_timing(pd_ctx* c, int enable) {
   if (!c) return PD_ERR_ARG;
   c->timing = enable != 0;
+  return PD_OK;
+}
+
+PD_API pd_status pd_ctx_set_timing_filter(pd_ctx* c, const char* name) {
+  if (!c) return PD_ERR_ARG;
+  try {
+    c->timing_filter = name ? name : "";
+  } catch (...) {
+    return fail(c, PD_ERR_OOM, "out of host memory");
+  }
   return PD_OK;
 }
 

@@ -41,6 +41,7 @@ struct pd_ctx {
   std::string err;
   uint64_t launches = 0;
   bool timing = false;
+  std::string timing_filter;  // empty: time every kernel; else only launches of this name
   std::vector<PendingTiming> pending;
   std::vector<cudaEvent_t> event_pool;
   std::map<std::string, std::pair<double, uint64_t>> kernel_ms;

@@ -94,6 +94,7 @@ _SIGNATURES = [
     ("pd_last_error", C.c_char_p, [_P]),
     ("pd_ctx_launch_count", C.c_uint64, [_P]),
     ("pd_ctx_set_timing", C.c_int, [_P, C.c_int]),
+    ("pd_ctx_set_timing_filter", C.c_int, [_P, C.c_char_p]),
     ("pd_ctx_kernel_time", C.c_int, [_P, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_uint64)]),
     ("pd_ctx_reset_timing", C.c_int, [_P]),
     ("pd_choose_k", C.c_int, [C.c_uint64, C.c_int]),
@@ -277,6 +278,12 @@ def pd_ctx_launch_count(ctx: Ctx) -> int:
 
 def pd_ctx_set_timing(ctx: Ctx, enable: bool) -> None:
     _check(ctx, _lib.pd_ctx_set_timing(ctx.handle, int(bool(enable))), "pd_ctx_set_timing")
+
+
+def pd_ctx_set_timing_filter(ctx: Ctx, name: str | None) -> None:
+    """Time only launches of kernel `name` (None: every kernel)."""
+    _check(ctx, _lib.pd_ctx_set_timing_filter(ctx.handle, name.encode() if name else None),
+           "pd_ctx_set_timing_filter")
 
 
 def pd_ctx_kernel_time(ctx: Ctx, name: str | None = None):

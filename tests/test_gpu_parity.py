@@ -319,3 +319,29 @@ def test_malformed_offsets_are_errors(ctx):
     # the context stays usable
     prof = pd.pd_build_profiles(ctx, res, good_gp, gn, 3)
     assert pd.pd_profiles_get_info(prof).n_genes == 3
+
+
+def test_kernel_timing_and_its_filter(pan4, ctx):
+    """Per-launch timing: every kernel by default, or the launches of one
+    kernel name; the filter changes no result."""
+    run, _ = pan4
+    prof = run.prof
+    ref = pd.pd_hits_copy(ctx, pd.pd_best_hits_all(ctx, prof))
+    pd.pd_ctx_reset_timing(ctx)
+    pd.pd_ctx_set_timing(ctx, True)
+    try:
+        pd.pd_best_hits_all(ctx, prof)
+        _, n_all = pd.pd_ctx_kernel_time(ctx, None)
+        ms_bh, n_bh = pd.pd_ctx_kernel_time(ctx, "summin_bh")
+        assert n_bh == 1 and ms_bh > 0 and n_all >= 2  # tier 1 and tier 2 at least
+        pd.pd_ctx_reset_timing(ctx)
+        pd.pd_ctx_set_timing_filter(ctx, "summin_bh")
+        got = pd.pd_hits_copy(ctx, pd.pd_best_hits_all(ctx, prof))
+        _, n_all = pd.pd_ctx_kernel_time(ctx, None)
+        _, n_bh = pd.pd_ctx_kernel_time(ctx, "summin_bh")
+        assert n_all == n_bh == 1
+        assert all(np.array_equal(a, b) for a, b in zip(got, ref))
+    finally:
+        pd.pd_ctx_set_timing(ctx, False)
+        pd.pd_ctx_set_timing_filter(ctx, None)
+        pd.pd_ctx_reset_timing(ctx)
