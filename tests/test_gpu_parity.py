@@ -345,3 +345,30 @@ def test_kernel_timing_and_its_filter(pan4, ctx):
         pd.pd_ctx_set_timing(ctx, False)
         pd.pd_ctx_set_timing_filter(ctx, None)
         pd.pd_ctx_reset_timing(ctx)
+
+
+@pytest.mark.parametrize("better_first", [True, False])
+def test_ratios_closer_than_float_resolution(ctx, better_first):
+    """Eq. (8) compares ratios exactly.  Two targets at 60000/60001 and
+    59999/60000 differ by 2.8e-10, less than a float's resolution there:
+    only the larger is a Best Hit, in either gene order (k = 1, so s is the
+    letter-count overlap)."""
+    assert np.float32(60000) / np.float32(60001) == np.float32(59999) / np.float32(60000)
+    rng = np.random.default_rng(7)
+    letters = np.frombuffer(b"ACDEFGHIKLMNPQRSTVWY", np.uint8)
+    a = rng.choice(letters, 60000)
+    better = np.concatenate([a, letters[:1]])  # s = 60000, den = 60000 + 60001 - 60000
+    worse = a[:-1]                             # s = 59999, den = 60000 + 59999 - 59999
+    genes = [a] + ([better, worse] if better_first else [worse, better])
+    res = np.concatenate(genes).astype(np.uint8)
+    gp = np.cumsum([0] + [len(g) for g in genes]).astype(np.int64)
+    gn = np.array([0, 1, 3], np.int32)
+    prof = pd.pd_build_profiles(ctx, res, gp, gn, 1)
+    want = 1 if better_first else 2
+    rp, cols, s = pd.pd_hits_copy(ctx, pd.pd_best_hits_all(ctx, prof))
+    assert cols[rp[0]:rp[1]].tolist() == [want] and s[rp[0]:rp[1]].tolist() == [60000]
+    rp, cols, s = pd.pd_hits_copy(ctx, pd.pd_best_hits(ctx, prof, 0, 1))
+    assert cols[rp[0]:rp[1]].tolist() == [want - 1] and s[rp[0]:rp[1]].tolist() == [60000]
+    # the oracle agrees
+    ds = synth.Pangenome(res, gp, gn, np.full(3, -1, np.int32))
+    assert oracle.pair_for_dataset(ds, 0, 1, 1).row_bh(0).tolist() == [want - 1]

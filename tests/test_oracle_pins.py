@@ -260,3 +260,26 @@ def test_rejects_letters_outside_alphabet():
     with pytest.raises(oracle.OracleError) as e:
         oracle.Profiles(ds.residues, ds.gene_ptr, 2)
     assert e.value.code == oracle.ERR_ALPHABET
+
+
+@pytest.mark.parametrize("better_first", [True, False])
+def test_bh_separates_ratios_closer_than_float_resolution(better_first):
+    """Eq. (8) by exact comparison: targets at 60000/60001 and 59999/60000
+    (equal as floats) give the larger alone; S and the denominators follow
+    from letter counts at k = 1 (a multiset intersection)."""
+    rng = np.random.default_rng(7)
+    letters = np.frombuffer(b"ACDEFGHIKLMNPQRSTVWY", np.uint8)
+    a = rng.choice(letters, 60000)
+    better = np.concatenate([a, letters[:1]])
+    worse = a[:-1]
+    genes = [a] + ([better, worse] if better_first else [worse, better])
+    res = np.concatenate(genes).astype(np.uint8)
+    gp = np.cumsum([0] + [len(g) for g in genes]).astype(np.int64)
+    prof = oracle.Profiles(res, gp, 1)
+    R = oracle.pair(prof, np.array([0, 1, 3], np.int32), 0, 1)
+    counts = [np.bincount(g, minlength=256) for g in genes]
+    s = [int(np.minimum(counts[0], counts[j]).sum()) for j in (1, 2)]
+    assert R.S[0].tolist() == s
+    ratios = [Fraction(s[j], len(genes[0]) + len(genes[j + 1]) - s[j]) for j in (0, 1)]
+    assert sorted(ratios) == [Fraction(59999, 60000), Fraction(60000, 60001)]
+    assert R.row_bh(0).tolist() == [int(np.argmax(ratios))] == [0 if better_first else 1]
