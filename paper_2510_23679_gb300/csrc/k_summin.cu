@@ -205,10 +205,11 @@ struct Table {
   uint32_t* vals;          // split layout only
   uint32_t* vpa;           // filtered queries only
   uint32_t* vpb;
-  TIdx* used;              // capacity cap
+  TIdx* used;              // capacity used_cap
   unsigned long long* out; // capacity out_cap
   uint32_t cap;            // power of two, a multiple of the block size
   uint32_t out_cap;
+  uint32_t used_cap;       // at most cap; a query with more occupied slots moves to the next tier
 };
 
 template <int kThreads, bool kEmitAll, bool kPacked, bool kFilter, typename TIdx>
@@ -362,15 +363,20 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
     __syncthreads();
   }
 
-  const bool overflow = sh->overflow != 0;
+  bool overflow = sh->overflow != 0;
   // Slots are visited interleaved (slot = i * kThreads + tid: conflict-free).
   const uint32_t slots = tb.cap / kThreads;
+  uint32_t n_occ = 0, pos = 0;
   if (!overflow) {
-    // ---- list the occupied slots (block prefix sum over per-thread counts)
+    // ---- count the occupied slots (block prefix sum over per-thread counts);
+    // more than the list holds: the query moves to the next tier
     uint32_t n_mine = 0;
     for (uint32_t i = 0; i < slots; ++i) n_mine += acc.occupied(i * kThreads + tid) ? 1u : 0u;
-    uint32_t n_occ;
-    uint32_t pos = block_exclusive_scan(n_mine, sh->warp_tmp, &n_occ);
+    pos = block_exclusive_scan(n_mine, sh->warp_tmp, &n_occ);
+    overflow = n_occ > tb.used_cap;  // uniform over the block
+  }
+  if (!overflow) {
+    // ---- list them
     for (uint32_t i = 0; i < slots; ++i) {
       const uint32_t h = i * kThreads + tid;
       if (acc.occupied(h)) tb.used[pos++] = (TIdx)h;
@@ -417,7 +423,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
       }
     }
   } else {
-    // the walk stopped early: clear every slot
+    // the walk stopped early, or the occupied slots do not fit the list: clear every slot
     for (uint32_t i = 0; i < slots; ++i) acc.clear(i * kThreads + tid);
   }
   __syncthreads();
@@ -459,22 +465,24 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
 }
 
 // ---- shared-memory tiers: [table][chunk | (used list, hits)][best]
-template <int kThreads, uint32_t kCap, uint32_t kOutCap, bool kPacked, bool kFilter = false>
+template <int kThreads, uint32_t kCap, uint32_t kOutCap, bool kPacked, bool kFilter = false,
+          uint32_t kUsedCap = kCap>
 struct SmemTier {
   static_assert(kCap % kThreads == 0, "table must split evenly over the block");
   static_assert(kCap <= 65536, "slot indices are 16-bit");
+  static_assert(kUsedCap <= kCap && kUsedCap % 8 == 0, "occupied-slot list");
   static constexpr size_t kTable = (size_t)kCap * (kPacked ? 4 : (kFilter ? 16 : 8));
-  static constexpr size_t kUsed = (size_t)kCap * 2;
+  static constexpr size_t kUsed = (size_t)kUsedCap * 2;
   static constexpr size_t kAfterWalk = kUsed + (size_t)kOutCap * 8;
   static constexpr size_t kUnion = Chunk<kThreads>::kBytes > kAfterWalk ? Chunk<kThreads>::kBytes : kAfterWalk;
   static size_t bytes(uint32_t n_best) { return kTable + kUnion + (size_t)(n_best ? n_best : 1) * 8; }
 };
 
 template <int kThreads, int kMinBlocks, uint32_t kCap, uint32_t kOutCap, bool kPacked, bool kEmitAll,
-          bool kFilter = false>
+          bool kFilter = false, uint32_t kUsedCap = kCap>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_summin_smem(ProfilesView P, QuerySet Q, HitsOut O,
                                                                       TierIO T, DevErr* err) {
-  using S = SmemTier<kThreads, kCap, kOutCap, kPacked, kFilter>;
+  using S = SmemTier<kThreads, kCap, kOutCap, kPacked, kFilter, kUsedCap>;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ Scalars sh;
   Table<uint16_t> tb;
@@ -484,6 +492,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_summin_smem(ProfilesVi
   tb.vpb = kFilter ? tb.vpa + kCap : nullptr;
   tb.cap = kCap;
   tb.out_cap = kOutCap;
+  tb.used_cap = kUsedCap;
   unsigned char* uni = smem + S::kTable;
   tb.used = (uint16_t*)uni;
   tb.out = (unsigned long long*)(uni + S::kUsed);
@@ -522,6 +531,7 @@ __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet 
   tb.out = B.out + (size_t)blockIdx.x * B.out_cap;
   tb.cap = B.cap;
   tb.out_cap = B.out_cap;
+  tb.used_cap = B.cap;
   uint32_t* c_post = (uint32_t*)smem;
   uint32_t* c_off = c_post + Chunk<kThreads>::kSize;
   uint16_t* c_cnt = (uint16_t*)(c_off + Chunk<kThreads>::kSize + 1);
@@ -544,11 +554,18 @@ __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet 
 // Tier 1 (packed 4096-slot table, several blocks per SM) and tier 2 (split
 // 16384-slot table, one 1024-thread block per SM) geometries.
 constexpr int kT1Threads = 256, kT1MinBlocks = 6;
-constexpr uint32_t kT1Cap = 4096, kT1Out = 512, kT1OutEmit = 3072;
+// Tier 1's shared memory is kept small enough for six blocks within the
+// 164 KB shared-memory carveout of an SM (at tens of genomes), which leaves
+// 92 KB of the SM's 256 KB as L1 for the posting loads of the walk; with 4 KB
+// more per block the carveout steps up to 196 KB, L1 shrinks to 60 KB and the
+// walk slows.  Hence a list of at most 3072 occupied slots and 448 hits per
+// query: a query beyond either moves to tier 2.
+constexpr uint32_t kT1Cap = 4096, kT1Out = 448, kT1OutEmit = 3072;
+constexpr uint32_t kT1Used = 3072;  // occupied slots listed; more and the query moves to tier 2
 constexpr int kT2Threads = 1024;
 constexpr uint32_t kT2Cap = 16384, kT2Out = 2048, kT2OutEmit = 4096;
-using T1 = SmemTier<kT1Threads, kT1Cap, kT1Out, true>;
-using T1E = SmemTier<kT1Threads, kT1Cap, kT1OutEmit, true>;
+using T1 = SmemTier<kT1Threads, kT1Cap, kT1Out, true, false, kT1Used>;
+using T1E = SmemTier<kT1Threads, kT1Cap, kT1OutEmit, true, false, kT1Used>;
 using T2 = SmemTier<kT2Threads, kT2Cap, kT2Out, false>;
 using T2E = SmemTier<kT2Threads, kT2Cap, kT2OutEmit, false>;
 static_assert(T1::kTable + T1::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 1 shared memory");
@@ -598,10 +615,10 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
   cudaError_t e;
   // tier 1: several resident blocks per SM, each looping over queries
   if (emit_all)
-    e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutEmit, true, true>, L, "summin_pairs",
+    e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutEmit, true, true, false, kT1Used>, L, "summin_pairs",
                     kT1Threads, T1E::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   else
-    e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false>, L, "summin_bh",
+    e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false, false, kT1Used>, L, "summin_bh",
                     kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   if (e != cudaSuccess) return e;
   // tier 2: one 1024-thread block per SM over the deferred queries (exits at once if none)

@@ -372,3 +372,24 @@ def test_ratios_closer_than_float_resolution(ctx, better_first):
     # the oracle agrees
     ds = synth.Pangenome(res, gp, gn, np.full(3, -1, np.int32))
     assert oracle.pair_for_dataset(ds, 0, 1, 1).row_bh(0).tolist() == [want - 1]
+
+
+@pytest.mark.parametrize("n_targets,n_tied", [(3000, 440), (3100, 460), (1000, 447), (1000, 449)])
+def test_occupied_list_and_hit_list_bounds(ctx, n_targets, n_tied):
+    """A query sharing one k-mer with n_targets genes, n_tied of them at the
+    shortest length (so tied Best Hits): around the tier-1 bounds of 3072
+    listed slots and 448 hits, every count gives the oracle's answer."""
+    rng = np.random.default_rng(n_targets + n_tied)
+    letters = np.frombuffer(b"FGHIKLMNPQRSTVWY", np.uint8)
+    targets = []
+    for t in range(n_targets):
+        extra = 6 if t < n_tied else 7 + int(rng.integers(0, 20))
+        targets.append(b"AC" + rng.choice(letters, size=extra).tobytes())
+    ds = synth.from_strings([[b"ACDE", b"GGGG"], targets])
+    run = GpuRun(ctx, ds, 2)
+    R = oracle_pairs(ds, 2, [(0, 1)])[(0, 1)]
+    rows, _ = run.best_hits(0, 1)
+    assert rows == csr_lists(R.row_ptr, R.row_col)
+    assert len(rows[0]) == n_tied
+    rp, cols, s, bbh, info = run.all_pairs()
+    assert [all_pairs_row_slice(ds, rp, cols, a, 1) for a in range(2)] == csr_lists(R.row_ptr, R.row_col)
