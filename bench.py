@@ -109,10 +109,10 @@ def config_of(ds, name, k, flush):
 
 
 # --------------------------------------------------------------------------- CPU oracle sample
-def captured_traffic(kernel_src, summary):
-    """DRAM bytes per launch from the committed ncu summary of the dominant
-    kernel on this workload, or None when there is no capture of it or the
-    kernel source changed since."""
+def captured_counter(kernel_src, summary, key="dram_bytes_per_launch"):
+    """A per-launch counter (DRAM bytes by default) from the committed ncu
+    summary of the dominant kernel on this workload, or None when there is no
+    capture of it or the kernel source changed since."""
     import hashlib
     import re
     try:
@@ -121,7 +121,7 @@ def captured_traffic(kernel_src, summary):
     except OSError:
         return None
     m_sha = re.search(r"sha256 \(first 16 hex\): ([0-9a-f]{16})", text)
-    m_val = re.search(r"dram_bytes_per_launch: (\d+)", text)
+    m_val = re.search(re.escape(key) + r": (\d+)", text)
     if not m_sha or not m_val or m_sha.group(1) != sha:
         return None
     return int(m_val.group(1))
@@ -686,6 +686,22 @@ def main():
                "sample": f"genome pairs {done} of the same workload ({npairs} gene pairs, {dt:.1f} s, "
                          f"profiles of both genomes included), oracle threads={cores}"}
 
+    # the pipe that bounds the sum-min kernel: L1TEX data-pipe wavefronts
+    # (shared-memory accumulator + posting loads; ncu counts one launch) per
+    # second of the live kernel time, against one wavefront per cycle per SM
+    # at the SM clock sampled during the timed region
+    clocks = clk.summary()
+    wavefronts = captured_counter("paper_2510_23679_gb300/csrc/k_summin.cu", f"summin_bh_{args.workload}.md",
+                                  "l1tex_wavefronts_per_launch")
+    l1tex = None
+    if wavefronts and clocks.get("sm_mhz"):
+        n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        l1_peak = n_sm * clocks["sm_mhz"] * 1e6 / 1e9
+        l1_achieved = wavefronts / (k_avg_ms / 1e3) / 1e9
+        l1tex = {"bound": "l1tex", "kernel": "summin_bh", "achieved": l1_achieved, "peak": l1_peak,
+                 "unit": "G wavefronts/s", "frac": l1_achieved / l1_peak, "wavefronts": wavefronts,
+                 "peak_source": f"{n_sm} SMs x 1 wavefront/cycle x {clocks['sm_mhz']:.0f} MHz"}
+
     if rank == 0:
         line = {
             "metric": "gene-pair GJ evals/s", "value": value, "unit": "gene-pairs/s", "n_gpus": world,
@@ -696,16 +712,17 @@ def main():
             "step_ms": step_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak,
-                         "traffic": captured_traffic("paper_2510_23679_gb300/csrc/k_summin.cu",
+                         "traffic": captured_counter("paper_2510_23679_gb300/csrc/k_summin.cu",
                                                      f"summin_bh_{args.workload}.md"),
                          "kernel": "summin_bh",
                          "kernel_ms": k_avg_ms, "alg_bytes": alg_bytes, "peak_source": peak_src},
             "e2e": e2e,
             "phases": phases,
             "encoder_roofline": encoder,
+            "l1tex_roofline": l1tex,
             "gpu_launches": gpu_launches,
             "cpu_baseline": cpu,
-            "clocks": clk.summary(),
+            "clocks": clocks,
             "stats": {"n_distinct_kmers": pinfo.n_distinct, "mv_entries": E, "postings_walked": J,
                       "best_hits": hinfo.n_hits, "bbh_pairs": n_bbh, "deferred_queries": hinfo.n_deferred,
                       "max_posting": pinfo.max_posting, "profile_bytes": pinfo.device_bytes},
