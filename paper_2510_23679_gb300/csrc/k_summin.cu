@@ -554,21 +554,30 @@ __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet 
 // Tier 1 (packed 4096-slot table, several blocks per SM) and tier 2 (split
 // 16384-slot table, one 1024-thread block per SM) geometries.
 constexpr int kT1Threads = 256, kT1MinBlocks = 6;
-// Tier 1's shared memory is kept small enough for six blocks within the
-// 164 KB shared-memory carveout of an SM (at tens of genomes), which leaves
-// 92 KB of the SM's 256 KB as L1 for the posting loads of the walk; with 4 KB
-// more per block the carveout steps up to 196 KB, L1 shrinks to 60 KB and the
-// walk slows.  Hence a list of at most 3072 occupied slots and 448 hits per
-// query: a query beyond either moves to tier 2.
-constexpr uint32_t kT1Cap = 4096, kT1Out = 448, kT1OutEmit = 3072;
-constexpr uint32_t kT1Used = 3072;  // occupied slots listed; more and the query moves to tier 2
+// Two tier-1 layouts, chosen per launch.  The compact one keeps six blocks
+// within the 164 KB shared-memory carveout of an SM, which leaves 92 KB of
+// the SM's 256 KB as L1 for the posting loads of the walk (with 4 KB more per
+// block the carveout steps up to 196 KB and L1 shrinks to 60 KB): at most 3072
+// listed occupied slots and 448 hits per query, a query beyond either moving
+// to tier 2.  Past kT1CompactGenomes target genomes the per-genome maxima no
+// longer leave room for that, and the full layout (4096 slots listed, 512
+// hits) defers fewer of the longer Best Hit rows of many-genome datasets.
+constexpr uint32_t kT1Cap = 4096, kT1OutEmit = 3072;
+constexpr uint32_t kT1Out = 448, kT1Used = 3072;          // compact layout
+constexpr uint32_t kT1OutFull = 512, kT1UsedFull = 4096;  // full layout
 constexpr int kT2Threads = 1024;
 constexpr uint32_t kT2Cap = 16384, kT2Out = 2048, kT2OutEmit = 4096;
 using T1 = SmemTier<kT1Threads, kT1Cap, kT1Out, true, false, kT1Used>;
+using T1F = SmemTier<kT1Threads, kT1Cap, kT1OutFull, true, false, kT1UsedFull>;
 using T1E = SmemTier<kT1Threads, kT1Cap, kT1OutEmit, true, false, kT1Used>;
+// genomes up to which six compact blocks (with their static scalars and the
+// 1 KB the runtime reserves per block) fit a 164 KB carveout
+constexpr uint32_t kT1CompactGenomes =
+    (uint32_t)((164u * 1024u / kT1MinBlocks - 1024u - sizeof(Scalars) - T1::kTable - T1::kUnion) / 8u);
+static_assert(kT1CompactGenomes >= 64, "compact tier-1 layout holds tens of genomes");
 using T2 = SmemTier<kT2Threads, kT2Cap, kT2Out, false>;
 using T2E = SmemTier<kT2Threads, kT2Cap, kT2OutEmit, false>;
-static_assert(T1::kTable + T1::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 1 shared memory");
+static_assert(T1F::kTable + T1F::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 1 shared memory");
 static_assert(T2::kTable + T2::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 2 shared memory");
 static_assert(T2E::kTable + T2E::kUnion + 8 <= 227 * 1024, "tier 2 (emit-all, one target genome) shared memory");
 // Filtered queries (Eqs. (6)-(7)): split 4096-slot table with the two
@@ -597,7 +606,8 @@ cudaError_t launch_smem(K kernel, Launcher* L, const char* name, int threads, si
 }  // namespace
 
 size_t summin_smem_bytes(uint32_t n_genomes, bool emit_all) {
-  return emit_all ? T1E::bytes(n_genomes) : T1::bytes(n_genomes);
+  return emit_all ? T1E::bytes(n_genomes)
+                  : (n_genomes <= kT1CompactGenomes ? T1::bytes(n_genomes) : T1F::bytes(n_genomes));
 }
 
 cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O, DevErr* err,
@@ -618,8 +628,11 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
     e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutEmit, true, true, false, kT1Used>, L, "summin_pairs",
                     kT1Threads, T1E::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   else
-    e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false, false, kT1Used>, L, "summin_bh",
-                    kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
+    e = n_best <= kT1CompactGenomes
+            ? launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false, false, kT1Used>, L,
+                          "summin_bh", kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s)
+            : launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutFull, true, false, false, kT1UsedFull>,
+                          L, "summin_bh", kT1Threads, T1F::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   if (e != cudaSuccess) return e;
   // tier 2: one 1024-thread block per SM over the deferred queries (exits at once if none)
   if (emit_all)

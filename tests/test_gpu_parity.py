@@ -393,3 +393,22 @@ def test_occupied_list_and_hit_list_bounds(ctx, n_targets, n_tied):
     assert len(rows[0]) == n_tied
     rp, cols, s, bbh, info = run.all_pairs()
     assert [all_pairs_row_slice(ds, rp, cols, a, 1) for a in range(2)] == csr_lists(R.row_ptr, R.row_col)
+
+
+@pytest.mark.parametrize("n_genomes", [80, 100])
+def test_both_tier1_layouts_against_oracle(ctx, n_genomes):
+    """Datasets below and above the genome count at which tier 1 switches from
+    its compact to its full shared-memory layout: all-pairs Best Hits and BBH
+    equal the oracle on sampled genome pairs."""
+    ds = synth.generate(n_genomes=n_genomes, genes_per_genome=("fixed", 12), n_families=30,
+                        length_dist=("uniform", 40, 160), core_frac=0.5, accessory_draw=None, subst_max=0.2,
+                        indel_max=0.03, paralog_frac=0.1, singleton_frac=0.05, seed=11)
+    k = 3
+    run = GpuRun(ctx, ds, k)
+    rp, cols, s, bbh, info = run.all_pairs()
+    for gi, gj in [(0, 1), (n_genomes - 1, 0), (37, n_genomes - 2)]:
+        R = oracle.pair_for_dataset(ds, gi, gj, k)
+        g0 = int(ds.genome_ptr[gi])
+        rows = [all_pairs_row_slice(ds, rp, cols, g0 + a, gj) for a in range(R.S.shape[0])]
+        assert rows == csr_lists(R.row_ptr, R.row_col), (gi, gj)
+        assert run.bbh(gi, gj) == [tuple(x) for x in R.bbh.tolist()], (gi, gj)
