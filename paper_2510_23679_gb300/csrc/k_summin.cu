@@ -605,11 +605,6 @@ cudaError_t launch_smem(K kernel, Launcher* L, const char* name, int threads, si
 
 }  // namespace
 
-size_t summin_smem_bytes(uint32_t n_genomes, bool emit_all) {
-  return emit_all ? T1E::bytes(n_genomes)
-                  : (n_genomes <= kT1CompactGenomes ? T1::bytes(n_genomes) : T1F::bytes(n_genomes));
-}
-
 cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O, DevErr* err,
                              bool emit_all, cudaStream_t s) {
   if (Q.n_queries == 0) return cudaSuccess;

@@ -95,22 +95,6 @@ __device__ __forceinline__ void block_bitonic_sort(K* a, uint32_t n) {
   }
 }
 
-// Ascending sort of one key per lane across a full warp.
-__device__ __forceinline__ uint32_t warp_sort32(uint32_t x) {
-  const uint32_t lane = threadIdx.x & 31u;
-#pragma unroll
-  for (uint32_t size = 2; size <= 32; size <<= 1) {
-#pragma unroll
-    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-      uint32_t y = __shfl_xor_sync(0xffffffffu, x, stride);
-      bool lower = (lane & stride) == 0;
-      bool asc = (lane & size) == 0;
-      x = (lower == asc) ? min(x, y) : max(x, y);
-    }
-  }
-  return x;
-}
-
 // Inclusive warp scan of v.
 __device__ __forceinline__ uint32_t warp_inclusive_scan(uint32_t v) {
   const uint32_t lane = threadIdx.x & 31u;
@@ -352,7 +336,6 @@ cudaError_t run_export_index(Launcher* L, const ProfilesView& P, int32_t* genes,
 // sum-min and Best Hits (k_summin.cu): shared-memory tiers 1 and 2 in one
 // call (tier 2 reads tier 1's deferred list on the device), then, only if
 // tier 2 deferred queries, the global-memory tier.
-size_t summin_smem_bytes(uint32_t n_genomes, bool emit_all);
 cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O, DevErr* err,
                              bool emit_all, cudaStream_t s);
 size_t summin_global_smem_bytes(uint32_t n_genomes);
