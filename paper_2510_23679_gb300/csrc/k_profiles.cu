@@ -70,16 +70,42 @@ __global__ void __launch_bounds__(kEncThreads)
     for (uint32_t p = lane; p < len; p += 32) {
       if (lut[s[p]] >= (uint32_t)alpha) raise_error(err, PD_ERR_ALPHABET, (unsigned long long)(r0 + p));
     }
-    for (uint32_t p = lane; p + (uint32_t)k <= len; p += 32) {
-      unsigned long long code = 0;
-      bool ok = true;
-      for (int t = 0; t < k; ++t) {
-        uint32_t c = lut[s[p + t]];
-        ok &= c < (uint32_t)alpha;
-        code = code * (unsigned long long)alpha + (c < (uint32_t)alpha ? c : 0u);
+    // Each lane rolls the code over a contiguous run of windows: the code of
+    // the window's last k-1 letters times alpha plus its last letter, then
+    // minus the leading letter's share for the next window (Eq. (1)).  A
+    // window is marked only if none of its letters is outside the alphabet.
+    const uint32_t n_win = len >= (uint32_t)k ? len - (uint32_t)k + 1u : 0u;
+    const uint32_t per = (n_win + 31u) / 32u;
+    const uint32_t p0 = lane * per, p1 = min(n_win, p0 + per);
+    if (p0 < p1) {
+      const unsigned long long a = (unsigned long long)alpha;
+      unsigned long long lead_w = 1;  // alpha^(k-1)
+      for (int t = 1; t < k; ++t) lead_w *= a;
+      unsigned long long code = 0;  // code of the k-1 letters before the next new letter
+      int64_t last_bad = -1;        // position of the last letter outside the alphabet
+      for (uint32_t q = p0; q + 1u < p0 + (uint32_t)k; ++q) {
+        uint32_t c = lut[s[q]];
+        if (c >= (uint32_t)alpha) {
+          last_bad = q;
+          c = 0;
+        }
+        code = code * a + c;
       }
-      code += base;
-      if (ok) atomicOr(&bitmap[code >> 6], 1ull << (code & 63u));
+      for (uint32_t p = p0; p < p1; ++p) {
+        const uint32_t q = p + (uint32_t)k - 1u;
+        uint32_t c = lut[s[q]];
+        if (c >= (uint32_t)alpha) {
+          last_bad = q;
+          c = 0;
+        }
+        code = code * a + c;
+        if (last_bad < (int64_t)p) {
+          const unsigned long long key = code + base;
+          atomicOr(&bitmap[key >> 6], 1ull << (key & 63u));
+        }
+        uint32_t lead = lut[s[p]];
+        code -= (unsigned long long)(lead < (uint32_t)alpha ? lead : 0u) * lead_w;
+      }
     }
   }
 }
