@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -156,7 +157,8 @@ class ClockSampler:
     def __init__(self, device_index):
         self.idx = device_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        # samples of this process only, summarised into the JSON line
+        self.path = os.path.join(tempfile.gettempdir(), f"pd_clocks_{os.getpid()}_{device_index}.csv")
 
     def __enter__(self):
         try:
