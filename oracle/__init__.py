@@ -17,6 +17,18 @@ function follows the passage of the paper named in its docstring:
 * ``families``     phase (c): connected components of the BBH graph;
 * ``paralog_hits`` Eq. (8) within one genome (the gene itself excluded);
 * ``filtered_pair`` Algorithms 2-3 with the theta and tau filters of Eqs. (6)-(7).
+
+A second, independent oracle (``pd_oracle_b.c``, no code shared with
+``pd_oracle.c``) walks an inverted index with a pool of host threads over the
+query genes -- the paper's own data decomposition ("Parallel implementation")
+-- and reaches the same integers fast enough to check whole datasets:
+
+* ``IndexB``       Eq. (1) and Algorithm 1 (codes, multiplicity vectors) plus
+                   the inverted index of the dataset;
+* ``best_hits_b``  Eq. (5) numerators by posting walk, Eq. (8) Best Hits of
+                   listed query genes towards listed genomes;
+* ``all_pairs_b``  every gene's Best Hits in every other genome and the BBH
+                   pairs of every genome pair (Eq. (9), Algorithm 3).
 """
 from __future__ import annotations
 
@@ -31,24 +43,31 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pd_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "libpd_oracle.so")
+_SRC_B = os.path.join(_HERE, "pd_oracle_b.c")
+_LIB_B = os.path.join(_HERE, "_build", "libpd_oracle_b.so")
 # A test may point the loader at another compiled copy (used to check that the
 # pins reject deliberately broken oracles).
 _LIB_OVERRIDE = os.environ.get("PD_ORACLE_LIB")
 _lock = threading.Lock()
 _lib = None
+_lib_b = None
 
 OK, ERR_ARG, ERR_ALPHABET, ERR_IDENTITY, ERR_OOM = 0, 1, 2, 3, 4
 
 
+def _compile(src: str, lib: str, force: bool) -> str:
+    os.makedirs(os.path.dirname(lib), exist_ok=True)
+    if force or not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread", "-o", tmp, src])
+        os.replace(tmp, lib)
+    return lib
+
+
 def build(force: bool = False) -> str:
-    """Compile pd_oracle.c into a shared library (gcc, plain C11)."""
-    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=gnu11", "-shared", "-fPIC", "-pthread",
-                               "-o", tmp, _SRC])
-        os.replace(tmp, _LIB)
-    return _LIB
+    """Compile pd_oracle.c and pd_oracle_b.c into two shared libraries (gcc, plain C11)."""
+    _compile(_SRC_B, _LIB_B, force)
+    return _compile(_SRC, _LIB, force)
 
 
 def _load():
@@ -345,3 +364,137 @@ def filtered_pair(ds, gi: int, gj: int, k: int, theta=(0, 1), tau=(0, 1), alphab
     cols = [best_set([(a, int(R.S[a, b]), int(R.Den[a, b])) for a in range(n_a) if cand[a][b]]) for b in range(n_b)]
     bbh = [(a, b) for a in range(n_a) for b in rows[a] if a in cols[b]]
     return rows, cols, bbh
+
+
+# --------------------------------------------------------------------------- oracle B
+def _load_b():
+    global _lib_b
+    with _lock:
+        if _lib_b is not None:
+            return _lib_b
+        override = os.environ.get("PD_ORACLE_B_LIB")  # a test may load a deliberately broken copy
+        lib = C.CDLL(override if override else _compile(_SRC_B, _LIB_B, False))
+        P, u8p, i64p, i32p, u32p = C.c_void_p, C.POINTER(C.c_uint8), C.POINTER(C.c_int64), \
+            C.POINTER(C.c_int32), C.POINTER(C.c_uint32)
+        lib.orb_build.restype = P
+        lib.orb_build.argtypes = [u8p, C.c_uint64, i64p, C.c_uint32, i32p, C.c_uint32, C.c_int, C.c_int, C.c_int,
+                                  C.POINTER(C.c_int)]
+        lib.orb_free.argtypes = [P]
+        lib.orb_n_entries.restype = C.c_uint64
+        lib.orb_n_entries.argtypes = [P]
+        lib.orb_n_lists.restype = C.c_uint64
+        lib.orb_n_lists.argtypes = [P]
+        lib.orb_La.restype = C.c_uint32
+        lib.orb_La.argtypes = [P, C.c_uint32]
+        lib.orb_best_hits.restype = P
+        lib.orb_best_hits.argtypes = [P, u32p, C.c_uint32, u8p, C.c_int, C.c_int, C.POINTER(C.c_int)]
+        lib.orb_hits_free.argtypes = [P]
+        lib.orb_hits_rows.restype = C.c_uint32
+        lib.orb_hits_rows.argtypes = [P]
+        lib.orb_hits_count.restype = C.c_uint64
+        lib.orb_hits_count.argtypes = [P]
+        lib.orb_hits_get.argtypes = [P, i64p, i32p, u32p]
+        lib.orb_bbh.restype = C.c_uint64
+        lib.orb_bbh.argtypes = [P, P, i32p, i32p, C.c_uint64]
+        _lib_b = lib
+        return lib
+
+
+def default_threads() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 4
+
+
+class IndexB:
+    """Oracle B over a whole dataset: multiplicity vectors (Algorithm 1) and
+    the inverted index (for every k-mer, its genes ascending)."""
+
+    def __init__(self, ds, k: int, alphabet: int = 20, n_threads: int = 0):
+        lib = _load_b()
+        self._res = np.ascontiguousarray(ds.residues, dtype=np.uint8)
+        self._gptr = np.ascontiguousarray(ds.gene_ptr, dtype=np.int64)
+        self.genome_ptr = np.ascontiguousarray(ds.genome_ptr, dtype=np.int32)
+        self.k, self.alphabet = int(k), int(alphabet)
+        self.n_genes = int(self._gptr.shape[0] - 1)
+        self.n_genomes = int(self.genome_ptr.shape[0] - 1)
+        self.n_threads = int(n_threads) or default_threads()
+        st = C.c_int(0)
+        res = self._res if self._res.size else np.zeros(1, np.uint8)
+        self._h = lib.orb_build(_ptr(res, C.c_uint8), self._res.size, _ptr(self._gptr, C.c_int64), self.n_genes,
+                                _ptr(self.genome_ptr, C.c_int32), self.n_genomes, self.k, self.alphabet,
+                                self.n_threads, C.byref(st))
+        if not self._h:
+            raise OracleError(st.value, "oracle B build")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib_b is not None:
+            _lib_b.orb_free(h)
+            self._h = None
+
+    @property
+    def n_entries(self) -> int:
+        return int(_lib_b.orb_n_entries(self._h))
+
+    def La(self, g: int) -> int:
+        return int(_lib_b.orb_La(self._h, g))
+
+
+def _hits_b(idx: IndexB, queries, targets=None, own_genome: bool = False):
+    lib = _load_b()
+    q = np.ascontiguousarray(queries, dtype=np.uint32)
+    qq = q if q.size else np.zeros(1, np.uint32)
+    mask = None
+    if targets is not None:
+        m = np.zeros(idx.n_genomes, np.uint8)
+        m[np.asarray(list(targets), dtype=np.int64)] = 1
+        mask = _ptr(m, C.c_uint8)
+    st = C.c_int(0)
+    h = lib.orb_best_hits(idx._h, _ptr(qq, C.c_uint32), q.size, mask, 1 if own_genome else 0, idx.n_threads,
+                          C.byref(st))
+    if not h:
+        raise OracleError(st.value, "oracle B best hits")
+    return h
+
+
+def best_hits_b(idx: IndexB, queries, targets=None, own_genome: bool = False):
+    """Eq. (8) Best Hits of the listed query genes (global ids) in each target
+    genome (``targets``: genome indices; None = every genome but the query's
+    own; ``own_genome`` adds the query's genome, the gene itself excluded).
+    Returns (row_ptr int64[n_q+1], cols int32 global gene ids ascending per
+    row, s uint32 sum-min)."""
+    lib = _load_b()
+    h = _hits_b(idx, queries, targets, own_genome)
+    try:
+        n = int(lib.orb_hits_count(h))
+        nr = int(lib.orb_hits_rows(h))
+        rp = np.zeros(nr + 1, np.int64)
+        cols = np.zeros(max(n, 1), np.int32)
+        s = np.zeros(max(n, 1), np.uint32)
+        lib.orb_hits_get(h, _ptr(rp, C.c_int64), _ptr(cols, C.c_int32), _ptr(s, C.c_uint32))
+        return rp, cols[:n], s[:n]
+    finally:
+        lib.orb_hits_free(h)
+
+
+def all_pairs_b(idx: IndexB):
+    """Algorithms 2-3 over every genome pair: (row_ptr, cols, s) of every
+    gene's Best Hits in every other genome (rows in gene order) and the BBH
+    pairs (a, b) with genome(a) < genome(b), ascending (int32 [n, 2])."""
+    lib = _load_b()
+    h = _hits_b(idx, np.arange(idx.n_genes, dtype=np.uint32))
+    try:
+        n = int(lib.orb_hits_count(h))
+        rp = np.zeros(idx.n_genes + 1, np.int64)
+        cols = np.zeros(max(n, 1), np.int32)
+        s = np.zeros(max(n, 1), np.uint32)
+        lib.orb_hits_get(h, _ptr(rp, C.c_int64), _ptr(cols, C.c_int32), _ptr(s, C.c_uint32))
+        nb = int(lib.orb_bbh(idx._h, h, None, None, 0))
+        a = np.zeros(max(nb, 1), np.int32)
+        b = np.zeros(max(nb, 1), np.int32)
+        lib.orb_bbh(idx._h, h, _ptr(a, C.c_int32), _ptr(b, C.c_int32), nb)
+        return rp, cols[:n], s[:n], np.stack([a[:nb], b[:nb]], axis=1)
+    finally:
+        lib.orb_hits_free(h)

@@ -62,6 +62,42 @@ PY_MUTANTS = {
 }
 
 
+# Mistakes planted in oracle B (pd_oracle_b.c), each rejected by its pins
+# against oracle A (test_oracle_b.py).
+SRC_B = os.path.join(ROOT, "oracle", "pd_oracle_b.c")
+B_MUTANTS = {
+    "b_min_becomes_max": ("acc[b] += ca < cb ? ca : cb;", "acc[b] += ca > cb ? ca : cb;"),
+    "b_window_count_off_by_one": ("const uint64_t La = len >= (uint64_t)k ? len - (uint64_t)k + 1 : 0;",
+                                  "const uint64_t La = len > (uint64_t)k ? len - (uint64_t)k : 0;"),
+    "b_own_genome_kept": ("if (gb == ga ? !J->own_genome : !J->target_genome[gb]) continue;",
+                          "if (gb != ga && !J->target_genome[gb]) continue;"),
+    "b_ties_dropped": ("if (ratio_cmp(s, den, best_s[gb], best_d[gb]) == 0) hit[n_hit++] = b;",
+                       "if (ratio_cmp(s, den, best_s[gb], best_d[gb]) == 0 && (n_hit == 0 || "
+                       "X->genome_of[hit[n_hit - 1]] != gb)) hit[n_hit++] = b;"),
+    "b_denominator_without_overlap": ("const uint32_t s = acc[b], den = X->La[a] + X->La[b] - s;\n      if (best_s",
+                                      "const uint32_t s = acc[b], den = X->La[a] + X->La[b];\n      if (best_s"),
+    "b_bbh_one_sided": ("      if (!row_has(H, b, (int32_t)a)) continue;\n", ""),
+    "b_multiplicity_ignored": ("X->mv_cnt[o] = (uint32_t)(q - p);", "X->mv_cnt[o] = 1u;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(B_MUTANTS))
+def test_oracle_b_pins_reject_mutant(name, tmp_path):
+    old, new = B_MUTANTS[name]
+    src = open(SRC_B).read()
+    assert src.count(old) == 1, f"mutation anchor for {name} not found exactly once"
+    mutant_c = tmp_path / "mutant_b.c"
+    mutant_c.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant_b.so"
+    subprocess.check_call(["gcc", "-O1", "-std=gnu11", "-shared", "-fPIC", "-pthread", "-o", str(so),
+                           str(mutant_c)])
+    env = dict(os.environ, PD_ORACLE_B_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        "-k", "not pan50x3000", os.path.join(ROOT, "tests", "test_oracle_b.py")],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert r.returncode != 0, f"mutant {name} survived the oracle-B pins:\n{r.stdout[-2000:]}"
+
+
 @pytest.mark.parametrize("name", sorted(MUTANTS))
 def test_pins_reject_mutant(name, tmp_path):
     old, new = MUTANTS[name]
