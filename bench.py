@@ -10,7 +10,7 @@ per second with inputs resident in HBM; `e2e` is the same metric through the
 public C ABI from pinned host buffers (host->device copy of the residues and
 offsets and device->host copy of the BBH pairs inside the timed region).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload pan50x3000]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload pan200x4000]
   python bench.py --impl reference ...   (the CPU oracle on bounded samples)
 """
 from __future__ import annotations
@@ -33,6 +33,7 @@ import numpy as np  # noqa: E402
 from paper_2510_23679_gb300 import synth  # noqa: E402
 
 L2_FLUSH_BYTES = 512 << 20  # larger than the 129 MB L2
+L2_NOTE = f"flushed ({L2_FLUSH_BYTES >> 20} MB write) between steps"
 
 
 def parse():
@@ -41,20 +42,32 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="pan50x3000", choices=sorted(synth.WORKLOADS) + ["jobs", "served", "pairs"],
+    ap.add_argument("--workload", default="pan200x4000", choices=sorted(synth.WORKLOADS) + ["jobs", "served", "pairs"],
                     help="a plain pangenome, 'jobs': a batch of independent genome-pair jobs, or 'served': "
                          "genomes arriving at a resident index")
     ap.add_argument("--rates", default="2,5,10,20,50", help="arrival rates (genomes/s) of --workload served")
     ap.add_argument("--seconds-per-rate", type=float, default=20.0,
                     help="arrivals per rate: min(incoming, rate x this)")
     ap.add_argument("--incoming", type=int, default=500, help="incoming genomes of --workload served")
+    ap.add_argument("--min-arrivals", type=int, default=100,
+                    help="arrivals per rate of --workload served at least (so p99 is a percentile of many)")
     ap.add_argument("--pairs-of", default="pan200x4000", choices=sorted(synth.WORKLOADS),
                     help="the pangenome whose genome pairs --workload pairs compares")
     ap.add_argument("--jobs", type=int, default=2000, help="jobs in the batch (--workload jobs)")
     ap.add_argument("--no-per-pair", action="store_true", help="skip the one-pair-per-launch comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-served", action="store_true",
+                    help="skip the genome-add latency probe of the plain workload's line")
+    ap.add_argument("--served-rate", type=float, default=20.0,
+                    help="arrival rate (genomes/s) of the latency probe in the plain workload's line")
+    ap.add_argument("--served-arrivals", type=int, default=100,
+                    help="arrivals of the latency probe in the plain workload's line")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="bounded oracle sample length")
+    ap.add_argument("--multi", default="shard", choices=["shard", "replicas"],
+                    help="N > 1: 'shard' splits the one dataset's query genes across the ranks (the index is "
+                         "replicated, the Best Hit rows are gathered to rank 0, BBH runs there); 'replicas' gives "
+                         "each rank a dataset of its own")
     return ap.parse_args()
 
 
@@ -101,12 +114,20 @@ def make_workload(name, rank):
     return ds
 
 
-def config_of(ds, name, k, flush):
+def parallelism_of(world, multi):
+    if world == 1:
+        return "1 GPU"
+    if multi == "shard":
+        return f"query genes sharded x{world}; index replicated; rows gathered to rank 0"
+    return f"replicas x{world} (a dataset per rank)"
+
+
+def config_of(ds, name, k, flush, parallelism="1 GPU"):
     return {"workload": f"{name}: {ds.n_genomes} genomes, {ds.n_genes} genes, {ds.n_residues} residues, "
                         f"k={k}, {'nucleotide' if alphabet_of(name) == 4 else 'amino-acid'} alphabet, "
                         f"all {ds.n_genomes * (ds.n_genomes - 1) // 2} genome pairs",
             "n_genomes": ds.n_genomes, "n_genes": ds.n_genes, "n_residues": ds.n_residues, "k": k,
-            "logical_pairs_per_step": ds.logical_pairs(), "l2": flush, "parallelism": "replicas"}
+            "logical_pairs_per_step": ds.logical_pairs(), "l2": flush, "parallelism": parallelism}
 
 
 # --------------------------------------------------------------------------- CPU oracle sample
@@ -214,17 +235,22 @@ def run_reference(args):
     per_step = max(1.0, args.cpu_seconds / max(1, args.steps))
     for _ in range(args.warmup):
         oracle_sample(ds, k, 0.0, cores, alpha)  # one genome pair each
-    rates, samples = [], []
+    rates, samples, step_ms = [], [], []
     for _ in range(args.steps):
         r, dt, done, npairs = oracle_sample(ds, k, per_step, cores, alpha)
         rates.append(r)
         samples.append(npairs)
+        step_ms.append(dt * 1e3)
     value = statistics.median(rates)
-    ms = ds.logical_pairs() / value * 1e3
+    # ms_per_step is the measured time of one sampled step; the time the
+    # oracle would take for the whole workload is extrapolated from its rate
     line = {"metric": "gene-pair GJ evals/s", "value": value, "unit": "gene-pairs/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "impl": "reference", "config": config_of(ds, args.workload, k, "n/a (CPU)"),
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(step_ms),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "impl": "reference",
+            "config": config_of(ds, args.workload, k, L2_NOTE, parallelism_of(world, args.multi)),
+            "step": "a bounded sample of the workload: whole genome pairs until the per-step time is reached",
+            "whole_workload_ms_extrapolated": ds.logical_pairs() / value * 1e3,
             "cpu_baseline": {"value": value, "unit": "gene-pairs/s", "cores": cores, "kind": "oracle",
                              "sample": f"whole genome pairs of the workload per step (~{per_step:.0f} s each, "
                                        f"{statistics.median(samples):.3g} gene pairs), oracle threads={cores}"},
@@ -353,13 +379,72 @@ def run_batch(args):
 
 
 # --------------------------------------------------------------------------- served index
+def serve_rate(pd, ctx, res, k, incoming, rate, n, budget, rng):
+    """Serve the first n incoming genomes, arriving as a Poisson process of
+    `rate` genomes/s, on a fresh index over the resident pangenome `res`.
+    Latency = answer time - submission time (the library's steady clock)."""
+    gaps = rng.exponential(1.0 / rate, size=n)
+    index = pd.pd_index_create(ctx, res.residues, res.gene_ptr, res.genome_ptr, k, budget)
+    # warm-up: one request through a separate index of the same size
+    warm = pd.pd_index_create(ctx, res.residues, res.gene_ptr, res.genome_ptr, k, budget)
+    pd.pd_index_poll(warm, pd.pd_index_submit(warm, *incoming[0]), -1)
+    warm.free()
+    tickets = []
+    start = time.perf_counter()
+    due = start
+    for i in range(n):
+        due += gaps[i]
+        d = due - time.perf_counter()
+        if d > 0:
+            time.sleep(d)
+        tickets.append(pd.pd_index_submit(index, *incoming[i]))
+    lat, t_first, t_last, ticks = [], None, None, []
+    for t in tickets:
+        info = pd.pd_reply_get_info(pd.pd_index_poll(index, t, -1))
+        assert info.status == 0, info.status
+        lat.append((info.t_done_ns - info.t_submit_ns) / 1e6)
+        t_first = info.t_submit_ns if t_first is None else min(t_first, info.t_submit_ns)
+        t_last = info.t_done_ns if t_last is None else max(t_last, info.t_done_ns)
+        ticks.append(info.tick_requests)
+    ii = pd.pd_index_get_info(index)
+    out = {"arrivals": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "mean_ms": float(np.mean(lat)), "max_ms": float(np.max(lat)),
+           "sustained_genomes_per_s": n / ((t_last - t_first) / 1e9),
+           "offered_genomes_per_s": rate, "ticks": int(ii.ticks),
+           "max_requests_per_tick": int(ii.max_tick_requests),
+           "resident_genomes_at_end": int(ii.n_genomes),
+           "index_device_bytes_at_end": int(ii.device_bytes)}
+    index.free()
+    return out
+
+
+def served_probe(args, pd, ctx):
+    """Genome-add latency beside the plain workload's throughput: a resident
+    index of 100 genomes of the pan50x3000 model answers `served_arrivals`
+    incoming genomes (U[1000, 7000] genes) arriving at `served_rate`/s."""
+    t0 = time.perf_counter()
+    ds = synth.served_stream(100, args.served_arrivals, seed=5)
+    gen_s = time.perf_counter() - t0
+    res = ds.subset(list(range(100)))
+    k = pd.pd_choose_k(res.n_residues)
+    incoming = [synth.genome_of(ds, x) for x in range(100, ds.n_genomes)]
+    rng = np.random.Generator(np.random.PCG64(55))
+    out = serve_rate(pd, ctx, res, k, incoming, args.served_rate, len(incoming), 120 << 30, rng)
+    out.update({"resident_genomes": 100, "resident_genes": res.n_genes, "k": k, "hbm_budget_bytes": 120 << 30,
+                "generation_s": gen_s,
+                "workload": f"resident 100 genomes (pan50x3000 model, {res.n_genes} genes, k={k}); "
+                            f"{len(incoming)} incoming genomes of U[1000,7000] genes, Poisson arrivals at "
+                            f"{args.served_rate:g}/s"})
+    return out
+
+
 def run_served(args):
     """Served form: a resident index of 100 genomes (the pan50x3000 model)
     answers incoming genomes (gene counts U[1000, 7000]) arriving as a
     Poisson process; each answer holds the genome's Best Hits in every
     resident genome and its BBH pairs, after which the genome is resident.
-    For each arrival rate a fresh index serves min(incoming, rate x
-    seconds-per-rate) arrivals; latency = answer time - submission time (the
+    For each arrival rate a fresh index serves min(incoming, max(min-arrivals,
+    rate x seconds-per-rate)) arrivals; latency = answer time - submission time (the
     library's steady clock).  Beside it: one full recomputation (profiles,
     all-pairs Best Hits and BBH of every genome) at the final size."""
     t0 = time.perf_counter()
@@ -380,39 +465,8 @@ def run_served(args):
     clk_all = None
     with ClockSampler(0) as clk:
         for rate in [float(x) for x in args.rates.split(",")]:
-            n = int(min(len(incoming), max(1, round(rate * args.seconds_per_rate))))
-            gaps = rng.exponential(1.0 / rate, size=n)
-            index = pd.pd_index_create(ctx, res.residues, res.gene_ptr, res.genome_ptr, k, budget)
-            # warm-up: one request through a separate index of the same size
-            warm = pd.pd_index_create(ctx, res.residues, res.gene_ptr, res.genome_ptr, k, budget)
-            pd.pd_index_poll(warm, pd.pd_index_submit(warm, *incoming[0]), -1)
-            warm.free()
-            tickets = []
-            start = time.perf_counter()
-            due = start
-            for i in range(n):
-                due += gaps[i]
-                d = due - time.perf_counter()
-                if d > 0:
-                    time.sleep(d)
-                tickets.append(pd.pd_index_submit(index, *incoming[i]))
-            lat, t_first, t_last, ticks = [], None, None, []
-            for t in tickets:
-                info = pd.pd_reply_get_info(pd.pd_index_poll(index, t, -1))
-                assert info.status == 0, info.status
-                lat.append((info.t_done_ns - info.t_submit_ns) / 1e6)
-                t_first = info.t_submit_ns if t_first is None else min(t_first, info.t_submit_ns)
-                t_last = info.t_done_ns if t_last is None else max(t_last, info.t_done_ns)
-                ticks.append(info.tick_requests)
-            ii = pd.pd_index_get_info(index)
-            per_rate[str(rate)] = {"arrivals": n, "p50_ms": float(np.percentile(lat, 50)),
-                                   "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(np.mean(lat)),
-                                   "sustained_genomes_per_s": n / ((t_last - t_first) / 1e9),
-                                   "offered_genomes_per_s": rate, "ticks": int(ii.ticks),
-                                   "max_requests_per_tick": int(ii.max_tick_requests),
-                                   "resident_genomes_at_end": int(ii.n_genomes),
-                                   "index_device_bytes_at_end": int(ii.device_bytes)}
-            index.free()
+            n = int(min(len(incoming), max(args.min_arrivals, round(rate * args.seconds_per_rate))))
+            per_rate[str(rate)] = serve_rate(pd, ctx, res, k, incoming, rate, n, budget, rng)
             torch.cuda.synchronize()
         clk_all = clk.summary()
     # full recomputation at the final size (every genome, all pairs)
@@ -512,6 +566,89 @@ def run_pairs(args):
     return 0
 
 
+# --------------------------------------------------------------------------- one dataset over N GPUs
+def run_sharded(args):
+    """N > 1, one dataset: every rank profiles the whole dataset (the index is
+    replicated), computes the Best Hit rows of its shard of the query genes
+    (pd_best_hits_shard), the rows are all-gathered (NCCL) and rank 0
+    assembles them (pd_hits_import) and runs BBH.  value = the dataset's
+    logical pairs / the slowest rank's step time (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2510_23679_gb300 import pd, shards
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local)
+    ds = synth.workload(args.workload)
+    alpha = alphabet_of(args.workload)
+    k = pd.pd_choose_k(ds.n_residues, alpha)
+    ctx = pd.pd_ctx_create(local)
+    stream = torch.cuda.current_stream(dev)
+    res_d = torch.from_numpy(ds.residues).to(dev)
+    gp_d = torch.from_numpy(ds.gene_ptr).to(dev)
+    gn_d = torch.from_numpy(ds.genome_ptr).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+    def step(res, gp, gn):
+        prof = pd.pd_build_profiles_alphabet(ctx, res, gp, gn, alpha, k)
+        hits, bbh = shards.sharded_bbh(ctx, prof)
+        return prof, hits, bbh
+
+    for _ in range(args.warmup):
+        step(res_d, gp_d, gn_d)
+    torch.cuda.synchronize()
+    pd.pd_ctx_reset_timing(ctx)
+    pd.pd_ctx_set_timing_filter(ctx, "summin_bh")
+    pd.pd_ctx_set_timing(ctx, True)
+    launches0 = pd.pd_ctx_launch_count(ctx)
+    times = []
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.fill_(i)
+            dist.barrier()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            keep = step(res_d, gp_d, gn_d)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    dist.barrier()
+    gpu_launches = pd.pd_ctx_launch_count(ctx) - launches0
+    k_ms, k_n = pd.pd_ctx_kernel_time(ctx, "summin_bh")
+    pd.pd_ctx_set_timing(ctx, False)
+    ms_local = sum(times) / len(times)
+    ms = max_over_ranks(ms_local, world)
+    pairs = ds.logical_pairs()
+    # roofline of this rank's shard: its postings walked and hits, and its
+    # share (1/world) of the vector, row and gene bytes
+    prof, hits, bbh = keep
+    pinfo = pd.pd_profiles_get_info(prof)
+    shard_hits = pd.pd_hits_get_info(pd.pd_best_hits_shard(ctx, prof, rank, world))
+    alg = (pinfo.n_entries * 14 + pinfo.n_genes * 12) / world + shard_hits.postings_walked * 4 + \
+        shard_hits.n_hits * 8
+    k_avg = k_ms / max(1, k_n)
+    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    clocks = clk.summary()
+    if rank == 0:
+        line = {"metric": "gene-pair GJ evals/s", "value": pairs / (ms / 1e3), "unit": "gene-pairs/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "u32",
+                "data": "synthetic",
+                "config": config_of(ds, args.workload, k, L2_NOTE, parallelism_of(world, "shard")),
+                "genome_pairs_per_s": ds.n_genomes * (ds.n_genomes - 1) // 2 / (ms / 1e3), "step_ms": times,
+                "roofline": {"bound": "hbm", "achieved": alg / (k_avg / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                             "frac": alg / (k_avg / 1e3) / 1e9 / peak, "traffic": None, "kernel": "summin_bh",
+                             "kernel_ms": k_avg, "alg_bytes": alg, "scope": "rank 0's shard"},
+                "e2e": None, "gpu_launches": gpu_launches, "cpu_baseline": None, "clocks": clocks,
+                "stats": {"best_hits": pd.pd_hits_get_info(hits).n_hits, "bbh_pairs": pd.pd_bbh_count(bbh)}}
+        print(json.dumps(line))
+    dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -526,6 +663,8 @@ def main():
     from paper_2510_23679_gb300 import pd
 
     rank, world, local = dist_info()
+    if world > 1 and args.multi == "shard":
+        return run_sharded(args)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("gloo")
@@ -641,26 +780,37 @@ def main():
                "achieved": enc_bytes / (enc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                "frac": enc_bytes / (enc_ms / 1e3) / 1e9 / peak, "sort_passes": passes}
 
-    # ---- end to end through the C ABI from pinned host buffers
+    # ---- end to end through the C ABI from pinned host buffers: inputs
+    # copied in, and the whole result (the Best Hit CSR with each hit's
+    # sum-min, and the BBH pairs) copied back, every step
     e2e = None
     if not args.no_e2e:
         res_h = torch.from_numpy(ds.residues).pin_memory()
         gp_h = torch.from_numpy(ds.gene_ptr).pin_memory()
         gn_h = torch.from_numpy(ds.genome_ptr).pin_memory()
-        out_a = torch.empty(max(n_bbh, 1) * 2, dtype=torch.int32).pin_memory()
-        out_b = torch.empty(max(n_bbh, 1) * 2, dtype=torch.int32).pin_memory()
+        n_hits0 = int(hinfo.n_hits)
+        host = {"a": torch.empty(max(n_bbh, 1), dtype=torch.int32).pin_memory(),
+                "b": torch.empty(max(n_bbh, 1), dtype=torch.int32).pin_memory(),
+                "row_ptr": torch.empty(ds.n_genes + 1, dtype=torch.int64).pin_memory(),
+                "cols": torch.empty(max(n_hits0, 1), dtype=torch.int32).pin_memory(),
+                "s": torch.empty(max(n_hits0, 1), dtype=torch.int32).pin_memory()}
         d2h = 0
+
+        def fit(name, n, dtype):
+            if n > host[name].numel():
+                host[name] = torch.empty(n, dtype=dtype).pin_memory()
+            return host[name]
 
         def step_e2e():
             nonlocal d2h
             p = pd.pd_build_profiles_alphabet(ctx, res_h, gp_h, gn_h, alpha, k)
             h = pd.pd_best_hits_all(ctx, p)
             b = pd.pd_bbh_all(ctx, p, h)
+            nh = int(pd.pd_hits_get_info(h).n_hits)
+            pd.pd_hits_copy(ctx, h, host["row_ptr"], fit("cols", nh, torch.int32), fit("s", nh, torch.int32))
             n = pd.pd_bbh_count(b)
-            oa = out_a if n <= out_a.numel() else torch.empty(n, dtype=torch.int32).pin_memory()
-            ob = out_b if n <= out_b.numel() else torch.empty(n, dtype=torch.int32).pin_memory()
-            pd.pd_bbh_copy(ctx, b, oa, ob)
-            d2h = 8 * n
+            pd.pd_bbh_copy(ctx, b, fit("a", n, torch.int32), fit("b", n, torch.int32))
+            d2h = 8 * n + 8 * (ds.n_genes + 1) + 8 * nh
 
         for _ in range(2):
             step_e2e()
@@ -679,7 +829,12 @@ def main():
         e2e_s = max_over_ranks(e2e_local, world)
         e2e = {"value": e2e_value, "unit": "gene-pairs/s",
                "h2d_bytes_per_step": int(ds.residues.nbytes + ds.gene_ptr.nbytes + ds.genome_ptr.nbytes),
-               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3}
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e2e_s * 1e3,
+               "copied_back": "Best Hit CSR (row offsets, columns, sum-min) and BBH pairs"}
+
+    served = None
+    if rank == 0 and world == 1 and not args.no_served:
+        served = served_probe(args, pd, ctx)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -710,7 +865,7 @@ def main():
             "metric": "gene-pair GJ evals/s", "value": value, "unit": "gene-pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": config_of(ds, args.workload, k, f"flushed ({L2_FLUSH_BYTES >> 20} MB write) between steps"),
+            "config": config_of(ds, args.workload, k, L2_NOTE, parallelism_of(world, "replicas")),
             "genome_pairs_per_s": genome_pairs_all / (ms_per_step / 1e3),
             "step_ms": step_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -720,6 +875,7 @@ def main():
                          "kernel": "summin_bh",
                          "kernel_ms": k_avg_ms, "alg_bytes": alg_bytes, "peak_source": peak_src},
             "e2e": e2e,
+            "served": served,
             "phases": phases,
             "encoder_roofline": encoder,
             "l1tex_roofline": l1tex,

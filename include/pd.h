@@ -51,10 +51,10 @@ typedef enum {
   PD_ERR_GENE_TOO_LONG = 3,  /* a gene has more than PD_MAX_WINDOWS k-mer windows */
   PD_ERR_K_RANGE = 4,        /* k outside [1, PD_MAX_K] */
   PD_ERR_OOM = 5,            /* the allocator returned NULL */
-  PD_ERR_BUDGET = 6,         /* reserved: request over a memory budget */
+  PD_ERR_BUDGET = 6,         /* over a stated memory budget or fixed limit (served index, segmented build, no-alloc call) */
   PD_ERR_CUDA = 7,           /* a CUDA runtime call or kernel launch failed */
-  PD_ERR_TIMEOUT = 8,        /* reserved: a bounded device wait expired */
-  PD_ERR_BUSY = 9,           /* reserved: no free slot */
+  PD_ERR_TIMEOUT = 8,        /* a bounded wait expired (pd_index_poll) */
+  PD_ERR_BUSY = 9,           /* no free slot (the served index would exceed PD_MAX_GENOMES) */
   PD_ERR_INTERNAL = 10       /* an internal invariant failed (a bug) */
 } pd_status;
 
@@ -170,9 +170,14 @@ typedef struct {
   uint32_t count_bits;  /* bits of the count field in a packed posting */
   uint64_t device_bytes;/* device memory held by the handle */
   int alphabet;         /* 20 or 4 */
+  uint64_t n_join;      /* postings the all-against-all Best Hit walk visits: the sum over MV entries of
+                           their k-mer's posting-list length (the sum over k-mers of length squared) */
 } pd_profiles_info;
 
 pd_status pd_profiles_get_info(const pd_profiles* prof, pd_profiles_info* info);
+/* The genome offsets the profiles were built with: n_genomes+1 int32 into a
+ * HOST buffer (genome i holds genes genome_ptr[i] .. genome_ptr[i+1]-1). */
+pd_status pd_profiles_genome_ptr(const pd_profiles* prof, int32_t* genome_ptr);
 
 /* Copy the multiplicity vector of every gene (test and inspection hook).
  *   mv_ptr  n_genes+1 int64 (CSR offsets), codes n_entries uint64 (base-20
@@ -200,6 +205,33 @@ void pd_profiles_free(pd_profiles* prof);
  * than a's own, the global ids of BH(a, G_j) (Eq. (8)); rows are grouped by
  * target genome because global ids are contiguous per genome, and ascending. */
 pd_status pd_best_hits_all(pd_ctx* ctx, const pd_profiles* prof, pd_hits** out);
+
+/* One shard of pd_best_hits_all, for splitting one dataset's all-against-all
+ * work across processes or GPUs that each hold the same profiles.  The paper
+ * decomposes phase (b) by data, one query gene (a row of Algorithm 2) being
+ * one unit of work ("Parallel implementation"); here shard `shard` of
+ * `n_shards` takes the query genes g with g mod n_shards == shard (genes of
+ * every genome and length, so shards get similar work, and the same shards
+ * whichever process built the profiles).  The result has a row
+ * for every gene (as pd_best_hits_all); rows of genes outside the shard are
+ * empty.  The union over shard = 0 .. n_shards-1 of the rows equals
+ * pd_best_hits_all exactly.  Errors: PD_ERR_ARG (n_shards 0, shard >=
+ * n_shards), PD_ERR_OOM, PD_ERR_CUDA. */
+pd_status pd_best_hits_shard(pd_ctx* ctx, const pd_profiles* prof, uint32_t shard, uint32_t n_shards,
+                             pd_hits** out);
+
+/* A Best Hit result assembled from pieces -- typically the shards of
+ * pd_best_hits_shard gathered from other processes or GPUs -- as one handle
+ * that pd_bbh_all and pd_hits_copy accept.  Piece p is a CSR over every gene:
+ * row_ptr[p] n_genes+1 int64 from 0 to n_hits[p]; cols[p] n_hits[p] int32
+ * global gene ids, strictly ascending inside a row and outside the row's own
+ * genome; s[p] n_hits[p] uint32 sum-min.  A gene's row may be non-empty in at
+ * most one piece (the merged row is that one).  Host or device pointers,
+ * copied before return.  Errors: PD_ERR_ARG (a malformed piece, or a row in
+ * two pieces), PD_ERR_OOM, PD_ERR_CUDA. */
+pd_status pd_hits_import(pd_ctx* ctx, const pd_profiles* prof, uint32_t n_pieces, const int64_t* const* row_ptr,
+                         const int32_t* const* cols, const uint32_t* const* s, const uint64_t* n_hits,
+                         pd_hits** out);
 
 /* Best Hits BH(a, G_gj) of every gene a of genome gi (Algorithm 2 for one
  * genome pair).  Rows are the genes of G_gi (local), columns local to G_gj.
@@ -438,6 +470,13 @@ pd_status pd_index_submit(pd_index* index, const uint8_t* residues, uint64_t n_r
  * it is not ready.  Each answer is returned once. */
 pd_status pd_index_poll(pd_index* index, uint64_t ticket, int wait_ms, pd_reply** out);
 pd_status pd_index_get_info(pd_index* index, pd_index_info* info);
+/* Admission control (no counterpart in the paper, which has no request
+ * loop).  hold != 0: the worker admits no further request -- a tick already
+ * running finishes, submissions still queue; hold == 0: admission resumes,
+ * and every request queued meanwhile is admitted under the budget rule above
+ * (so a burst submitted while held shares its launches).  Errors: PD_ERR_ARG
+ * (null index). */
+pd_status pd_index_hold(pd_index* index, int hold);
 /* genome_ptr of the first n_genomes resident genomes (n_genomes+1 int32, host). */
 pd_status pd_index_genome_ptr(pd_index* index, uint32_t n_genomes, int32_t* genome_ptr);
 /* Stops the worker (after its current tick) and frees the index; requests
@@ -478,7 +517,10 @@ void pd_reply_free(pd_reply* reply);
  * (else PD_ERR_ARG), at most PD_NOALLOC_MAX_HITS entries (else PD_ERR_BUDGET),
  * and capacity >= the entry count (else PD_ERR_ARG, *n_hits set).
  * The first call on a device looks up the array's device address (set-up,
- * once per device); make that first call before any stream capture.  All
+ * once per device) and keeps it for the life of the device's primary context
+ * (after cudaDeviceReset the library must be reloaded); make that first call
+ * before any stream capture.  row_ptr, cols and s must be device memory of
+ * ctx's device.  All
  * calls share the one array, which keeps the last call's contents: calls that
  * overlap on the GPU (other streams, other host threads, other contexts) race
  * and must be serialized by the caller.  The call synchronizes ctx's stream. */

@@ -35,7 +35,9 @@ void* g_scratch_addr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array on `device` (which must be current).
 // In host code the array's name only stands in for the symbol, so the address
-// is looked up once per device and cached.
+// is looked up once per device and cached.  The cached address belongs to the
+// device's primary context: it stays valid until that context is destroyed
+// (cudaDeviceReset), after which the library must be loaded again.
 cudaError_t scratch_address(int device, unsigned char** out) {
   if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
   std::lock_guard<std::mutex> lock(g_setup_mu);
@@ -63,14 +65,16 @@ struct Carve {
   }
 };
 
-bool is_device_ptr(const void* p) {
+// True if p is device (or managed) memory that kernels on `device` address.
+bool is_device_ptr(const void* p, int device) {
   if (!p) return false;
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
     return false;
   }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+  if (a.type == cudaMemoryTypeManaged) return true;
+  return a.type == cudaMemoryTypeDevice && a.device == device;
 }
 
 }  // namespace
@@ -95,8 +99,10 @@ pd_status noalloc_impl(pd_ctx* ctx, const pd_profiles* prof, uint32_t gi, uint32
   if (ta1 - ta0 > PD_NOALLOC_MAX_TARGETS)
     return ctx_fail(ctx, PD_ERR_ARG,
                     "pd_best_hits_noalloc: target genome has more than PD_NOALLOC_MAX_TARGETS genes");
-  if (!is_device_ptr(row_ptr) || (capacity > 0 && (!is_device_ptr(cols) || !is_device_ptr(s))))
-    return ctx_fail(ctx, PD_ERR_ARG, "pd_best_hits_noalloc: row_ptr, cols and s must be device pointers");
+  if (!is_device_ptr(row_ptr, cv.device) ||
+      (capacity > 0 && (!is_device_ptr(cols, cv.device) || !is_device_ptr(s, cv.device))))
+    return ctx_fail(ctx, PD_ERR_ARG,
+                    "pd_best_hits_noalloc: row_ptr, cols and s must be device memory of the context's device");
   cudaError_t e = cudaSetDevice(cv.device);
   unsigned char* scratch = nullptr;
   if (e == cudaSuccess) e = scratch_address(cv.device, &scratch);

@@ -285,14 +285,18 @@ __global__ void __launch_bounds__(kMvLongThreads)
 }
 
 // Every multiplicity-vector entry gets its posting range [mv_post, +mv_plen);
-// the longest list length goes to *max_posting.
+// the longest list length goes to *max_posting and, if join is not null, the
+// sum of the entries' list lengths -- the postings an all-against-all walk
+// visits -- is added to *join.
 __global__ void __launch_bounds__(256)
     k_mv_post(const uint32_t* __restrict__ win_off, const uint32_t* __restrict__ mv_n,
               const uint32_t* __restrict__ mv_id, uint32_t n_genes, const uint32_t* __restrict__ post_ptr,
-              uint32_t* __restrict__ mv_post, uint32_t* __restrict__ mv_plen, uint32_t* __restrict__ max_posting) {
+              uint32_t* __restrict__ mv_post, uint32_t* __restrict__ mv_plen, uint32_t* __restrict__ max_posting,
+              unsigned long long* __restrict__ join) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   uint32_t m = 0;
+  unsigned long long jsum = 0;
   for (uint32_t g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < n_genes; g += warps) {
     const uint32_t off = win_off[g], n = mv_n[g];
     // four entries per lane in flight: their ids, then their list bounds
@@ -314,13 +318,18 @@ __global__ void __launch_bounds__(256)
           mv_post[off + e0 + 32 * j] = lo[j];
           mv_plen[off + e0 + 32 * j] = hi[j] - lo[j];
           m = max(m, hi[j] - lo[j]);
+          jsum += hi[j] - lo[j];
         }
       }
     }
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  for (int o = 16; o > 0; o >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    jsum += __shfl_xor_sync(0xffffffffu, jsum, o);
+  }
   if (lane == 0 && m) atomicMax(max_posting, m);
+  if (lane == 0 && join && jsum) atomicAdd(join, jsum);
 }
 
 // ------------------------------------------------------------ query order
@@ -502,10 +511,10 @@ uint32_t mv_build_table_cap(uint32_t La) { return mv_table_cap(La); }
 
 cudaError_t run_mv_post(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
                         uint32_t n_genes, const uint32_t* post_ptr, uint32_t* mv_post, uint32_t* mv_plen,
-                        uint32_t* max_posting, cudaStream_t s) {
+                        uint32_t* max_posting, unsigned long long* join, cudaStream_t s) {
   PD_LAUNCH(L, "mv_post",
             k_mv_post<<<grid_for((uint64_t)n_genes * 32, 256, 152u * 16u), 256, 0, s>>>(
-                win_off, mv_n, mv_id, n_genes, post_ptr, mv_post, mv_plen, max_posting));
+                win_off, mv_n, mv_id, n_genes, post_ptr, mv_post, mv_plen, max_posting, join));
   return cudaSuccess;
 }
 

@@ -194,8 +194,19 @@ template <int kThreads>
 struct Chunk {
   static constexpr uint32_t kSize = 2 * kThreads;  // query k-mers staged per round
   static constexpr uint32_t kItems = 2;
-  static constexpr size_t kBytes = (((size_t)kSize * 4 + (size_t)(kSize + 1) * 4 + (size_t)kSize * 2) + 15) & ~(size_t)15;
+  // c_post (4 B), c_off (4 B, one more), c_cnt (2 B), c_ent (2 B) per k-mer
+  static constexpr size_t kBytes =
+      (((size_t)kSize * 4 + (size_t)(kSize + 1) * 4 + (size_t)kSize * 2 + (size_t)kSize * 2) + 15) & ~(size_t)15;
 };
+
+// Rounds of 32 postings a warp has in flight before accumulating them (the
+// warp-cooperative walk), and the average posting-list length, weighted by
+// use (a dataset's join over its vector entries), from which tier 1 takes
+// that walk rather than the merge-path walk: a warp round then reads few
+// lists, while for short lists each thread's run of postings stays within the
+// sectors it has already loaded.
+constexpr uint32_t kRounds = 4;
+constexpr uint32_t kWarpWalkMinAvg = 16;
 
 // Memory of one call: table, the list of occupied slots (filled after the
 // walk) and the hit list.
@@ -212,13 +223,14 @@ struct Table {
   uint32_t used_cap;       // at most cap; a query with more occupied slots moves to the next tier
 };
 
-template <int kThreads, bool kEmitAll, bool kPacked, bool kFilter, typename TIdx>
+template <int kThreads, bool kEmitAll, bool kPacked, bool kFilter, typename TIdx, bool kWarpWalk>
 __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P, const QuerySet& Q,
                                               const HitsOut& O, const TierIO& T, DevErr* err,
                                               const Table<TIdx>& tb, uint32_t* c_post, uint32_t* c_off,
                                               uint16_t* c_cnt, unsigned long long* best, Scalars* sh) {
   constexpr uint32_t kChunk = Chunk<kThreads>::kSize, kItems = Chunk<kThreads>::kItems;
   const Acc<kPacked, kFilter> acc{tb.keys, tb.vals, tb.vpa, tb.vpb, P.cnt_bits, 32u - (31u - (uint32_t)__clz(tb.cap))};
+  uint16_t* c_ent = c_cnt + Chunk<kThreads>::kSize;  // chunk entry of each staged k-mer
   unsigned long long* out = tb.out;
   const uint32_t mask = tb.cap - 1u;
   // ---- query gene, its output row and its targets
@@ -226,6 +238,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
   unsigned long long key_lo = 0, key_hi = 0;
   if (Q.all_pairs) {
     a = Q.order ? Q.order[qi] : Q.q0 + qi;
+    if (Q.n_shards && a % Q.n_shards != Q.shard) return;  // another shard's query (uniform over the block)
     row = a;
     if (Q.q_genome) {  // external query: no own genome among the targets
       const uint32_t x = Q.q_genome[a];
@@ -281,82 +294,171 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
   }
   __syncthreads();
   unsigned long long walked = 0;
+  const uint32_t lane = tid & 31u, warp = tid >> 5;
+  constexpr uint32_t kWarps = kThreads / 32;
   for (uint32_t c0 = 0; c0 < E && !sh->overflow; c0 += kChunk) {
-    const uint32_t n_c = min(kChunk, E - c0);
-    // ---- stage the chunk: posting ranges and their prefix sum
-    uint32_t len_loc[kItems];
-    uint32_t my_sum = 0;
+    const uint32_t n_in = min(kChunk, E - c0);
+    // Each posting (b, mult_b) adds min(mult_a, mult_b) to b's accumulator.
+    // Own-genome postings are accumulated too and dropped when the Best Hits
+    // are chosen (a few slots per query), which keeps the walks free of
+    // per-posting range tests.  `e` is the query's chunk entry of the k-mer.
+    auto accumulate = [&](uint32_t p, uint32_t ca, uint32_t e) {
+      uint32_t cb = p & cnt_mask;
+      if (cb == P.cnt_cap && ca > cb) cb = mv_count_of(P, p >> P.cnt_bits, q_mv_id[m0 + c0 + e]);
+      const uint32_t key = kPacked ? (p & ~cnt_mask) : (p >> P.cnt_bits);
+      if (!acc.add(mask, key, min(ca, cb), ca, cb)) sh->overflow = 1;
+    };
+    if constexpr (kWarpWalk) {
+      // ---- stage the chunk: posting ranges and their prefix sum.  Empty
+      // ranges (the restricted forms narrow lists to a target genome) are
+      // dropped, so the staged list starts strictly increase, as the walk's
+      // k-mer lookup needs.
+      uint32_t lo_loc[kItems], len_loc[kItems];
+      uint32_t my_sum = 0, my_n = 0;
 #pragma unroll
-    for (uint32_t r = 0; r < kItems; ++r) {
-      const uint32_t e = tid * kItems + r;
-      uint32_t len = 0;
-      if (e < n_c) {
-        uint32_t lo = q_mv_post[m0 + c0 + e];
-        uint32_t hi = lo + q_mv_plen[m0 + c0 + e];
-        if (!Q.all_pairs) {
-          lo = lower_bound_post(P.post, lo, hi, key_lo);
-          hi = lower_bound_post(P.post, lo, hi, key_hi);
+      for (uint32_t r = 0; r < kItems; ++r) {
+        const uint32_t e = tid * kItems + r;
+        uint32_t lo = 0, len = 0;
+        if (e < n_in) {
+          lo = q_mv_post[m0 + c0 + e];
+          uint32_t hi = lo + q_mv_plen[m0 + c0 + e];
+          if (!Q.all_pairs) {
+            lo = lower_bound_post(P.post, lo, hi, key_lo);
+            hi = lower_bound_post(P.post, lo, hi, key_hi);
+          }
+          len = hi - lo;
         }
-        c_post[e] = lo;
-        c_cnt[e] = q_mv_cnt[m0 + c0 + e];
-        len = hi - lo;
+        lo_loc[r] = lo;
+        len_loc[r] = len;
+        my_sum += len;
+        my_n += len ? 1u : 0u;
       }
-      len_loc[r] = len;
-      my_sum += len;
-    }
-    uint32_t J_c;
-    uint32_t run = block_exclusive_scan(my_sum, sh->warp_tmp, &J_c);
+      uint32_t J_c, n_c;
+      uint32_t run = block_exclusive_scan(my_sum, sh->warp_tmp, &J_c);
+      uint32_t slot = block_exclusive_scan(my_n, sh->warp_tmp, &n_c);
 #pragma unroll
-    for (uint32_t r = 0; r < kItems; ++r) {
-      const uint32_t e = tid * kItems + r;
-      if (e < n_c) c_off[e] = run;
-      run += len_loc[r];
-    }
-    if (tid == 0) c_off[n_c] = J_c;
-    __syncthreads();
-    walked += J_c;
-    // ---- merge-path walk of the chunk's postings
-    const uint32_t per = (J_c + kThreads - 1) / kThreads;
-    uint32_t x = min(J_c, tid * per);
-    const uint32_t x_end = min(J_c, x + per);
-    if (x < x_end) {
-      uint32_t lo = 0, hi = n_c;
-      while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (c_off[mid] <= x) lo = mid; else hi = mid;
+      for (uint32_t r = 0; r < kItems; ++r) {
+        const uint32_t e = tid * kItems + r;
+        if (len_loc[r]) {
+          c_post[slot] = lo_loc[r];
+          c_cnt[slot] = q_mv_cnt[m0 + c0 + e];
+          c_ent[slot] = (uint16_t)e;
+          c_off[slot] = run;
+          ++slot;
+        }
+        run += len_loc[r];
       }
-      uint32_t e = lo, e_end = c_off[lo + 1], base = c_post[lo] - c_off[lo], ca = c_cnt[lo];
-      while (x < x_end) {
-        uint32_t pv[4], cav[4], ev[4];
-        uint32_t nb = 0;
+      if (tid == 0) c_off[n_c] = J_c;
+      __syncthreads();
+      walked += J_c;
+      // ---- warp-cooperative walk.  Warp w takes the flat postings [x0, x1)
+      // and reads them 32 consecutive positions per round, lane l position
+      // xr + l, so a round reads one or a few lists contiguously.  The k-mer
+      // of each lane's position comes from the starts of the next 32 staged
+      // k-mers (one per lane): bit d of `starts` marks a k-mer starting d
+      // positions after the round's first, and a lane's k-mer is the round's
+      // first k-mer plus the number of starts at or before it.
+      const uint32_t per_w = ((J_c + kWarps - 1) / kWarps + 31u) & ~31u;
+      const uint32_t x0 = min(J_c, warp * per_w), x1 = min(J_c, x0 + per_w);
+      if (x0 < x1) {
+        uint32_t e_lo = 0, hi = n_c;  // the k-mer holding x0: last e with c_off[e] <= x0
+        while (hi - e_lo > 1) {
+          const uint32_t mid = (e_lo + hi) >> 1;
+          if (c_off[mid] <= x0) e_lo = mid; else hi = mid;
+        }
+        for (uint32_t xb = x0; xb < x1; xb += 32u * kRounds) {
+          uint32_t pv[kRounds], cav[kRounds], ev[kRounds];
 #pragma unroll
-        for (uint32_t j = 0; j < 4; ++j) {
-          if (x < x_end) {
-            while (x >= e_end) {
-              ++e;
-              e_end = c_off[e + 1];
-              base = c_post[e] - c_off[e];
-              ca = c_cnt[e];
+          for (uint32_t u = 0; u < kRounds; ++u) {
+            const uint32_t xr = xb + 32u * u, x = xr + lane;
+            const uint32_t j = e_lo + 1u + lane;
+            const uint32_t d = (j <= n_c && xr < x1) ? c_off[j] - xr : 0xFFFFFFFFu;
+            const uint32_t starts = __reduce_or_sync(0xFFFFFFFFu, d < 32u ? (1u << d) : 0u);
+            const uint32_t e = e_lo + __popc(starts & (0xFFFFFFFFu >> (31u - lane)));
+            e_lo += __popc(starts) + (__ballot_sync(0xFFFFFFFFu, d == 32u) ? 1u : 0u);
+            pv[u] = kEmpty;
+            cav[u] = 0;
+            ev[u] = 0;
+            if (x < x1) {
+              pv[u] = P.post[c_post[e] + (x - c_off[e])];
+              cav[u] = c_cnt[e];
+              ev[u] = c_ent[e];
             }
-            pv[j] = P.post[base + x];
-            cav[j] = ca;
-            ev[j] = e;
-            ++x;
-            nb = j + 1;
           }
-        }
-        // Own-genome postings are accumulated too and dropped when the
-        // Best Hits are chosen (a few slots per query), which keeps this loop
-        // free of per-posting range tests.
 #pragma unroll
-        for (uint32_t j = 0; j < 4; ++j) {
-          if (j < nb) {
-            const uint32_t p = pv[j];
-            uint32_t cb = p & cnt_mask;
-            if (cb == P.cnt_cap && cav[j] > cb) cb = mv_count_of(P, p >> P.cnt_bits, q_mv_id[m0 + c0 + ev[j]]);
-            const uint32_t key = kPacked ? (p & ~cnt_mask) : (p >> P.cnt_bits);
-            if (!acc.add(mask, key, min(cav[j], cb), cav[j], cb)) sh->overflow = 1;
+          for (uint32_t u = 0; u < kRounds; ++u)
+            if (xb + 32u * u + lane < x1) accumulate(pv[u], cav[u], ev[u]);
+        }
+      }
+    } else {
+      // ---- stage the chunk: posting ranges and their prefix sum
+      uint32_t len_loc[kItems];
+      uint32_t my_sum = 0;
+#pragma unroll
+      for (uint32_t r = 0; r < kItems; ++r) {
+        const uint32_t e = tid * kItems + r;
+        uint32_t len = 0;
+        if (e < n_in) {
+          uint32_t lo = q_mv_post[m0 + c0 + e];
+          uint32_t hi = lo + q_mv_plen[m0 + c0 + e];
+          if (!Q.all_pairs) {
+            lo = lower_bound_post(P.post, lo, hi, key_lo);
+            hi = lower_bound_post(P.post, lo, hi, key_hi);
           }
+          c_post[e] = lo;
+          c_cnt[e] = q_mv_cnt[m0 + c0 + e];
+          len = hi - lo;
+        }
+        len_loc[r] = len;
+        my_sum += len;
+      }
+      uint32_t J_c;
+      uint32_t run = block_exclusive_scan(my_sum, sh->warp_tmp, &J_c);
+#pragma unroll
+      for (uint32_t r = 0; r < kItems; ++r) {
+        const uint32_t e = tid * kItems + r;
+        if (e < n_in) c_off[e] = run;
+        run += len_loc[r];
+      }
+      if (tid == 0) c_off[n_in] = J_c;
+      __syncthreads();
+      walked += J_c;
+      // ---- merge-path walk: thread t takes the flat range [t*per,
+      // (t+1)*per), finds its first k-mer by one binary search and then
+      // advances sequentially, loading four postings before using any (a
+      // thread's next postings mostly share the sector of its last one).
+      const uint32_t per = (J_c + kThreads - 1) / kThreads;
+      uint32_t x = min(J_c, tid * per);
+      const uint32_t x_end = min(J_c, x + per);
+      if (x < x_end) {
+        uint32_t lo = 0, hi = n_in;
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (c_off[mid] <= x) lo = mid; else hi = mid;
+        }
+        uint32_t e = lo, e_end = c_off[lo + 1], base = c_post[lo] - c_off[lo], ca = c_cnt[lo];
+        while (x < x_end) {
+          uint32_t pv[4], cav[4], ev[4];
+          uint32_t nb = 0;
+#pragma unroll
+          for (uint32_t j = 0; j < 4; ++j) {
+            if (x < x_end) {
+              while (x >= e_end) {
+                ++e;
+                e_end = c_off[e + 1];
+                base = c_post[e] - c_off[e];
+                ca = c_cnt[e];
+              }
+              pv[j] = P.post[base + x];
+              cav[j] = ca;
+              ev[j] = e;
+              ++x;
+              nb = j + 1;
+            }
+          }
+#pragma unroll
+          for (uint32_t j = 0; j < 4; ++j)
+            if (j < nb) accumulate(pv[j], cav[j], ev[j]);
         }
       }
     }
@@ -479,7 +581,7 @@ struct SmemTier {
 };
 
 template <int kThreads, int kMinBlocks, uint32_t kCap, uint32_t kOutCap, bool kPacked, bool kEmitAll,
-          bool kFilter = false, uint32_t kUsedCap = kCap>
+          bool kFilter = false, uint32_t kUsedCap = kCap, bool kWarpWalk = false>
 __global__ void __launch_bounds__(kThreads, kMinBlocks) k_summin_smem(ProfilesView P, QuerySet Q, HitsOut O,
                                                                       TierIO T, DevErr* err) {
   using S = SmemTier<kThreads, kCap, kOutCap, kPacked, kFilter, kUsedCap>;
@@ -511,7 +613,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) k_summin_smem(ProfilesVi
   __syncthreads();
   const uint32_t n = T.in_list ? *T.in_count : Q.n_queries;
   for (uint32_t x = blockIdx.x; x < n; x += gridDim.x)
-    process_query<kThreads, kEmitAll, kPacked, kFilter, uint16_t>(T.in_list ? T.in_list[x] : x, P, Q, O, T, err, tb, c_post,
+    process_query<kThreads, kEmitAll, kPacked, kFilter, uint16_t, kWarpWalk>(T.in_list ? T.in_list[x] : x, P, Q, O, T, err, tb, c_post,
                                                          c_off, c_cnt, best, &sh);
 }
 
@@ -547,7 +649,7 @@ __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet 
   __syncthreads();
   const uint32_t n = *T.in_count;
   for (uint32_t x = blockIdx.x; x < n; x += gridDim.x)
-    process_query<kThreads, kEmitAll, false, kFilter, uint32_t>(T.in_list[x], P, Q, O, T, err, tb, c_post, c_off, c_cnt, best,
+    process_query<kThreads, kEmitAll, false, kFilter, uint32_t, false>(T.in_list[x], P, Q, O, T, err, tb, c_post, c_off, c_cnt, best,
                                                        &sh);
 }
 
@@ -622,12 +724,19 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
   if (emit_all)
     e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutEmit, true, true, false, kT1Used>, L, "summin_pairs",
                     kT1Threads, T1E::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
-  else
+  else if (P.n_join < (uint64_t)kWarpWalkMinAvg * P.n_entries)  // short lists: merge-path walk
     e = n_best <= kT1CompactGenomes
             ? launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false, false, kT1Used>, L,
                           "summin_bh", kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s)
             : launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutFull, true, false, false, kT1UsedFull>,
                           L, "summin_bh", kT1Threads, T1F::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
+  else  // long lists: warp-cooperative walk
+    e = n_best <= kT1CompactGenomes
+            ? launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false, false, kT1Used, true>,
+                          L, "summin_bh", kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s)
+            : launch_smem(
+                  k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutFull, true, false, false, kT1UsedFull, true>, L,
+                  "summin_bh", kT1Threads, T1F::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   if (e != cudaSuccess) return e;
   // tier 2: one 1024-thread block per SM over the deferred queries (exits at once if none)
   if (emit_all)

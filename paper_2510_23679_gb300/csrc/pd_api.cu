@@ -254,6 +254,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
                                      uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
                                      const uint32_t* genome_seg, pd_profiles** out, const int64_t* gene_src,
                                      int alphabet, int length_buckets) {
+  PhaseRange range_("pd: profiles");
   if (alphabet != PD_ALPHABET_AMINO && alphabet != PD_ALPHABET_NUCLEOTIDE)
     return fail(c, PD_ERR_ARG, "alphabet must be 20 (amino acids) or 4 (nucleotides)");
   const int max_k = alphabet == PD_ALPHABET_AMINO ? PD_MAX_K : PD_MAX_K_NUCLEOTIDE;
@@ -450,7 +451,8 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   if (n_genes && D)
     CK(pdg::run_mv_post(L, P->win_off.as<uint32_t>(), P->mv_n.as<uint32_t>(), P->mv_id.as<uint32_t>(), n_genes,
                         P->post_ptr.as<uint32_t>(), P->mv_post.as<uint32_t>(), P->mv_plen.as<uint32_t>(),
-                        d_counts.as<uint32_t>() + 1, c->stream));
+                        d_counts.as<uint32_t>() + 1, (unsigned long long*)(d_counts.as<uint32_t>() + 2),
+                        c->stream));
 
   // ---- all-pairs query order: min-hash buckets
   Buf ocount;
@@ -468,6 +470,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   if (st != PD_OK) return st;
   const uint64_t E = hb32[0];
   const uint32_t max_posting = hb32[3];
+  const uint64_t n_join = ((const unsigned long long*)c->h_build)[2];  // d_counts words 2-3
 
   pdg::ProfilesView& v = P->view;
   v.k = k;
@@ -479,6 +482,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   v.cnt_bits = cnt_bits;
   v.cnt_cap = cnt_cap;
   v.max_posting = max_posting;
+  v.n_join = n_join;
   v.win_off = P->win_off.as<uint32_t>();
   v.mv_n = P->mv_n.as<uint32_t>();
   v.mv_id = P->mv_id.as<uint32_t>();
@@ -503,6 +507,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   in.n_distinct = D;
   in.n_entries = E;
   in.max_posting = max_posting;
+  in.n_join = n_join;
   in.count_bits = cnt_bits;
   in.alphabet = alphabet;
   in.device_bytes = P->genome_ptr.n + P->La.n + P->win_off.n + P->mv_n.n + P->mv_id.n + P->mv_cnt.n +
@@ -561,6 +566,12 @@ PD_API pd_status pd_build_profiles_segmented(pd_ctx* c, const uint8_t* residues,
 PD_API pd_status pd_profiles_get_info(const pd_profiles* P, pd_profiles_info* info) {
   if (!P || !info) return PD_ERR_ARG;
   *info = P->info;
+  return PD_OK;
+}
+
+PD_API pd_status pd_profiles_genome_ptr(const pd_profiles* P, int32_t* genome_ptr) {
+  if (!P || !genome_ptr) return PD_ERR_ARG;
+  for (uint32_t g = 0; g <= P->info.n_genomes; ++g) genome_ptr[g] = pdg::profiles_genome_start(P, g);
   return PD_OK;
 }
 
@@ -843,7 +854,7 @@ pd_status pdh::query_profiles_impl(pd_ctx* c, const pd_profiles* P, const uint8_
                          d_long_off.as<unsigned long long>(), c->stream));
     CK(pdg::run_mv_post(L, Qp->win_off.as<uint32_t>(), Qp->mv_n.as<uint32_t>(), Qp->mv_id.as<uint32_t>(), n_genes,
                         v.post_ptr, Qp->mv_post.as<uint32_t>(), Qp->mv_plen.as<uint32_t>(), dummy.as<uint32_t>(),
-                        c->stream));
+                        nullptr, c->stream));
   }
   return check_dev_err(c);  // synchronizes: the host offsets and temporaries end here
 }
@@ -874,6 +885,7 @@ static pd_status hits_pair_impl(pd_ctx* c, const pd_profiles* P, uint32_t gi, ui
 }
 
 PD_API pd_status pd_best_hits_all(pd_ctx* c, const pd_profiles* P, pd_hits** out) {
+  PhaseRange range_("pd: best hits");
   if (!c || !P || !out) return PD_ERR_ARG;
   *out = nullptr;
   try {
@@ -897,7 +909,150 @@ PD_API pd_status pd_best_hits_all(pd_ctx* c, const pd_profiles* P, pd_hits** out
   }
 }
 
+PD_API pd_status pd_best_hits_shard(pd_ctx* c, const pd_profiles* P, uint32_t shard, uint32_t n_shards,
+                                    pd_hits** out) {
+  PhaseRange range_("pd: best hits (shard)");
+  if (!c || !P || !out) return PD_ERR_ARG;
+  *out = nullptr;
+  if (n_shards == 0 || shard >= n_shards) return fail(c, PD_ERR_ARG, "shard must be < n_shards");
+  try {
+    CK(cudaSetDevice(c->device));
+    std::unique_ptr<pd_hits> H(new pd_hits());
+    H->ctx = c;
+    H->all_pairs = 1;
+    pdg::QuerySet Q{};
+    Q.all_pairs = 1;
+    Q.order = P->view.order;
+    Q.q0 = 0;
+    const uint32_t G = P->view.n_genes;
+    Q.n_queries = G;  // every order position; the kernel skips other shards' genes
+    Q.n_shards = n_shards;
+    Q.shard = shard;
+    pd_status st = run_hits(c, P, Q, false, H.get());
+    if (st != PD_OK) return st;
+    *out = H.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_best_hits_shard");
+  }
+}
+
+namespace {
+// Rows of imported CSR pieces: for every gene the piece whose row is
+// non-empty (at most one), its offset in the concatenated hit buffer and its
+// length; and the checks: offsets non-decreasing from 0 to each piece's
+// count, columns inside the dataset, outside the row's own genome and
+// strictly ascending inside a row (the mutual check of BBH searches rows).
+__global__ void k_import_rows(const unsigned long long* __restrict__ row_ptr, uint32_t n_pieces, uint32_t n_rows,
+                              const unsigned long long* __restrict__ piece_n,
+                              const unsigned long long* __restrict__ piece_base, const uint32_t* __restrict__ cols,
+                              const uint16_t* __restrict__ gene_genome, unsigned long long* __restrict__ row_off,
+                              uint32_t* __restrict__ row_len, pdg::DevErr* err) {
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < n_rows; r += gridDim.x * blockDim.x) {
+    unsigned long long off = 0;
+    uint32_t len = 0, owners = 0;
+    for (uint32_t p = 0; p < n_pieces; ++p) {
+      const unsigned long long* rp = row_ptr + (size_t)p * (n_rows + 1);
+      const unsigned long long b = rp[r], e = rp[r + 1];
+      if (b > e || e > piece_n[p] || (r == 0 && b != 0) || (r == n_rows - 1 && e != piece_n[p])) {
+        pdg::raise_error(err, PD_ERR_ARG, r);
+        owners = 2;
+        break;
+      }
+      if (e > b) {
+        ++owners;
+        off = piece_base[p] + b;
+        len = (uint32_t)(e - b);
+      }
+    }
+    if (owners > 1) {
+      pdg::raise_error(err, PD_ERR_ARG, r);  // a row in two pieces
+      len = 0;
+    }
+    row_off[r] = off;
+    row_len[r] = len;
+    uint32_t prev = 0;
+    for (uint32_t x = 0; x < len; ++x) {
+      const uint32_t col = cols[off + x];
+      if (col >= n_rows || gene_genome[col] == gene_genome[r] || (x > 0 && col <= prev)) {
+        pdg::raise_error(err, PD_ERR_ARG, r);
+        break;
+      }
+      prev = col;
+    }
+  }
+}
+}  // namespace
+
+PD_API pd_status pd_hits_import(pd_ctx* c, const pd_profiles* P, uint32_t n_pieces, const int64_t* const* row_ptr,
+                                const int32_t* const* cols, const uint32_t* const* s, const uint64_t* n_hits,
+                                pd_hits** out) {
+  if (!c || !P || !out || n_pieces == 0 || !row_ptr || !cols || !s || !n_hits) return PD_ERR_ARG;
+  *out = nullptr;
+  try {
+    CK(cudaSetDevice(c->device));
+    const uint32_t G = P->view.n_genes;
+    std::vector<unsigned long long> base(n_pieces), cnt(n_pieces);
+    unsigned long long total = 0;
+    for (uint32_t p = 0; p < n_pieces; ++p) {
+      if (!row_ptr[p] || (n_hits[p] && (!cols[p] || !s[p]))) return fail(c, PD_ERR_ARG, "null piece pointer");
+      base[p] = total;
+      cnt[p] = n_hits[p];
+      total += n_hits[p];
+    }
+    std::unique_ptr<pd_hits> H(new pd_hits());
+    H->ctx = c;
+    H->all_pairs = 1;
+    H->n_rows = G;
+    H->n_hits = total;
+    Buf d_rp, d_meta;
+    ALLOC(d_rp, sizeof(int64_t) * (size_t)(G + 1) * n_pieces);
+    ALLOC(d_meta, sizeof(unsigned long long) * 2 * n_pieces);
+    ALLOC(H->row_off, sizeof(unsigned long long) * std::max<uint32_t>(G, 1));
+    ALLOC(H->row_len, sizeof(uint32_t) * std::max<uint32_t>(G, 1));
+    ALLOC(H->out_b, sizeof(uint32_t) * std::max<unsigned long long>(total, 1));
+    ALLOC(H->out_s, sizeof(uint32_t) * std::max<unsigned long long>(total, 1));
+    std::vector<unsigned long long> meta(cnt);
+    meta.insert(meta.end(), base.begin(), base.end());
+    CK(cudaMemcpyAsync(d_meta.p, meta.data(), sizeof(unsigned long long) * 2 * n_pieces, cudaMemcpyHostToDevice,
+                       c->stream));
+    for (uint32_t p = 0; p < n_pieces; ++p) {
+      CK(cudaMemcpyAsync(d_rp.as<int64_t>() + (size_t)p * (G + 1), row_ptr[p], sizeof(int64_t) * (G + 1),
+                         cudaMemcpyDefault, c->stream));
+      if (n_hits[p]) {
+        CK(cudaMemcpyAsync(H->out_b.as<uint32_t>() + base[p], cols[p], sizeof(int32_t) * n_hits[p],
+                           cudaMemcpyDefault, c->stream));
+        CK(cudaMemcpyAsync(H->out_s.as<uint32_t>() + base[p], s[p], sizeof(uint32_t) * n_hits[p],
+                           cudaMemcpyDefault, c->stream));
+      }
+    }
+    if (G) {
+      const unsigned grid = (unsigned)std::min<uint64_t>((G + 255) / 256, 152u * 8u);
+      CK(pdg::launch_begin(&c->L, "import_rows"));
+      k_import_rows<<<grid, 256, 0, c->stream>>>(d_rp.as<unsigned long long>(), n_pieces, G,
+                                                 d_meta.as<unsigned long long>(),
+                                                 d_meta.as<unsigned long long>() + n_pieces, H->out_b.as<uint32_t>(),
+                                                 P->view.gene_genome, H->row_off.as<unsigned long long>(),
+                                                 H->row_len.as<uint32_t>(), c->d_err);
+      CK(pdg::launch_end(&c->L, "import_rows"));
+    }
+    pd_status st = check_dev_err(c);  // synchronizes: the staging buffers end here
+    if (st != PD_OK)
+      return fail(c, st, "pd_hits_import: malformed pieces (offsets, a row in two pieces, columns out of range, "
+                         "in the row's own genome, or not ascending)");
+    *out = H.release();
+    return PD_OK;
+  } catch (const std::bad_alloc&) {
+    return fail(c, PD_ERR_OOM, "host allocation failed");
+  } catch (...) {
+    return fail(c, PD_ERR_INTERNAL, "exception in pd_hits_import");
+  }
+}
+
 PD_API pd_status pd_best_hits(pd_ctx* c, const pd_profiles* P, uint32_t gi, uint32_t gj, pd_hits** out) {
+  PhaseRange range_("pd: best hits (pair)");
   if (!c || !P || !out) return PD_ERR_ARG;
   *out = nullptr;
   try {
@@ -996,6 +1151,7 @@ pd_status pdh::bbh_impl(pd_ctx* c, const pdg::BbhRows& R, uint64_t n_hit_slots, 
 }
 
 PD_API pd_status pd_bbh_all(pd_ctx* c, const pd_profiles* P, const pd_hits* H, pd_bbh_set** out) {
+  PhaseRange range_("pd: bbh");
   if (!c || !P || !H || !out) return PD_ERR_ARG;
   *out = nullptr;
   if (!H->all_pairs || H->paralog) return fail(c, PD_ERR_ARG, "pd_bbh_all needs the result of pd_best_hits_all");
@@ -1144,6 +1300,7 @@ PD_API pd_status pd_paralog_bbh(pd_ctx* c, const pd_profiles* P, const pd_hits* 
 }
 
 PD_API pd_status pd_bbh(pd_ctx* c, const pd_profiles* P, uint32_t gi, uint32_t gj, pd_bbh_set** out) {
+  PhaseRange range_("pd: bbh (pair)");
   if (!c || !P || !out) return PD_ERR_ARG;
   *out = nullptr;
   try {

@@ -542,6 +542,7 @@ pd_status pairs_impl(pd_ctx* c, const pd_profiles* P, const uint32_t* jobs, uint
 
 PD_API pd_status pd_bbh_pairs(pd_ctx* c, const pd_profiles* P, const uint32_t* jobs, uint32_t n_jobs,
                               pd_batch** out) {
+  PhaseRange range_("pd: bbh of listed pairs");
   if (!c || !P || !out) return PD_ERR_ARG;
   *out = nullptr;
   try {
@@ -556,6 +557,7 @@ PD_API pd_status pd_bbh_pairs(pd_ctx* c, const pd_profiles* P, const uint32_t* j
 PD_API pd_status pd_bbh_batch(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                               uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* jobs,
                               const int32_t* job_k, uint32_t n_jobs, const pd_batch_tuning* tuning, pd_batch** out) {
+  PhaseRange range_("pd: batch");
   if (!c || !out) return PD_ERR_ARG;
   *out = nullptr;
   try {

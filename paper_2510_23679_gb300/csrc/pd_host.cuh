@@ -12,10 +12,22 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pd.h"
 #include "pd_internal.cuh"
 
 #define PD_API extern "C" __attribute__((visibility("default")))
+
+// A named range around one phase of a call (profile build, Best Hits, BBH,
+// a served tick), visible to profilers as an NVTX range; without a profiler
+// attached it costs a pointer test.
+struct PhaseRange {
+  explicit PhaseRange(const char* name) { nvtxRangePushA(name); }
+  ~PhaseRange() { nvtxRangePop(); }
+  PhaseRange(const PhaseRange&) = delete;
+  PhaseRange& operator=(const PhaseRange&) = delete;
+};
 
 struct pd_ctx;
 

@@ -141,6 +141,7 @@ struct ProfilesView {
   uint32_t n_genes, n_genomes;
   uint64_t n_windows, n_distinct, n_entries;
   uint32_t cnt_bits, cnt_cap, max_posting;
+  uint64_t n_join;              // postings the all-against-all walk visits (sum over entries of list length)
   const uint32_t* win_off;      // [G+1] window range of each gene
   const uint32_t* mv_n;         // [G]   distinct k-mers of each gene
   const uint32_t* mv_id;        // [W]   multiplicity vectors: dense ids
@@ -181,6 +182,10 @@ struct QuerySet {
   int all_pairs;
   const uint32_t* order;
   uint32_t q0, n_queries;
+  // Sharded all-pairs form (n_shards = 0: off): only the query genes g with
+  // g mod n_shards == shard are computed (the others are skipped before any
+  // work), so the shards partition the genes whatever the query order.
+  uint32_t n_shards, shard;
   uint32_t qa0, nA, ta0, ta1;
   uint32_t qb0, tb0, tb1;
   // Served queries (all-pairs form; null = off).  tgt_end[genome of the
@@ -314,10 +319,11 @@ size_t radix_counts_words(uint64_t n);
 cudaError_t run_index_sort(Launcher* L, unsigned long long* a, unsigned long long* b, uint64_t n, uint32_t key_bits,
                            uint32_t* counts, void* scan_tmp, uint64_t n_ids, uint32_t* post, uint32_t* post_ptr,
                            cudaStream_t s);
-// Posting range of every multiplicity-vector entry; also the longest list.
+// Posting range of every multiplicity-vector entry; also the longest list and
+// (join not null) the sum of the entries' list lengths.
 cudaError_t run_mv_post(Launcher* L, const uint32_t* win_off, const uint32_t* mv_n, const uint32_t* mv_id,
                         uint32_t n_genes, const uint32_t* post_ptr, uint32_t* mv_post, uint32_t* mv_plen,
-                        uint32_t* max_posting, cudaStream_t s);
+                        uint32_t* max_posting, unsigned long long* join, cudaStream_t s);
 // count must hold 2 * 2^(32-shift) + 1 words (counts, then their prefix sum).
 cudaError_t run_order(Launcher* L, const uint32_t* minhash, uint32_t n_genes, uint32_t shift, uint32_t* count,
                       uint32_t* order, void* scan_tmp, cudaStream_t s);

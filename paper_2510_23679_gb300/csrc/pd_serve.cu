@@ -193,6 +193,7 @@ struct pd_index {
   std::vector<int32_t> committed_genome_ptr;
   uint64_t resident_bytes = 0;
   bool stop = false;
+  bool hold = false;  // admission paused: queued requests wait (pd_index_hold)
   std::thread worker;
   pd_index_info stats{};
 
@@ -364,6 +365,7 @@ pd_status answer_level(pd_index* I, const Level& L, const uint8_t* tick_res, con
 // request of the tick against both levels (the levels hold the committed
 // genomes; the tick's genomes join them when the levels are next refreshed).
 pd_status run_tick(pd_index* I, std::vector<Request>& tick, std::vector<std::unique_ptr<pd_reply>>& replies) {
+  PhaseRange range_("pd: served tick");
   pd_ctx* c = I->c;
   pd_status st0 = refresh_levels(I);  // no-op unless an earlier refresh failed
   if (st0 != PD_OK) return st0;
@@ -456,7 +458,7 @@ void worker_main(pd_index* I) {
     std::vector<Request> tick;
     {
       std::unique_lock<std::mutex> lk(I->mu);
-      I->cv_work.wait(lk, [&] { return I->stop || !I->queue.empty(); });
+      I->cv_work.wait(lk, [&] { return I->stop || (!I->hold && !I->queue.empty()); });
       if (I->stop) return;
       // admission in arrival order while the tick's estimate fits the budget
       uint64_t W = I->committed_windows, G = I->committed_genes, tick_genes = 0;
@@ -673,6 +675,16 @@ PD_API pd_status pd_index_poll(pd_index* I, uint64_t ticket, int wait_ms, pd_rep
   auto it = I->done.find(ticket);
   *out = it->second.release();
   I->done.erase(it);
+  return PD_OK;
+}
+
+PD_API pd_status pd_index_hold(pd_index* I, int hold) {
+  if (!I) return PD_ERR_ARG;
+  {
+    std::lock_guard<std::mutex> lk(I->mu);
+    I->hold = hold != 0;
+  }
+  I->cv_work.notify_all();
   return PD_OK;
 }
 

@@ -43,7 +43,7 @@ class ProfilesInfo(C.Structure):
     _fields_ = [("k", C.c_int), ("n_genes", C.c_uint32), ("n_genomes", C.c_uint32),
                 ("n_windows", C.c_uint64), ("n_distinct", C.c_uint64), ("n_entries", C.c_uint64),
                 ("max_posting", C.c_uint32), ("count_bits", C.c_uint32), ("device_bytes", C.c_uint64),
-                ("alphabet", C.c_int)]
+                ("alphabet", C.c_int), ("n_join", C.c_uint64)]
 
 
 class HitsInfo(C.Structure):
@@ -137,6 +137,10 @@ _SIGNATURES = [
     ("pd_index_submit", C.c_int, [_P, _P, C.c_uint64, _P, C.c_uint32, C.POINTER(C.c_uint64)]),
     ("pd_index_poll", C.c_int, [_P, C.c_uint64, C.c_int, _PP]),
     ("pd_index_get_info", C.c_int, [_P, C.POINTER(IndexInfo)]),
+    ("pd_index_hold", C.c_int, [_P, C.c_int]),
+    ("pd_profiles_genome_ptr", C.c_int, [_P, _P]),
+    ("pd_best_hits_shard", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _PP]),
+    ("pd_hits_import", C.c_int, [_P, _P, C.c_uint32, _P, _P, _P, _P, _PP]),
     ("pd_index_genome_ptr", C.c_int, [_P, C.c_uint32, _P]),
     ("pd_index_free", None, [_P]),
     ("pd_reply_get_info", C.c_int, [_P, C.POINTER(ReplyInfo)]),
@@ -196,9 +200,16 @@ def _check(ctx, st, func):
 
 # ---------------------------------------------------------------- context
 class Ctx:
-    """Owns a pd_ctx*; device memory comes from torch's caching allocator."""
+    """Owns a pd_ctx*; device memory comes from torch's caching allocator.
 
-    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True):
+    on_alloc(nbytes) -> bool and on_free(ptr), if given, see every device
+    allocation and release the library makes through this context (torch's
+    allocator serves them).  on_alloc returning False refuses that
+    allocation: the library then reports PD_ERR_OOM for the call.  Use them to
+    account for or cap the library's device memory."""
+
+    def __init__(self, device: int = 0, stream=None, use_torch_allocator: bool = True, on_alloc=None,
+                 on_free=None):
         import torch
         lib = load()
         self.device = int(device)
@@ -212,16 +223,22 @@ class Ctx:
 
             def _alloc(nbytes, strm, user):
                 try:
+                    if on_alloc is not None and on_alloc(int(nbytes)) is False:
+                        return None
                     return torch.cuda.caching_allocator_alloc(int(nbytes), dev, strm or 0)
                 except Exception:
                     return None
 
             def _free(p, nbytes, strm, user):
+                if on_free is not None:
+                    on_free(p)
                 torch.cuda.caching_allocator_delete(p)
 
             a, f = ALLOC_FN(_alloc), FREE_FN(_free)
             self._keep = [a, f]
         else:
+            if on_alloc is not None or on_free is not None:
+                raise ValueError("allocation observers need use_torch_allocator=True")
             a, f = ALLOC_FN(), FREE_FN()
         h = C.c_void_p()
         st = lib.pd_ctx_create(self.device, stream, a, f, None, C.byref(h))
@@ -255,8 +272,9 @@ class Ctx:
         self.close()
 
 
-def pd_ctx_create(device: int = 0, stream=None, use_torch_allocator: bool = True) -> Ctx:
-    return Ctx(device, stream, use_torch_allocator)
+def pd_ctx_create(device: int = 0, stream=None, use_torch_allocator: bool = True, on_alloc=None,
+                  on_free=None) -> Ctx:
+    return Ctx(device, stream, use_torch_allocator, on_alloc, on_free)
 
 
 def pd_ctx_destroy(ctx: Ctx) -> None:
@@ -393,6 +411,13 @@ def pd_profiles_get_info(prof: Profiles) -> ProfilesInfo:
     return info
 
 
+def pd_profiles_genome_ptr(prof: Profiles):
+    """Host int32 genome offsets (n_genomes+1) the profiles were built with."""
+    out = np.zeros(pd_profiles_get_info(prof).n_genomes + 1, np.int32)
+    _check(prof.ctx, _lib.pd_profiles_genome_ptr(prof.handle, _ptr(out)), "pd_profiles_genome_ptr")
+    return out
+
+
 def pd_profiles_copy_mv(ctx: Ctx, prof: Profiles):
     """(mv_ptr int64[G+1], codes uint64[E], counts uint32[E], La uint32[G]) on the host."""
     info = pd_profiles_get_info(prof)
@@ -422,6 +447,35 @@ def pd_profiles_copy_index(ctx: Ctx, prof: Profiles):
 def pd_best_hits_all(ctx: Ctx, prof: Profiles) -> Hits:
     h = C.c_void_p()
     _check(ctx, _lib.pd_best_hits_all(ctx.handle, prof.handle, C.byref(h)), "pd_best_hits_all")
+    return Hits(ctx, h)
+
+
+def pd_best_hits_shard(ctx: Ctx, prof: Profiles, shard: int, n_shards: int) -> Hits:
+    """pd_best_hits_all restricted to shard `shard` of `n_shards` of the query
+    genes (rows of other genes empty); the union over shards is the whole."""
+    h = C.c_void_p()
+    _check(ctx, _lib.pd_best_hits_shard(ctx.handle, prof.handle, int(shard), int(n_shards), C.byref(h)),
+           "pd_best_hits_shard")
+    return Hits(ctx, h)
+
+
+def pd_hits_import(ctx: Ctx, prof: Profiles, pieces) -> Hits:
+    """One Best Hit handle from CSR pieces [(row_ptr int64 [n_genes+1], cols
+    int32 global ids ascending per row, s 32-bit), ...] (host or device), each
+    gene's row non-empty in at most one piece."""
+    G = pd_profiles_get_info(prof).n_genes
+    pieces = list(pieces)
+    n = len(pieces)
+    if n == 0:
+        raise ValueError("pd_hits_import: no pieces")
+    rps, cls, ss, ns = (C.c_void_p * n)(), (C.c_void_p * n)(), (C.c_void_p * n)(), (C.c_uint64 * n)()
+    for i, (rp, cols, s) in enumerate(pieces):
+        if int(rp.shape[0]) != G + 1 or int(s.shape[0]) != int(cols.shape[0]):
+            raise ValueError("pd_hits_import: row_ptr must have n_genes+1 entries and s one per column")
+        k = int(cols.shape[0])
+        rps[i], cls[i], ss[i], ns[i] = _ptr(rp), _ptr(cols) if k else None, _ptr(s) if k else None, k
+    h = C.c_void_p()
+    _check(ctx, _lib.pd_hits_import(ctx.handle, prof.handle, n, rps, cls, ss, ns, C.byref(h)), "pd_hits_import")
     return Hits(ctx, h)
 
 
@@ -538,9 +592,20 @@ def pd_best_hits_noalloc(ctx: Ctx, prof: Profiles, gi: int, gj: int, row_ptr, co
     """Best Hits of genome gi against gj into caller-owned device tensors, with
     no device allocation by the library (for callers that cannot allocate while
     they run).  row_ptr: int64 [|G_gi|+1]; cols: int32 [capacity]; s: uint32 or
-    int32 [capacity].  Returns the number of entries written."""
+    int32 [capacity], all CUDA tensors on ctx's device.  Returns the number of
+    entries written."""
+    import torch
+    gptr = pd_profiles_genome_ptr(prof)
+    n_rows = int(gptr[gi + 1] - gptr[gi]) if 0 <= gi < len(gptr) - 1 else 0
+    for name, t in (("row_ptr", row_ptr), ("cols", cols), ("s", s)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda or t.device.index != ctx.device:
+            raise ValueError(f"pd_best_hits_noalloc: {name} must be a CUDA tensor on device {ctx.device}")
+    if row_ptr.dtype != torch.int64 or row_ptr.numel() < n_rows + 1:
+        raise ValueError(f"pd_best_hits_noalloc: row_ptr must be int64 with at least {n_rows + 1} entries")
+    if cols.dtype != torch.int32 or s.dtype not in (torch.int32, getattr(torch, "uint32", torch.int32)):
+        raise ValueError("pd_best_hits_noalloc: cols must be int32 and s 32-bit")
     n = C.c_uint64(0)
-    cap = int(cols.shape[0])
+    cap = min(int(cols.numel()), int(s.numel()))
     _check(ctx, _lib.pd_best_hits_noalloc(ctx.handle, prof.handle, int(gi), int(gj), _ptr(row_ptr), _ptr(cols),
                                           _ptr(s), cap, C.byref(n)), "pd_best_hits_noalloc")
     return int(n.value)
@@ -667,6 +732,11 @@ def pd_index_get_info(index: Index) -> IndexInfo:
     info = IndexInfo()
     _check_status(_lib.pd_index_get_info(index.handle, C.byref(info)), "pd_index_get_info")
     return info
+
+
+def pd_index_hold(index: Index, hold: bool) -> None:
+    """Pause (True) or resume (False) the admission of queued requests."""
+    _check_status(_lib.pd_index_hold(index.handle, 1 if hold else 0), "pd_index_hold")
 
 
 def pd_index_genome_ptr(index: Index, n_genomes: int):

@@ -2,9 +2,10 @@
 
 A workload is profiled and compared all-against-all on the GPU exactly as
 bench.py times it (device-resident inputs, pd_build_profiles,
-pd_best_hits_all, pd_bbh_all).  The oracle then recomputes sampled genome
-pairs in full, and properties that hold at any size are checked on the whole
-result.
+pd_best_hits_all, pd_bbh_all).  Oracle B (inverted index on host threads,
+pinned to oracle A) then recomputes the whole result, every genome pair;
+oracle A recomputes sampled genome pairs in full; and properties that hold at
+any size are checked on the whole result.
 """
 import os
 
@@ -32,6 +33,19 @@ def run_full(name, expect_k):
     info = pd.pd_hits_get_info(hits)
     del hits, res, gp, gn
     return dict(ds=ds, k=k, ctx=ctx, prof=prof, rp=rp, cols=cols, s=s, bbh=bbh, La=La, info=info)
+
+
+def check_whole_against_oracle_b(full):
+    """Every Best Hit (with its sum-min) of every gene in every other genome,
+    and every BBH pair of every genome pair, equal oracle B's."""
+    ds = full["ds"]
+    idx = oracle.IndexB(ds, full["k"])
+    rp, cols, s, bbh = oracle.all_pairs_b(idx)
+    del idx
+    assert np.array_equal(full["rp"], rp), "Best Hit row lengths"
+    assert np.array_equal(full["cols"], cols), "Best Hit columns"
+    assert np.array_equal(full["s"], s), "Best Hit sum-min values"
+    assert np.array_equal(full["bbh"], bbh), "BBH pairs"
 
 
 def rows_towards(full, genome_from, genome_to):

@@ -95,27 +95,53 @@ def test_answer_against_oracle(ctx, stream):
 
 
 def test_alone_and_in_a_mix_agree(ctx, stream):
+    """The same genome answered alone and inside a burst that provably shares
+    one launch sequence: admission is held while the burst is queued, then
+    released, so every request of the burst is admitted by the same tick."""
     ds, res, k = stream
     x0 = N_RES
     r, gp = synth.genome_of(ds, x0)
     alone_idx = _index(ctx, res, k)
     alone = _reply(alone_idx, pd.pd_index_submit(alone_idx, r, gp))
+    assert alone[0].tick_requests == 1
     mix_idx = _index(ctx, res, k)
+    pd.pd_index_hold(mix_idx, True)
     tickets = [pd.pd_index_submit(mix_idx, r, gp)]
     for x in range(N_RES + 1, N_RES + N_INC):
         tickets.append(pd.pd_index_submit(mix_idx, *synth.genome_of(ds, x)))
+    assert pd.pd_index_get_info(mix_idx).queued == N_INC
+    pd.pd_index_hold(mix_idx, False)
     replies = [_reply(mix_idx, t) for t in tickets]
-    assert replies[0][0].snapshot_genomes == N_RES
+    info0 = replies[0][0]
+    assert info0.snapshot_genomes == N_RES
+    assert info0.tick_requests == N_INC, "the checked request did not share its tick with the burst"
+    assert all(rep[0].t_start_ns == info0.t_start_ns for rep in replies), "the burst ran in more than one tick"
     assert replies[0][1:] == alone[1:]
-    # every other answer equals the plain path at its own snapshot
-    resident = list(range(N_RES)) + list(range(N_RES, N_RES + N_INC))  # insertion order = submission order
-    shared = 0
+    # every other answer equals the plain path at its own snapshot (all of the
+    # burst was submitted before any of it was answered: snapshot = N_RES)
     for (info, rows, bbh), x in zip(replies, range(N_RES, N_RES + N_INC)):
-        exp_rows, exp_bbh, _ = _expected(ctx, ds, resident[:info.snapshot_genomes], x, k)
+        assert info.snapshot_genomes == N_RES
+        exp_rows, exp_bbh, _ = _expected(ctx, ds, list(range(N_RES)), x, k)
         assert rows == exp_rows and bbh == exp_bbh, f"genome {x}"
-        shared = max(shared, info.tick_requests)
-    assert pd.pd_index_get_info(mix_idx).requests_done == N_INC
-    assert shared >= 1
+    ii = pd.pd_index_get_info(mix_idx)
+    assert ii.requests_done == N_INC and ii.max_tick_requests == N_INC and ii.ticks == 1
+
+
+def test_poll_times_out_on_a_pending_request(ctx, stream):
+    ds, res, k = stream
+    index = _index(ctx, res, k)
+    pd.pd_index_hold(index, True)
+    t = pd.pd_index_submit(index, *synth.genome_of(ds, N_RES))
+    for wait_ms in (0, 50):
+        with pytest.raises(pd.PdError) as e:
+            pd.pd_index_poll(index, t, wait_ms)
+        assert e.value.status == 8  # PD_ERR_TIMEOUT
+    pd.pd_index_hold(index, False)
+    info, rows, bbh = _reply(index, t)
+    assert info.status == 0 and len(rows) == int(np.diff(synth.genome_of(ds, N_RES)[1]).size)
+    with pytest.raises(pd.PdError) as e:  # each answer is returned once
+        pd.pd_index_poll(index, t, 0)
+    assert e.value.status == 8
 
 
 def test_budget_and_arguments(ctx, stream):
