@@ -398,17 +398,21 @@ def serve_rate(pd, ctx, res, k, incoming, rate, n, budget, rng):
         if d > 0:
             time.sleep(d)
         tickets.append(pd.pd_index_submit(index, *incoming[i]))
-    lat, t_first, t_last, ticks = [], None, None, []
+    lat, wait, service, t_first, t_last, ticks = [], [], [], None, None, []
     for t in tickets:
         info = pd.pd_reply_get_info(pd.pd_index_poll(index, t, -1))
         assert info.status == 0, info.status
         lat.append((info.t_done_ns - info.t_submit_ns) / 1e6)
+        wait.append((info.t_start_ns - info.t_submit_ns) / 1e6)
+        service.append((info.t_done_ns - info.t_start_ns) / 1e6)
         t_first = info.t_submit_ns if t_first is None else min(t_first, info.t_submit_ns)
         t_last = info.t_done_ns if t_last is None else max(t_last, info.t_done_ns)
         ticks.append(info.tick_requests)
     ii = pd.pd_index_get_info(index)
     out = {"arrivals": n, "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
            "mean_ms": float(np.mean(lat)), "max_ms": float(np.max(lat)),
+           "queue_wait_p50_ms": float(np.percentile(wait, 50)), "queue_wait_p99_ms": float(np.percentile(wait, 99)),
+           "tick_p50_ms": float(np.percentile(service, 50)), "tick_p99_ms": float(np.percentile(service, 99)),
            "sustained_genomes_per_s": n / ((t_last - t_first) / 1e9),
            "offered_genomes_per_s": rate, "ticks": int(ii.ticks),
            "max_requests_per_tick": int(ii.max_tick_requests),
@@ -780,6 +784,25 @@ def main():
                "achieved": enc_bytes / (enc_ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                "frac": enc_bytes / (enc_ms / 1e3) / 1e9 / peak, "sort_passes": passes}
 
+    # ---- the merge form of Eq. (5) (pd_summin_list: two sorted vectors
+    # walked side by side, one warp per pair) on this step's BBH pairs, once
+    merge_form = None
+    if n_bbh:
+        a_d, b_d = torch.empty(n_bbh, dtype=torch.int32, device=dev), torch.empty(n_bbh, dtype=torch.int32, device=dev)
+        pd.pd_bbh_copy(ctx, bbh, a_d, b_d)
+        s_d, den_d = torch.empty_like(a_d), torch.empty_like(a_d)
+        for rep in range(2):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pd.pd_summin_list(ctx, prof, a_d, b_d, s_d, den_d)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        m_ms = e0.elapsed_time(e1)
+        merge_form = {"pairs": n_bbh, "ms": m_ms, "pairs_per_s": n_bbh / (m_ms / 1e3),
+                      "what": "sum-min and sum-max of every BBH pair of the step by the two-pointer merge of their "
+                              "sorted multiplicity vectors (the vectors of the genes involved sorted first)"}
+        del a_d, b_d, s_d, den_d
+
     # ---- end to end through the C ABI from pinned host buffers: inputs
     # copied in, and the whole result (the Best Hit CSR with each hit's
     # sum-min, and the BBH pairs) copied back, every step
@@ -876,6 +899,7 @@ def main():
                          "kernel_ms": k_avg_ms, "alg_bytes": alg_bytes, "peak_source": peak_src},
             "e2e": e2e,
             "served": served,
+            "merge_form": merge_form,
             "phases": phases,
             "encoder_roofline": encoder,
             "l1tex_roofline": l1tex,

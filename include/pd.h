@@ -325,6 +325,19 @@ pd_status pd_families(pd_ctx* ctx, const pd_bbh_set* bbh, uint32_t n_genes, int3
 
 /* ---------------------------------------------------------------- sum-min */
 
+/* Sum-min of listed gene pairs by the paper's own form: the two
+ * multiplicity vectors, sorted by k-mer, walked side by side (the similarity
+ * of Algorithm 2; Eq. (5)).  Pair i is (a[i], b[i]), global gene ids of this
+ * dataset (any genomes, a gene with itself allowed).  s[i] receives sum-min,
+ * den[i] the Eq. (5) denominator sum-max = La + Lb - s; GJ = s / den (0/0 for
+ * two genes without windows).  a, b, s, den are host or device pointers (n
+ * entries each; s or den NULL to skip).  One warp merges one pair, so the
+ * call suits known pairs (the similarity of BBH pairs, a candidate list); the
+ * all-against-all search is pd_best_hits_all.  Errors: PD_ERR_ARG (a gene id
+ * not below n_genes), PD_ERR_OOM, PD_ERR_CUDA. */
+pd_status pd_summin_list(pd_ctx* ctx, const pd_profiles* prof, const uint32_t* a, const uint32_t* b, uint64_t n,
+                         uint32_t* s, uint32_t* den);
+
 /* Every pair (a in G_gi, b in G_gj) with s >= 1 and its s (Eq. (5)
  * numerator), local indices, ascending (a, b).  Two-phase: with a == NULL
  * only *n is written; otherwise a, b, s must hold *n entries (host or device)

@@ -26,11 +26,48 @@ __device__ __forceinline__ uint32_t partner_row(const BbhRows& R, uint32_t b) {
   return R.all_pairs ? b : R.nA + (b - R.qb0);
 }
 
+// Is a in the ascending row hit_b[off .. off+n)?  Rows of the all-pairs form
+// hold about one target per genome, so gene ids spread evenly over the row:
+// an interpolation guess lands next to a, a galloping step brackets it and a
+// binary search finishes (two to four reads instead of a full binary search).
 __device__ __forceinline__ bool row_contains(const uint32_t* __restrict__ hit_b, unsigned long long off, uint32_t n,
                                              uint32_t a) {
-  uint32_t lo = 0, hi = n;
+  if (n == 0) return false;
+  const uint32_t first = hit_b[off], last = hit_b[off + n - 1];
+  if (a < first || a > last) return false;
+  if (a == first || a == last) return true;
+  // here first < a < last, so n >= 3 and the answer lies in [1, n-1)
+  const uint32_t g = (uint32_t)(((unsigned long long)(a - first) * (n - 1)) / (last - first));
+  const uint32_t v = hit_b[off + g];
+  if (v == a) return true;
+  uint32_t lo, hi;  // a, if present, is in [lo, hi)
+  if (v < a) {
+    lo = g + 1;
+    hi = n - 1;
+    for (uint32_t step = 1; g + step < n - 1; step <<= 1) {
+      const uint32_t w = hit_b[off + g + step];
+      if (w == a) return true;
+      if (w > a) {
+        hi = g + step;
+        break;
+      }
+      lo = g + step + 1;
+    }
+  } else {
+    lo = 1;
+    hi = g;
+    for (uint32_t step = 1; step < g; step <<= 1) {
+      const uint32_t w = hit_b[off + g - step];
+      if (w == a) return true;
+      if (w < a) {
+        lo = g - step + 1;
+        break;
+      }
+      hi = g - step;
+    }
+  }
   while (lo < hi) {
-    uint32_t mid = (lo + hi) >> 1;
+    const uint32_t mid = (lo + hi) >> 1;
     if (hit_b[off + mid] < a) lo = mid + 1; else hi = mid;
   }
   return lo < n && hit_b[off + lo] == a;
@@ -45,13 +82,16 @@ __global__ void __launch_bounds__(256) k_bbh_count(BbhRows R, uint8_t* __restric
       const uint32_t a = row_gene(R, x);
       const unsigned long long off = R.row_off[x];
       const uint32_t n = R.row_len[x];
-      const uint32_t ga = R.all_pairs ? R.gene_genome[a] : 0u;
+      // all form: a pair is emitted from the row of its gene in the earlier
+      // genome; genes are numbered genome by genome, so a target lies in a
+      // later genome exactly when it is past the end of a's genome
+      const uint32_t own_end = (R.all_pairs && !R.paralog) ? (uint32_t)R.genome_ptr[R.gene_genome[a] + 1] : 0u;
       for (uint32_t e0 = 0; e0 < n; e0 += 32) {
         const uint32_t e = e0 + lane;
         bool f = false;
         if (e < n) {
           const uint32_t b = R.hit_b[off + e];
-          if (!R.all_pairs || (R.paralog ? b > a : R.gene_genome[b] > ga)) {
+          if (!R.all_pairs || (R.paralog ? b > a : b >= own_end)) {
             const uint32_t y = partner_row(R, b);
             f = row_contains(R.hit_b, R.row_off[y], R.row_len[y], a);
           }

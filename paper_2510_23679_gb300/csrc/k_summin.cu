@@ -207,6 +207,9 @@ struct Chunk {
 // sectors it has already loaded.
 constexpr uint32_t kRounds = 4;
 constexpr uint32_t kWarpWalkMinAvg = 16;
+// Target genomes from which a query's Best Hits are ranked through per-genome
+// positions rather than pairwise.
+constexpr uint32_t kRankByGenomeMin = 64;
 
 // Memory of one call: table, the list of occupied slots (filled after the
 // walk) and the hit list.
@@ -466,6 +469,14 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
   }
 
   bool overflow = sh->overflow != 0;
+  const uint32_t n_best = Q.all_pairs ? P.n_genomes : 1u;
+  // With few target genomes a row has few hits and ranking them pairwise is
+  // cheaper than a block scan over the genomes.
+  const bool by_genome = !kEmitAll && n_best >= kRankByGenomeMin;
+  // Best Hits of each target genome, then (exclusive scan) the first output
+  // position of each genome's hits: rows come out ordered by gene because
+  // genes are numbered genome by genome
+  uint32_t* hcnt = (uint32_t*)(best + n_best);
   // Slots are visited interleaved (slot = i * kThreads + tid: conflict-free).
   const uint32_t slots = tb.cap / kThreads;
   uint32_t n_occ = 0, pos = 0;
@@ -495,8 +506,10 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
       }
     } else {
       // ---- per target genome: the maximum ratio, then every entry at it
-      const uint32_t n_best = Q.all_pairs ? P.n_genomes : 1u;
-      for (uint32_t j = tid; j < n_best; j += kThreads) best[j] = 0ull;
+      for (uint32_t j = tid; j < n_best; j += kThreads) {
+        best[j] = 0ull;
+        if (by_genome) hcnt[j] = 0u;
+      }
       __syncthreads();
       for (uint32_t u = tid; u < n_occ; u += kThreads) {
         uint32_t b, s;
@@ -518,8 +531,11 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
         if (!(Q.all_pairs && ((b >= own0 && b < own1) || b >= tend)) && b != self &&
             (!kFilter || filter_pass(Q, P.k, La_a, gi & 0xFFFFu, acc.vpa[h], acc.vpb[h])) &&
             ratio_equal(s, La_a + (gi & 0xFFFFu) - s, (uint32_t)(bv >> 32), (uint32_t)bv)) {
+          // s <= La <= 65535 and the genome < 65536: (b, genome, s) in one word
+          const uint32_t g = Q.all_pairs ? (gi >> 16) : 0u;
           const uint32_t slot = atomicAdd(&sh->n_out, 1u);
-          if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | s;
+          if (slot < tb.out_cap) out[slot] = ((unsigned long long)b << 32) | (g << 16) | s;
+          if (by_genome) atomicAdd(&hcnt[g], 1u);
         }
         acc.clear(h);
       }
@@ -543,6 +559,23 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
     __syncthreads();
     return;
   }
+  if (by_genome) {
+    // ---- first output position of each target genome's hits (exclusive
+    // scan of the per-genome counts; each thread scans a run of genomes)
+    const uint32_t per = (n_best + kThreads - 1) / kThreads;
+    const uint32_t j0 = min(n_best, tid * per), j1 = min(n_best, j0 + per);
+    uint32_t mine = 0;
+    for (uint32_t j = j0; j < j1; ++j) mine += hcnt[j];
+    uint32_t total;
+    uint32_t run = block_exclusive_scan(mine, sh->warp_tmp, &total);
+    for (uint32_t j = j0; j < j1; ++j) {
+      const uint32_t c = hcnt[j];
+      hcnt[j] = run;
+      run += c;
+    }
+    if (tid == 0) hcnt[n_best] = total;
+    __syncthreads();
+  }
   // ---- append: each hit goes to its rank among the query's hits
   if (tid == 0) {
     const unsigned long long base = atomicAdd(O.cursor, (unsigned long long)n_out);
@@ -557,10 +590,27 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
   if (base + n_out <= O.out_cap) {
     for (uint32_t t = tid; t < n_out; t += kThreads) {
       const unsigned long long v = out[t];
-      uint32_t rank = 0;
-      for (uint32_t u = 0; u < n_out; ++u) rank += (out[u] < v) ? 1u : 0u;
-      O.out_b[base + rank] = (uint32_t)(v >> 32);
-      O.out_s[base + rank] = (uint32_t)v;
+      const uint32_t b = (uint32_t)(v >> 32);
+      uint32_t rank = 0, sv;
+      if (!by_genome) {
+        // rank = hits with a smaller gene id (the genome field sits below the
+        // gene id, so comparing whole words orders by gene)
+        for (uint32_t u = 0; u < n_out; ++u) rank += (out[u] < v) ? 1u : 0u;
+        sv = kEmitAll ? (uint32_t)v : ((uint32_t)v & 0xFFFFu);
+      } else {
+        // the genome's first position, plus the tied hits of the same genome
+        // with a smaller gene id (genomes with one Best Hit skip the loop)
+        const uint32_t g = ((uint32_t)v >> 16) & 0xFFFFu;
+        rank = hcnt[g];
+        if (hcnt[g + 1] - rank > 1u)
+          for (uint32_t u = 0; u < n_out; ++u) {
+            const unsigned long long w = out[u];
+            rank += ((((uint32_t)w >> 16) & 0xFFFFu) == g && (uint32_t)(w >> 32) < b) ? 1u : 0u;
+          }
+        sv = (uint32_t)v & 0xFFFFu;
+      }
+      O.out_b[base + rank] = b;
+      O.out_s[base + rank] = sv;
     }
   }
   __syncthreads();
@@ -577,7 +627,8 @@ struct SmemTier {
   static constexpr size_t kUsed = (size_t)kUsedCap * 2;
   static constexpr size_t kAfterWalk = kUsed + (size_t)kOutCap * 8;
   static constexpr size_t kUnion = Chunk<kThreads>::kBytes > kAfterWalk ? Chunk<kThreads>::kBytes : kAfterWalk;
-  static size_t bytes(uint32_t n_best) { return kTable + kUnion + (size_t)(n_best ? n_best : 1) * 8; }
+  // per target genome: best ratio (8 B) and hit count / first position (4 B), one more position
+  static constexpr size_t bytes(uint32_t n_best) { return kTable + kUnion + (size_t)(n_best ? n_best : 1) * 12 + 4; }
 };
 
 template <int kThreads, int kMinBlocks, uint32_t kCap, uint32_t kOutCap, bool kPacked, bool kEmitAll,
@@ -675,19 +726,19 @@ using T1E = SmemTier<kT1Threads, kT1Cap, kT1OutEmit, true, false, kT1Used>;
 // genomes up to which six compact blocks (with their static scalars and the
 // 1 KB the runtime reserves per block) fit a 164 KB carveout
 constexpr uint32_t kT1CompactGenomes =
-    (uint32_t)((164u * 1024u / kT1MinBlocks - 1024u - sizeof(Scalars) - T1::kTable - T1::kUnion) / 8u);
-static_assert(kT1CompactGenomes >= 64, "compact tier-1 layout holds tens of genomes");
+    (uint32_t)((164u * 1024u / kT1MinBlocks - 1024u - sizeof(Scalars) - T1::kTable - T1::kUnion - 4u) / 12u);
+static_assert(kT1CompactGenomes >= 50, "compact tier-1 layout holds tens of genomes");
 using T2 = SmemTier<kT2Threads, kT2Cap, kT2Out, false>;
 using T2E = SmemTier<kT2Threads, kT2Cap, kT2OutEmit, false>;
-static_assert(T1F::kTable + T1F::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 1 shared memory");
-static_assert(T2::kTable + T2::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "tier 2 shared memory");
-static_assert(T2E::kTable + T2E::kUnion + 8 <= 227 * 1024, "tier 2 (emit-all, one target genome) shared memory");
+static_assert(T1F::bytes(PD_MAX_GENOMES) <= 227 * 1024, "tier 1 shared memory");
+static_assert(T2::bytes(PD_MAX_GENOMES) <= 227 * 1024, "tier 2 shared memory");
+static_assert(T2E::bytes(1) <= 227 * 1024, "tier 2 (emit-all, one target genome) shared memory");
 // Filtered queries (Eqs. (6)-(7)): split 4096-slot table with the two
 // directional sums; what does not fit goes straight to the global tier.
 constexpr int kFThreads = 256, kFMinBlocks = 2;
 constexpr uint32_t kFCap = 4096, kFOut = 512;
 using TF = SmemTier<kFThreads, kFCap, kFOut, false, true>;
-static_assert(TF::kTable + TF::kUnion + PD_MAX_GENOMES * 8 <= 227 * 1024, "filtered tier shared memory");
+static_assert(TF::bytes(PD_MAX_GENOMES) <= 227 * 1024, "filtered tier shared memory");
 
 template <typename K>
 cudaError_t launch_smem(K kernel, Launcher* L, const char* name, int threads, size_t smem, uint32_t max_grid,
@@ -749,7 +800,7 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
 }
 
 size_t summin_global_smem_bytes(uint32_t n_genomes) {
-  return Chunk<256>::kBytes + (size_t)(n_genomes ? n_genomes : 1) * 8;
+  return Chunk<256>::kBytes + (size_t)(n_genomes ? n_genomes : 1) * 12 + 4;
 }
 
 cudaError_t run_summin_global(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O,

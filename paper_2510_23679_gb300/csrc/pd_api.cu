@@ -1161,6 +1161,7 @@ PD_API pd_status pd_bbh_all(pd_ctx* c, const pd_profiles* P, const pd_hits* H, p
     R.all_pairs = 1;
     R.n_rows = H->n_rows;
     R.gene_genome = P->view.gene_genome;
+    R.genome_ptr = P->view.genome_ptr;
     R.row_off = H->row_off.as<unsigned long long>();
     R.row_len = H->row_len.as<uint32_t>();
     R.hit_b = H->out_b.as<uint32_t>();
@@ -1284,6 +1285,7 @@ PD_API pd_status pd_paralog_bbh(pd_ctx* c, const pd_profiles* P, const pd_hits* 
     R.paralog = 1;
     R.n_rows = H->n_rows;
     R.gene_genome = P->view.gene_genome;
+    R.genome_ptr = P->view.genome_ptr;
     R.row_off = H->row_off.as<unsigned long long>();
     R.row_len = H->row_len.as<uint32_t>();
     R.hit_b = H->out_b.as<uint32_t>();

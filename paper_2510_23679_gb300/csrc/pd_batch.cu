@@ -279,6 +279,7 @@ pd_status batch_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const i
     R.all_pairs = 1;
     R.n_rows = C->hits.n_rows;
     R.gene_genome = P->view.gene_genome;
+    R.genome_ptr = P->view.genome_ptr;
     R.row_off = C->hits.row_off.as<unsigned long long>();
     R.row_len = C->hits.row_len.as<uint32_t>();
     R.hit_b = C->hits.out_b.as<uint32_t>();

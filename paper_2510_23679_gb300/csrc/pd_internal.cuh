@@ -361,6 +361,7 @@ struct BbhRows {
   uint32_t n_rows;
   uint32_t nA, qa0, qb0;       // pair form: rows 0..nA-1 = genes qa0.., rest = genes qb0..
   const uint16_t* gene_genome; // all form: genome of each gene
+  const int32_t* genome_ptr;   // all form: first gene of each genome (n_genomes + 1)
   const unsigned long long* row_off;
   const uint32_t* row_len;
   const uint32_t* hit_b;

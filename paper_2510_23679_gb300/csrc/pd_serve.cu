@@ -194,8 +194,25 @@ struct pd_index {
   uint64_t resident_bytes = 0;
   bool stop = false;
   bool hold = false;  // admission paused: queued requests wait (pd_index_hold)
+  // The levels index genomes [0, covered); genomes committed since then make
+  // them stale.  A request is answered from levels covering its snapshot.
+  uint32_t covered = 0;
+  bool stale = false;
   std::thread worker;
   pd_index_info stats{};
+  // Background merge: a builder thread with a context (stream, memory pool)
+  // of its own builds the next base from a copy of the residues while the
+  // worker keeps answering ticks from the current base and delta.
+  pd_ctx* bc = nullptr;
+  cudaStream_t bstream = nullptr;
+  std::thread builder;
+  std::mutex bmu;
+  bool merging = false;     // a builder thread was started and not yet joined
+  bool merge_done = false;  // the builder finished (its status in merge_status)
+  pd_status merge_status = PD_OK;
+  Level merged;             // its result: the profiles of genomes [0, merged.genome1)
+  Buf merge_res;            // the builder's copy of the residues (its context)
+  uint64_t merge_bytes = 0; // device bytes the builder holds or will hold
 
   ~pd_index() {
     {
@@ -204,62 +221,156 @@ struct pd_index {
     }
     cv_work.notify_all();
     if (worker.joinable()) worker.join();
+    if (builder.joinable()) builder.join();
     if (c) {
       cudaSetDevice(device);
       base.P.reset();
       delta.P.reset();
+      merged.P.reset();
+      merge_res.release();
       res.release();
       cudaStreamSynchronize(stream);
+      if (bstream) cudaStreamSynchronize(bstream);
       pd_ctx_destroy(c);
+      if (bc) pd_ctx_destroy(bc);
     }
     if (stream) cudaStreamDestroy(stream);
+    if (bstream) cudaStreamDestroy(bstream);
   }
 };
 
 namespace {
 
-// Profiles of resident genomes [g0, g1) as one level.
-pd_status build_level(pd_index* I, uint32_t g0, uint32_t g1, Level* L) {
-  pd_ctx* c = I->c;
+// Profiles of resident genomes [g0, g1) as one level, built on context c
+// from residues `res` (device) and the host offsets gene_ptr / genome_ptr.
+pd_status build_level_on(pd_ctx* c, int k, const uint8_t* res, const std::vector<int64_t>& gene_ptr,
+                         const std::vector<int32_t>& genome_ptr, const std::vector<uint64_t>& genome_windows,
+                         uint32_t g0, uint32_t g1, Level* L) {
   L->P.reset();
   L->genome0 = g0;
   L->genome1 = g1;
-  L->gene0 = (uint32_t)I->genome_ptr[g0];
-  L->gene1 = (uint32_t)I->genome_ptr[g1];
+  L->gene0 = (uint32_t)genome_ptr[g0];
+  L->gene1 = (uint32_t)genome_ptr[g1];
   L->windows = 0;
-  for (uint32_t i = g0; i < g1; ++i) L->windows += I->genome_windows[i];
+  for (uint32_t i = g0; i < g1; ++i) L->windows += genome_windows[i];
   if (g1 == g0 || L->gene1 == L->gene0) return PD_OK;
-  const int64_t r0 = I->gene_ptr[L->gene0];
-  std::vector<int64_t> gp(I->gene_ptr.begin() + L->gene0, I->gene_ptr.begin() + L->gene1 + 1);
+  const int64_t r0 = gene_ptr[L->gene0];
+  std::vector<int64_t> gp(gene_ptr.begin() + L->gene0, gene_ptr.begin() + L->gene1 + 1);
   for (auto& x : gp) x -= r0;
-  std::vector<int32_t> gn(I->genome_ptr.begin() + g0, I->genome_ptr.begin() + g1 + 1);
+  std::vector<int32_t> gn(genome_ptr.begin() + g0, genome_ptr.begin() + g1 + 1);
   for (auto& x : gn) x -= (int32_t)L->gene0;
   pd_profiles* P = nullptr;
-  pd_status st = build_profiles_impl(c, I->res.as<uint8_t>() + r0, (uint64_t)gp.back(), gp.data(),
-                                     L->gene1 - L->gene0, gn.data(), g1 - g0, I->k, nullptr, &P);
+  pd_status st = build_profiles_impl(c, res + r0, (uint64_t)gp.back(), gp.data(), L->gene1 - L->gene0, gn.data(),
+                                     g1 - g0, k, nullptr, &P);
   if (st != PD_OK) return st;
   L->P.reset(P);
   return PD_OK;
 }
 
-// Brings the levels up to the committed genomes: rebuild the delta over the
-// genomes after the base, or merge everything into a new base once the delta
-// holds more than a quarter of the base's windows.
+pd_status build_level(pd_index* I, uint32_t g0, uint32_t g1, Level* L) {
+  return build_level_on(I->c, I->k, I->res.as<uint8_t>(), I->gene_ptr, I->genome_ptr, I->genome_windows, g0, g1, L);
+}
+
+// Builder thread: the profiles of genomes [0, n) from the snapshot taken by
+// start_merge (host offsets passed by value, residues in merge_res).
+void builder_main(pd_index* I, uint32_t n, std::vector<int64_t> gene_ptr, std::vector<int32_t> genome_ptr,
+                  std::vector<uint64_t> genome_windows) {
+  cudaSetDevice(I->device);
+  Level L;
+  pd_status st;
+  try {
+    st = build_level_on(I->bc, I->k, I->merge_res.as<uint8_t>(), gene_ptr, genome_ptr, genome_windows, 0, n, &L);
+    if (st == PD_OK && cudaStreamSynchronize(I->bstream) != cudaSuccess) st = PD_ERR_CUDA;
+  } catch (...) {
+    st = PD_ERR_INTERNAL;
+  }
+  std::lock_guard<std::mutex> lk(I->bmu);
+  I->merged = std::move(L);
+  I->merge_status = st;
+  I->merge_done = true;
+}
+
+// Starts a background merge of the committed genomes [0, n) (the worker's
+// thread, between ticks): the builder gets a copy of the residues -- the
+// worker may grow (move) its own buffer meanwhile -- and of the host offsets.
+pd_status start_merge(pd_index* I, uint32_t n) {
+  pd_ctx* c = I->c;
+  if (!I->bc) {
+    // the background merge yields the SMs to ticks: lowest stream priority
+    int least = 0, greatest = 0;
+    CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    CK(cudaStreamCreateWithPriority(&I->bstream, cudaStreamNonBlocking, least));
+    pd_status st = pd_ctx_create(I->device, I->bstream, nullptr, nullptr, nullptr, &I->bc);
+    if (st != PD_OK) return fail(c, st, "could not create the builder context");
+    uint64_t keep = I->budget;
+    CK(cudaMemPoolSetAttribute(I->bc->pool, cudaMemPoolAttrReleaseThreshold, &keep));
+  }
+  const uint64_t r_end = (uint64_t)I->gene_ptr[I->genome_ptr[n]];
+  if (!I->merge_res.alloc(I->bc, std::max<uint64_t>(r_end, 1)))
+    return fail(c, PD_ERR_OOM, "residue copy for the background merge");
+  // the residues were written on the worker's stream; the copy reads them on
+  // the builder's and ends before the worker can move its buffer
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(ev, c->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(I->bstream, ev, 0);
+  if (e == cudaSuccess && r_end) e = cudaMemcpyAsync(I->merge_res.p, I->res.p, r_end, cudaMemcpyDeviceToDevice, I->bstream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(I->bstream);
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return fail_cuda(c, e, "residue copy for the background merge");
+  I->merging = true;
+  I->merge_done = false;
+  I->merge_bytes = I->merge_res.n + I->base.bytes() + I->delta.bytes();  // the new base is about their size
+  std::vector<int64_t> gp(I->gene_ptr.begin(), I->gene_ptr.begin() + I->genome_ptr[n] + 1);
+  std::vector<int32_t> gn(I->genome_ptr.begin(), I->genome_ptr.begin() + n + 1);
+  std::vector<uint64_t> gw(I->genome_windows.begin(), I->genome_windows.begin() + n);
+  I->builder = std::thread(builder_main, I, n, std::move(gp), std::move(gn), std::move(gw));
+  return PD_OK;
+}
+
+// Brings the levels up to the committed genomes (the worker's thread, between
+// ticks).  The delta is rebuilt over the genomes after the base.  Once it holds
+// more than a quarter of the base's windows, a builder thread merges
+// everything into a new base in the background while ticks go on against the
+// old base and the delta; when it is done the new base replaces the old one
+// and the delta shrinks to the genomes committed since the merge began.
 pd_status refresh_levels(pd_index* I) {
   const uint32_t n = (uint32_t)I->genome_ptr.size() - 1;
+  // ---- a finished background merge takes over
+  bool done = false;
+  {
+    std::lock_guard<std::mutex> lk(I->bmu);
+    done = I->merging && I->merge_done;
+  }
+  if (done) {
+    I->builder.join();
+    I->merging = false;
+    I->merge_res.release();  // the builder's stream is idle: its work was synchronized
+    I->merge_bytes = 0;
+    if (I->merge_status == PD_OK) {
+      I->base = std::move(I->merged);  // the old base's last use ended with the previous tick
+      I->delta = Level();
+      I->delta.genome0 = I->delta.genome1 = I->base.genome1;
+      I->delta.gene0 = I->delta.gene1 = I->base.gene1;
+    }
+    I->merged = Level();
+  }
   const uint32_t nb = I->base.genome1;
   if (I->delta.genome0 == nb && I->delta.genome1 == n && (I->delta.P || nb == n)) return PD_OK;
   uint64_t dw = 0;
   for (uint32_t i = nb; i < n; ++i) dw += I->genome_windows[i];
   I->delta.P.reset();
-  if (4 * dw > I->base.windows) {
-    I->base.P.reset();
-    pd_status st = build_level(I, 0, n, &I->base);
-    if (st != PD_OK) return st;
-    I->delta = Level();
-    I->delta.genome0 = I->delta.genome1 = n;
-    I->delta.gene0 = I->delta.gene1 = (uint32_t)I->genome_ptr[n];
-    return PD_OK;
+  if (!I->merging && 4 * dw > I->base.windows) {
+    pd_status st = start_merge(I, n);
+    if (st != PD_OK) {  // no background merge: merge here, as the fallback
+      I->base.P.reset();
+      st = build_level(I, 0, n, &I->base);
+      if (st != PD_OK) return st;
+      I->delta = Level();
+      I->delta.genome0 = I->delta.genome1 = n;
+      I->delta.gene0 = I->delta.gene1 = (uint32_t)I->genome_ptr[n];
+      return PD_OK;
+    }
   }
   return build_level(I, nb, n, &I->delta);
 }
@@ -367,8 +478,6 @@ pd_status answer_level(pd_index* I, const Level& L, const uint8_t* tick_res, con
 pd_status run_tick(pd_index* I, std::vector<Request>& tick, std::vector<std::unique_ptr<pd_reply>>& replies) {
   PhaseRange range_("pd: served tick");
   pd_ctx* c = I->c;
-  pd_status st0 = refresh_levels(I);  // no-op unless an earlier refresh failed
-  if (st0 != PD_OK) return st0;
   const uint32_t n_tick = (uint32_t)tick.size();
   const uint32_t g_res = (uint32_t)I->genome_ptr.size() - 1;
   if (g_res + n_tick > PD_MAX_GENOMES) return fail(c, PD_ERR_BUDGET, "the index holds at most PD_MAX_GENOMES genomes");
@@ -456,14 +565,26 @@ void worker_main(pd_index* I) {
   cudaSetDevice(I->device);
   for (;;) {
     std::vector<Request> tick;
+    bool refresh = false;
     {
       std::unique_lock<std::mutex> lk(I->mu);
-      I->cv_work.wait(lk, [&] { return I->stop || (!I->hold && !I->queue.empty()); });
+      // work: queued requests (unless held), or stale levels to refresh while
+      // nothing waits
+      I->cv_work.wait(lk, [&] {
+        return I->stop || (!I->hold && !I->queue.empty()) || (I->stale && (I->hold || I->queue.empty()));
+      });
       if (I->stop) return;
+      // The levels are refreshed only when a queued request needs the genomes
+      // committed since (its snapshot is past the levels' coverage), or when
+      // no request waits; requests queued during a tick were stamped before
+      // its commit and are answered at once from the levels as they are.
+      const bool needs = !I->hold && !I->queue.empty() && I->queue.front().snapshot > I->covered;
+      refresh = needs || (I->stale && (I->hold || I->queue.empty()));
       // admission in arrival order while the tick's estimate fits the budget
       uint64_t W = I->committed_windows, G = I->committed_genes, tick_genes = 0;
-      while (!I->queue.empty() && tick.size() < I->max_tick) {
+      while (!refresh && !I->queue.empty() && tick.size() < I->max_tick) {
         const Request& r = I->queue.front();
+        if (r.snapshot > I->covered) break;  // needs a refresh first
         const uint64_t ng = r.gene_ptr.size() - 1;
         const uint64_t est = I->resident_bytes + tick_bytes(W + r.windows, G + ng, tick_genes + ng,
                                                             I->committed_genes, I->committed, tick.size() + 1) +
@@ -487,6 +608,39 @@ void worker_main(pd_index* I) {
         tick.push_back(std::move(I->queue.front()));
         I->queue.pop_front();
       }
+    }
+    if (refresh) {
+      // take the committed genomes into the levels (the delta is rebuilt, or
+      // a background merge begins or is taken over)
+      pd_status rs;
+      try {
+        rs = refresh_levels(I);
+      } catch (...) {
+        rs = PD_ERR_INTERNAL;
+      }
+      const uint32_t cov = (I->delta.P || I->delta.genome1 == I->delta.genome0)
+                               ? std::max(I->base.genome1, I->delta.genome1)
+                               : I->base.genome1;
+      std::lock_guard<std::mutex> lk2(I->mu);
+      I->covered = cov;
+      // a failed idle refresh is not retried until the next commit or a
+      // request that needs it (which then receives the error)
+      I->stale = rs == PD_OK && cov < (uint32_t)I->genome_ptr.size() - 1;
+      I->resident_bytes = I->res.n + I->base.bytes() + I->delta.bytes() + I->merge_bytes;
+      if (rs != PD_OK && !I->queue.empty() && I->queue.front().snapshot > cov) {
+        // the refresh failed: answer the waiting request with the error rather than retry forever
+        Request r = std::move(I->queue.front());
+        I->queue.pop_front();
+        std::unique_ptr<pd_reply> R(new pd_reply());
+        R->info.ticket = r.ticket;
+        R->info.status = rs;
+        R->info.t_submit_ns = r.t_submit;
+        R->info.t_done_ns = now_ns();
+        R->err = I->c->err;
+        I->done[r.ticket] = std::move(R);
+        I->cv_done.notify_all();
+      }
+      continue;
     }
     if (tick.empty()) continue;
     const int64_t t_start = now_ns();
@@ -536,20 +690,8 @@ void worker_main(pd_index* I) {
         I->done[r.ticket] = std::move(R);
       }
     }
+    if (st == PD_OK) I->stale = true;  // the tick's genomes are resident, not yet indexed
     I->cv_done.notify_all();
-    lk.unlock();
-    // take the new residents into the index before the next tick
-    if (st == PD_OK) {
-      pd_status rs;
-      try {
-        rs = refresh_levels(I);
-      } catch (...) {
-        rs = PD_ERR_INTERNAL;
-      }
-      (void)rs;  // a failed refresh is retried (and reported) by the next tick
-      std::lock_guard<std::mutex> lk2(I->mu);
-      I->resident_bytes = I->res.n + I->base.bytes() + I->delta.bytes();
-    }
   }
 }
 
@@ -565,7 +707,10 @@ pd_status index_create(pd_ctx* caller, const uint8_t* residues, uint64_t n_res, 
   I->k = k;
   I->budget = hbm_budget;
   CK(cudaSetDevice(I->device));
-  CK(cudaStreamCreateWithFlags(&I->stream, cudaStreamNonBlocking));
+  // ticks run at the highest stream priority, ahead of a background merge
+  int least = 0, greatest = 0;
+  CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+  CK(cudaStreamCreateWithPriority(&I->stream, cudaStreamNonBlocking, greatest));
   pd_status st = pd_ctx_create(I->device, I->stream, nullptr, nullptr, nullptr, &I->c);
   if (st != PD_OK) return fail(caller, st, "could not create the index context");
   c = I->c;
@@ -596,6 +741,7 @@ pd_status index_create(pd_ctx* caller, const uint8_t* residues, uint64_t n_res, 
   I->committed_windows = windows_of(I->gene_ptr, 0, n_genes, k);
   I->committed_genome_ptr = I->genome_ptr;
   I->committed_res = n_res;
+  I->covered = n_genomes;
   I->resident_bytes = I->res.n + I->base.bytes();
   if (I->resident_bytes > hbm_budget) return fail(caller, PD_ERR_BUDGET, "the resident index exceeds the budget");
   I->worker = std::thread(worker_main, I.get());

@@ -140,6 +140,7 @@ _SIGNATURES = [
     ("pd_index_hold", C.c_int, [_P, C.c_int]),
     ("pd_profiles_genome_ptr", C.c_int, [_P, _P]),
     ("pd_best_hits_shard", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _PP]),
+    ("pd_summin_list", C.c_int, [_P, _P, _P, _P, C.c_uint64, _P, _P]),
     ("pd_hits_import", C.c_int, [_P, _P, C.c_uint32, _P, _P, _P, _P, _PP]),
     ("pd_index_genome_ptr", C.c_int, [_P, C.c_uint32, _P]),
     ("pd_index_free", None, [_P]),
@@ -586,6 +587,29 @@ def pd_summin_pairs(ctx: Ctx, prof: Profiles, gi: int, gj: int):
     _check(ctx, _lib.pd_summin_pairs(ctx.handle, prof.handle, int(gi), int(gj), _ptr(a), _ptr(b), _ptr(s),
                                      C.byref(n)), "pd_summin_pairs")
     return a[:cnt], b[:cnt], s[:cnt]
+
+
+def pd_summin_list(ctx: Ctx, prof: Profiles, a, b, s=None, den=None):
+    """Sum-min and sum-max (Eq. (5)) of the gene pairs (a[i], b[i]) by merging
+    their sorted multiplicity vectors.  a, b: uint32 global gene ids (host
+    arrays or device tensors).  Without output buffers returns host arrays
+    (s uint32, den uint32); with them (host or device, n entries) returns None."""
+    n = int(a.shape[0])
+    if int(b.shape[0]) != n:
+        raise ValueError("pd_summin_list: a and b must have the same length")
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.uint32)
+    if isinstance(b, np.ndarray):
+        b = np.ascontiguousarray(b, dtype=np.uint32)
+    ret = s is None and den is None
+    if ret:
+        s = np.zeros(max(n, 1), np.uint32)
+        den = np.zeros(max(n, 1), np.uint32)
+    _check(ctx, _lib.pd_summin_list(ctx.handle, prof.handle, _ptr(a) if n else None, _ptr(b) if n else None, n,
+                                    _ptr(s), _ptr(den)), "pd_summin_list")
+    if ret:
+        return s[:n], den[:n]
+    return None
 
 
 def pd_best_hits_noalloc(ctx: Ctx, prof: Profiles, gi: int, gj: int, row_ptr, cols, s) -> int:
