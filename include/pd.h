@@ -206,6 +206,16 @@ void pd_profiles_free(pd_profiles* prof);
  * target genome because global ids are contiguous per genome, and ascending. */
 pd_status pd_best_hits_all(pd_ctx* ctx, const pd_profiles* prof, pd_hits** out);
 
+/* How pd_best_hits_all covers the genome pairs (no counterpart in the paper;
+ * the results are identical either way).  enable != 0 (the default): the
+ * similarity is symmetric (Eq. (5)), so each unordered genome pair is walked
+ * from one side -- a query gene walks only the genomes after its own, emits
+ * its Best Hits there and keeps, for every target, the best ratio over the
+ * query's genome (the reverse direction, the column maximum of Algorithm 3);
+ * used while genes x genomes x 8 bytes stay within 4 GiB.  enable == 0: every
+ * query walks every other genome.  Errors: PD_ERR_ARG (null context). */
+pd_status pd_ctx_set_symmetric(pd_ctx* ctx, int enable);
+
 /* One shard of pd_best_hits_all, for splitting one dataset's all-against-all
  * work across processes or GPUs that each hold the same profiles.  The paper
  * decomposes phase (b) by data, one query gene (a row of Algorithm 2) being

@@ -190,6 +190,36 @@ __device__ __forceinline__ void best_update(unsigned long long* slot, uint32_t s
   }
 }
 
+// Reverse-direction maximum of the symmetric form: the best (s, den) of
+// target b over the query genome, with the query gene a that reaches it,
+// packed s << 48 | den << 31 | a (s < 2^16, den < 2^17, a < 2^31); a pair
+// that equals the stored maximum is listed as a tie (b << 32 | a, s).  Ties of
+// a maximum later beaten stay in the list and are dropped when the rows are
+// assembled.
+__device__ __forceinline__ void sym_update(const QuerySet& Q, unsigned long long* slot, uint32_t b, uint32_t a,
+                                           uint32_t s, uint32_t den) {
+  const unsigned long long mine =
+      ((unsigned long long)s << 48) | ((unsigned long long)den << 31) | (unsigned long long)a;
+  unsigned long long old = *((volatile unsigned long long*)slot);
+  while (true) {
+    if (old != 0ull) {
+      const uint32_t os = (uint32_t)(old >> 48), od = (uint32_t)(old >> 31) & 0x1FFFFu;
+      if (ratio_greater(os, od, s, den)) return;
+      if (ratio_equal(os, od, s, den)) {
+        const unsigned long long t = atomicAdd(Q.tie_count, 1ull);
+        if (t < Q.tie_cap) {
+          Q.tie_rec[2 * t] = ((unsigned long long)b << 32) | a;
+          Q.tie_rec[2 * t + 1] = s;
+        }
+        return;
+      }
+    }
+    const unsigned long long prev = atomicCAS(slot, old, mine);
+    if (prev == old) return;
+    old = prev;
+  }
+}
+
 template <int kThreads>
 struct Chunk {
   static constexpr uint32_t kSize = 2 * kThreads;  // query k-mers staged per round
@@ -254,6 +284,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
       own1 = (uint32_t)P.genome_ptr[gg + 1];
       if (Q.tgt_end) tend = Q.tgt_end[gg];
       col = gg - Q.col_genome0;
+      if (Q.symbest) key_lo = (unsigned long long)own1 << P.cnt_bits;  // first posting past a's genome
     }
   } else {
     uint32_t tlo, thi;
@@ -328,6 +359,8 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
           if (!Q.all_pairs) {
             lo = lower_bound_post(P.post, lo, hi, key_lo);
             hi = lower_bound_post(P.post, lo, hi, key_hi);
+          } else if (Q.symbest) {
+            lo = lower_bound_post(P.post, lo, hi, key_lo);  // the genomes after the query's own
           }
           len = hi - lo;
         }
@@ -407,6 +440,8 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
           if (!Q.all_pairs) {
             lo = lower_bound_post(P.post, lo, hi, key_lo);
             hi = lower_bound_post(P.post, lo, hi, key_hi);
+          } else if (Q.symbest) {
+            lo = lower_bound_post(P.post, lo, hi, key_lo);  // the genomes after the query's own
           }
           c_post[e] = lo;
           c_cnt[e] = q_mv_cnt[m0 + c0 + e];
@@ -520,6 +555,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
         const uint32_t den = La_a + (gi & 0xFFFFu) - s;
         best_update(&best[Q.all_pairs ? (gi >> 16) : 0u], s, den);
         if (Q.colbest) best_update(&Q.colbest[(size_t)b * Q.col_stride + col], s, den);
+        if (Q.symbest) sym_update(Q, &Q.symbest[(size_t)b * P.n_genomes + col], b, a, s, den);
       }
       __syncthreads();
       for (uint32_t u = tid; u < n_occ; u += kThreads) {

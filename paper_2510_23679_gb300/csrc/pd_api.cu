@@ -170,6 +170,12 @@ PD_API const char* pd_last_error(const pd_ctx* c) { return c ? c->err.c_str() : 
 
 PD_API uint64_t pd_ctx_launch_count(const pd_ctx* c) { return c ? c->launches : 0; }
 
+PD_API pd_status pd_ctx_set_symmetric(pd_ctx* c, int enable) {
+  if (!c) return PD_ERR_ARG;
+  c->symmetric = enable != 0;
+  return PD_OK;
+}
+
 PD_API pd_status pd_ctx_set_timing(pd_ctx* c, int enable) {
   if (!c) return PD_ERR_ARG;
   c->timing = enable != 0;
@@ -707,6 +713,10 @@ static pd_status run_hits_on(pd_ctx* c, const pdg::ProfilesView& v, const pdg::Q
     ALLOC(H->out_s, sizeof(uint32_t) * cap);
     CK(cudaMemsetAsync(counters.p, 0, 4 * sizeof(unsigned long long), c->stream));
     CK(cudaMemsetAsync(H->row_len.p, 0, sizeof(uint32_t) * std::max<uint32_t>(n_rows, 1), c->stream));
+    if (Q.symbest) {  // a rerun starts the reverse maxima and their tie list afresh
+      CK(cudaMemsetAsync(Q.symbest, 0, sizeof(unsigned long long) * v.n_genes * v.n_genomes, c->stream));
+      CK(cudaMemsetAsync(Q.tie_count, 0, sizeof(unsigned long long), c->stream));
+    }
     unsigned long long* cnt = counters.as<unsigned long long>();
     pdg::HitsOut O;
     O.out_b = H->out_b.as<uint32_t>();
@@ -884,6 +894,106 @@ static pd_status hits_pair_impl(pd_ctx* c, const pd_profiles* P, uint32_t gi, ui
   return run_hits(c, P, Q, emit_all, H);
 }
 
+// Largest reverse-maximum table (genes x genomes x 8 B) of the symmetric form.
+constexpr unsigned long long kSymMaxBytes = 4ull << 30;
+
+// The symmetric all-pairs form (k_sym.cu): each unordered genome pair is
+// walked from one side; the launch emits the forward Best Hits and keeps the
+// reverse maxima, and the rows are assembled from both.
+static pd_status sym_hits_impl(pd_ctx* c, const pd_profiles* P, pd_hits* H) {
+  const pdg::ProfilesView& v = P->view;
+  pdg::Launcher* L = &c->L;
+  const uint32_t G = v.n_genes, NG = v.n_genomes;
+  const unsigned long long sym_bytes = 8ull * G * NG;
+  unsigned long long tie_cap = std::max<unsigned long long>(G, 1ull << 16);
+  Buf symbest, ties, tcount;
+  ALLOC(symbest, sym_bytes);
+  ALLOC(tcount, sizeof(unsigned long long));
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    ALLOC(ties, 2 * sizeof(unsigned long long) * tie_cap);
+    pdg::QuerySet Q{};  // run_hits clears the maxima and the tie count before each launch
+    Q.all_pairs = 1;
+    Q.order = v.order;
+    Q.q0 = 0;
+    Q.n_queries = G;
+    Q.symbest = symbest.as<unsigned long long>();
+    Q.tie_rec = ties.as<unsigned long long>();
+    Q.tie_count = tcount.as<unsigned long long>();
+    Q.tie_cap = tie_cap;
+    pd_hits F;
+    F.ctx = c;
+    F.all_pairs = 1;
+    pd_status st = run_hits(c, P, Q, false, &F);  // forward rows (genomes after each query's own)
+    if (st != PD_OK) return st;
+    unsigned long long n_ties = 0;
+    CK(cudaMemcpyAsync(&n_ties, tcount.p, sizeof(n_ties), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_ties > tie_cap) {  // more exact ties than the list held: run again with room for all
+      tie_cap = n_ties + 4096;
+      continue;
+    }
+    // a query handed to the next tier after its Best Hit passes records its
+    // ties twice: a set keeps the first record of each pair
+    Buf tie_set;
+    const unsigned long long set_slots = pdg::next_pow2((uint32_t)std::min<unsigned long long>(
+        std::max<unsigned long long>(2 * n_ties, 2), 1ull << 31));
+    ALLOC(tie_set, sizeof(unsigned long long) * set_slots);
+    CK(cudaMemsetAsync(tie_set.p, 0xFF, sizeof(unsigned long long) * set_slots, c->stream));
+    pdg::SymRows R{G, NG, v.gene_genome, v.La, symbest.as<unsigned long long>(), ties.as<unsigned long long>(),
+                   n_ties, tie_set.as<unsigned long long>(), set_slots - 1, F.row_off.as<unsigned long long>(),
+                   F.row_len.as<uint32_t>(), F.out_b.as<uint32_t>(), F.out_s.as<uint32_t>()};
+    Buf stored, tiecnt, tie_ok, total, row_ptr, tmp, tie_fill;
+    const size_t G1 = std::max<uint32_t>(G, 1);
+    ALLOC(stored, sizeof(uint32_t) * G1);
+    ALLOC(tiecnt, sizeof(uint32_t) * G1);
+    ALLOC(tie_fill, sizeof(uint32_t) * G1);
+    ALLOC(tie_ok, std::max<unsigned long long>(n_ties, 1));
+    ALLOC(total, sizeof(uint32_t) * G1);
+    ALLOC(row_ptr, sizeof(unsigned long long) * (G + 1));
+    ALLOC(tmp, pdg::scan_temp_bytes(G + 1) + 64);
+    CK(cudaMemsetAsync(tiecnt.p, 0, sizeof(uint32_t) * G1, c->stream));
+    CK(cudaMemsetAsync(tie_fill.p, 0, sizeof(uint32_t) * G1, c->stream));
+    CK(pdg::run_sym_count(L, R, stored.as<uint32_t>(), tiecnt.as<uint32_t>(), tie_ok.as<uint8_t>(),
+                          total.as<uint32_t>(), c->stream));
+    CK(pdg::scan_u32_to_u64(L, total.as<uint32_t>(), G, row_ptr.as<unsigned long long>(), tmp.p, c->stream));
+    unsigned long long n = 0;
+    CK(cudaMemcpyAsync(&n, row_ptr.as<unsigned long long>() + G, sizeof(n), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    ALLOC(H->out_b, sizeof(uint32_t) * std::max<unsigned long long>(n, 1));
+    ALLOC(H->out_s, sizeof(uint32_t) * std::max<unsigned long long>(n, 1));
+    CK(pdg::run_sym_write(L, R, stored.as<uint32_t>(), tiecnt.as<uint32_t>(), tie_ok.as<uint8_t>(),
+                          row_ptr.as<unsigned long long>(), tie_fill.as<uint32_t>(), H->out_b.as<uint32_t>(),
+                          H->out_s.as<uint32_t>(), c->stream));
+    // BBH while the reverse maxima are at hand
+    Buf flag, bcnt, bstart;
+    ALLOC(flag, std::max<unsigned long long>(F.out_b.n / sizeof(uint32_t), 1));
+    ALLOC(bcnt, sizeof(uint32_t) * G1);
+    ALLOC(bstart, sizeof(uint32_t) * (G + 1));
+    CK(pdg::run_sym_bbh_count(L, R, flag.as<uint8_t>(), bcnt.as<uint32_t>(), bstart.as<uint32_t>(), tmp.p,
+                              c->stream));
+    uint32_t n_bbh = 0;
+    CK(cudaMemcpyAsync(&n_bbh, bstart.as<uint32_t>() + G, sizeof(n_bbh), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    ALLOC(H->bbh_a, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
+    ALLOC(H->bbh_b, sizeof(int32_t) * std::max<uint32_t>(n_bbh, 1));
+    if (n_bbh)
+      CK(pdg::run_sym_bbh_write(L, R, flag.as<uint8_t>(), bstart.as<uint32_t>(), H->bbh_a.as<int32_t>(),
+                                H->bbh_b.as<int32_t>(), c->stream));
+    st = check_dev_err(c);  // synchronizes: the forward rows and the tables end here
+    if (st != PD_OK) return st;
+    H->has_bbh = true;
+    H->n_bbh = n_bbh;
+    H->row_off = std::move(row_ptr);
+    H->row_len = std::move(total);
+    H->n_rows = G;
+    H->n_hits = n;
+    H->walked = F.walked;
+    H->n_deferred = F.n_deferred;
+    return PD_OK;
+  }
+  return fail(c, PD_ERR_INTERNAL, "symmetric Best Hits: the tie list did not converge");
+}
+
 PD_API pd_status pd_best_hits_all(pd_ctx* c, const pd_profiles* P, pd_hits** out) {
   PhaseRange range_("pd: best hits");
   if (!c || !P || !out) return PD_ERR_ARG;
@@ -893,6 +1003,13 @@ PD_API pd_status pd_best_hits_all(pd_ctx* c, const pd_profiles* P, pd_hits** out
     std::unique_ptr<pd_hits> H(new pd_hits());
     H->ctx = c;
     H->all_pairs = 1;
+    const uint32_t G = P->view.n_genes, NG = P->view.n_genomes;
+    if (c->symmetric && G > 0 && NG >= 2 && 8ull * G * NG <= kSymMaxBytes) {
+      pd_status st = sym_hits_impl(c, P, H.get());
+      if (st != PD_OK) return st;
+      *out = H.release();
+      return PD_OK;
+    }
     pdg::QuerySet Q{};
     Q.all_pairs = 1;
     Q.order = P->view.order;
@@ -1157,6 +1274,20 @@ PD_API pd_status pd_bbh_all(pd_ctx* c, const pd_profiles* P, const pd_hits* H, p
   if (!H->all_pairs || H->paralog) return fail(c, PD_ERR_ARG, "pd_bbh_all needs the result of pd_best_hits_all");
   try {
     CK(cudaSetDevice(c->device));
+    if (H->has_bbh) {  // found with the rows (the symmetric form)
+      std::unique_ptr<pd_bbh_set> S(new pd_bbh_set());
+      S->ctx = c;
+      S->n = H->n_bbh;
+      ALLOC(S->a, sizeof(int32_t) * std::max<uint64_t>(H->n_bbh, 1));
+      ALLOC(S->b, sizeof(int32_t) * std::max<uint64_t>(H->n_bbh, 1));
+      if (H->n_bbh) {
+        CK(cudaMemcpyAsync(S->a.p, H->bbh_a.p, sizeof(int32_t) * H->n_bbh, cudaMemcpyDeviceToDevice, c->stream));
+        CK(cudaMemcpyAsync(S->b.p, H->bbh_b.p, sizeof(int32_t) * H->n_bbh, cudaMemcpyDeviceToDevice, c->stream));
+      }
+      CK(cudaStreamSynchronize(c->stream));
+      *out = S.release();
+      return PD_OK;
+    }
     pdg::BbhRows R{};
     R.all_pairs = 1;
     R.n_rows = H->n_rows;

@@ -53,6 +53,7 @@ struct pd_ctx {
   std::string err;
   uint64_t launches = 0;
   bool timing = false;
+  bool symmetric = true;  // pd_best_hits_all walks each genome pair from one side (pd_ctx_set_symmetric)
   std::string timing_filter;  // empty: time every kernel; else only launches of this name
   std::vector<PendingTiming> pending;
   std::vector<cudaEvent_t> event_pool;
@@ -222,6 +223,10 @@ struct pd_hits {
   uint64_t n_hits = 0, walked = 0;
   uint32_t n_deferred = 0;
   Buf row_off, row_len, out_b, out_s;
+  // the symmetric all-pairs form finds the BBH pairs with the rows
+  bool has_bbh = false;
+  uint64_t n_bbh = 0;
+  Buf bbh_a, bbh_b;
 };
 
 struct pd_bbh_set {

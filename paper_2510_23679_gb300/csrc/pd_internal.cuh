@@ -186,6 +186,17 @@ struct QuerySet {
   // g mod n_shards == shard are computed (the others are skipped before any
   // work), so the shards partition the genes whatever the query order.
   uint32_t n_shards, shard;
+  // Symmetric all-pairs form (symbest not null): each unordered genome pair is
+  // walked from one side.  Query a walks only the targets in genomes after its
+  // own; for every candidate b it keeps the best (s, den, a) of b over a's
+  // genome at symbest[b * n_genomes + genome(a)] -- the reverse-direction
+  // maximum, packed s << 48 | den << 31 | a -- and lists exact ties of that
+  // maximum as the pair of words (b << 32 | a, s) in tie_rec (tie_cap pairs;
+  // the count keeps counting past it).
+  unsigned long long* symbest;
+  unsigned long long* tie_rec;
+  unsigned long long* tie_count;
+  unsigned long long tie_cap;
   uint32_t qa0, nA, ta0, ta1;
   uint32_t qb0, tb0, tb1;
   // Served queries (all-pairs form; null = off).  tgt_end[genome of the
@@ -347,6 +358,40 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
 size_t summin_global_smem_bytes(uint32_t n_genomes);
 cudaError_t run_summin_global(Launcher* L, const ProfilesView& P, const QuerySet& Q, const HitsOut& O,
                               const BigScratch& B, uint32_t n_ctas, DevErr* err, bool emit_all, cudaStream_t s);
+
+// Symmetric all-pairs form (k_sym.cu): rows = the reverse part (from symbest
+// and the valid ties, ascending) followed by the forward part of the launch.
+struct SymRows {
+  uint32_t n_genes, n_genomes;
+  const uint16_t* gene_genome;
+  const uint32_t* La;
+  const unsigned long long* symbest;  // [n_genes * n_genomes]
+  const unsigned long long* tie_rec;  // [2 * n_ties]: (b << 32 | a), s
+  unsigned long long n_ties;
+  unsigned long long* tie_set;        // [tie_set_mask + 1] all-ones: the pairs already counted
+  unsigned long long tie_set_mask;
+  const unsigned long long* fwd_off;  // forward rows of the launch
+  const uint32_t* fwd_len;
+  const uint32_t* fwd_b;
+  const uint32_t* fwd_s;
+};
+// Per gene: stored maxima (stored), valid ties (tiecnt, must start at zero;
+// tie_ok flags each tie) and the row length (total).
+cudaError_t run_sym_count(Launcher* L, const SymRows& R, uint32_t* stored, uint32_t* tiecnt, uint8_t* tie_ok,
+                          uint32_t* total, cudaStream_t s);
+// Rows written at row_ptr (exclusive scan of total); tie_fill must start at zero.
+cudaError_t run_sym_write(Launcher* L, const SymRows& R, const uint32_t* stored, const uint32_t* tiecnt,
+                          const uint8_t* tie_ok, const unsigned long long* row_ptr, uint32_t* tie_fill,
+                          uint32_t* out_b, uint32_t* out_s, cudaStream_t s);
+
+// BBH of the symmetric form: a forward hit is a BBH when its ratio equals the
+// target's stored maximum over the query genome.  count: flags per forward
+// hit, per-row counts and their exclusive scan (start[n_genes] = pairs);
+// write: the pairs (a, b) ascending.
+cudaError_t run_sym_bbh_count(Launcher* L, const SymRows& R, uint8_t* flag, uint32_t* cnt, uint32_t* start,
+                              void* scan_tmp, cudaStream_t s);
+cudaError_t run_sym_bbh_write(Launcher* L, const SymRows& R, const uint8_t* flag, const uint32_t* start, int32_t* pa,
+                              int32_t* pb, cudaStream_t s);
 
 // BBH and result gathering (k_bbh.cu)
 cudaError_t run_gather_rows(Launcher* L, uint32_t n_rows, const unsigned long long* row_off,

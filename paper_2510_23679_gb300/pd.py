@@ -141,6 +141,7 @@ _SIGNATURES = [
     ("pd_profiles_genome_ptr", C.c_int, [_P, _P]),
     ("pd_best_hits_shard", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _PP]),
     ("pd_summin_list", C.c_int, [_P, _P, _P, _P, C.c_uint64, _P, _P]),
+    ("pd_ctx_set_symmetric", C.c_int, [_P, C.c_int]),
     ("pd_hits_import", C.c_int, [_P, _P, C.c_uint32, _P, _P, _P, _P, _PP]),
     ("pd_index_genome_ptr", C.c_int, [_P, C.c_uint32, _P]),
     ("pd_index_free", None, [_P]),
@@ -297,6 +298,12 @@ def pd_ctx_launch_count(ctx: Ctx) -> int:
 
 def pd_ctx_set_timing(ctx: Ctx, enable: bool) -> None:
     _check(ctx, _lib.pd_ctx_set_timing(ctx.handle, int(bool(enable))), "pd_ctx_set_timing")
+
+
+def pd_ctx_set_symmetric(ctx: Ctx, enable: bool) -> None:
+    """pd_best_hits_all walks each genome pair from one side (True, the
+    default) or every genome from every query (False); same results."""
+    _check(ctx, _lib.pd_ctx_set_symmetric(ctx.handle, 1 if enable else 0), "pd_ctx_set_symmetric")
 
 
 def pd_ctx_set_timing_filter(ctx: Ctx, name: str | None) -> None:
