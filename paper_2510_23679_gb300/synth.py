@@ -289,6 +289,14 @@ WORKLOADS = {
                         length_dist=("lognormal", 300, 0.5, 30, 2500), core_frac=0.25,
                         accessory_draw=None, subst_max=0.30, indel_max=0.05, paralog_frac=0.10,
                         singleton_frac=0.05, seed=3),
+    # The pan200x4000 model at a quarter of the genes (Poisson(1000) genes per
+    # genome, 3000 families): the same 200 genomes and k = 7, so posting lists
+    # of the same lengths and the same walk, in a case small enough for
+    # counter captures.
+    "pan200x1000": dict(n_genomes=200, genes_per_genome=("poisson", 1000), n_families=3000,
+                        length_dist=("lognormal", 300, 0.5, 30, 2500), core_frac=0.25,
+                        accessory_draw=None, subst_max=0.30, indel_max=0.05, paralog_frac=0.10,
+                        singleton_frac=0.05, seed=7),
     # Nucleotide stand-in: 8 genomes x Poisson(600) genes, gene lengths
     # log-normal with median 900 nt (300 codons), clipped to 90..7500, ACGT at
     # 50% GC, the pan50x3000 mutation model.
