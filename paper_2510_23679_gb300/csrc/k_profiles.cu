@@ -4,15 +4,18 @@
 // Steps (one launch each):
 //   encode_mark    letter -> 0..|G|-1 (|G| = 20 amino acids or 4
 //                  nucleotides), base-|G| code of every window (Eq. (1):
-//                  windows of exactly k letters), one bit per code in a bitmap
-//                  over all |G|^k codes; letters outside the alphabet raise
-//                  PD_ERR_ALPHABET.  Segmented datasets (independent problems
-//                  profiled together) give each segment its own 20^k range of
-//                  the bitmap, code + segment * 20^k, so k-mers of different
-//                  segments get different ids and never meet in a posting list.
-//   (scan)         popcount prefix of the bitmap words: the dense id of a code
-//                  is its rank among the codes present (an injective f that is
-//                  ascending with the code, "Multiplicity vector building").
+//                  windows of exactly k letters), one bit per code in the
+//                  dictionary's bit array over all |G|^k codes; letters
+//                  outside the alphabet raise PD_ERR_ALPHABET.  Segmented
+//                  datasets (independent problems profiled together) give each
+//                  segment its own 20^k range of codes, code + segment * 20^k,
+//                  so k-mers of different segments get different ids and never
+//                  meet in a posting list.
+//   (scan)         popcount prefix over the dictionary's 32-byte rank blocks
+//                  (224 codes each): the dense id of a code is its rank among
+//                  the codes present (an injective f that is ascending with
+//                  the code, "Multiplicity vector building"), found with one
+//                  sector read.
 //   mv_build       per gene: ids of its windows counted in a shared-memory
 //                  hash table, compacted into (id, multiplicity) pairs (Eqs.
 //                  (2)-(3)), one index record per pair; also a min-hash.
@@ -52,7 +55,7 @@ __device__ __forceinline__ uint32_t mix32(uint32_t x) {
 // ------------------------------------------------------------ encode_mark
 __global__ void __launch_bounds__(kEncThreads)
     k_encode_mark(const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr, uint32_t n_genes, int k,
-                  unsigned long long* __restrict__ bitmap, const uint16_t* __restrict__ gene_genome,
+                  uint32_t* __restrict__ dict, const uint16_t* __restrict__ gene_genome,
                   const unsigned long long* __restrict__ genome_code_base, const int64_t* __restrict__ gene_src,
                   int alpha, uint64_t n_res, DevErr* err) {
   __shared__ uint8_t lut[256];
@@ -100,8 +103,10 @@ __global__ void __launch_bounds__(kEncThreads)
         }
         code = code * a + c;
         if (last_bad < (int64_t)p) {
-          const unsigned long long key = code + base;
-          atomicOr(&bitmap[key >> 6], 1ull << (key & 63u));
+          unsigned long long blk;
+          uint32_t w, bit;
+          dict_locate(code + base, &blk, &w, &bit);
+          atomicOr(&dict[blk * 8 + w], 1u << bit);
         }
         uint32_t lead = lut[s[p]];
         code -= (unsigned long long)(lead < (uint32_t)alpha ? lead : 0u) * lead_w;
@@ -149,13 +154,6 @@ __global__ void k_narrow_u64(const unsigned long long* __restrict__ in, uint64_t
 }
 
 // ------------------------------------------------------------ mv_build
-__device__ __forceinline__ uint32_t code_rank(unsigned long long code, const unsigned long long* __restrict__ bitmap,
-                                              const uint32_t* __restrict__ word_rank) {
-  const unsigned long long w = bitmap[code >> 6];
-  const unsigned long long below = (1ull << (code & 63u)) - 1ull;
-  return word_rank[code >> 6] + (uint32_t)__popcll(w & below);
-}
-
 // Multiplicity vector of gene g (Eqs. (2)-(3)): the dense ids of its windows
 // are counted in an open-addressing table of 64-bit slots (id << 32 | count)
 // of `cap` slots (a power of two, at least 1.5 x La), then the occupied slots
@@ -169,8 +167,7 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
                                              const uint8_t* __restrict__ lut, uint32_t* warp_tmp,
                                              const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr,
                                              const uint32_t* __restrict__ win_off, int k,
-                                             const unsigned long long* __restrict__ bitmap,
-                                             const uint32_t* __restrict__ word_rank, const MvOut& M) {
+                                             const uint32_t* __restrict__ dict, const MvOut& M) {
   constexpr unsigned long long kFree = ~0ull;
   const uint32_t off = win_off[g];
   const uint32_t La = win_off[g + 1] - off;
@@ -184,8 +181,8 @@ __device__ __forceinline__ void mv_build_one(uint32_t g, unsigned long long* tab
       const uint32_t c = lut[s[p + t]];
       code = code * (unsigned long long)M.alpha + (c < (uint32_t)M.alpha ? c : 0u);
     }
-    if (M.frozen && !((bitmap[(code + base) >> 6] >> ((code + base) & 63u)) & 1ull)) continue;  // not in that dictionary
-    const uint32_t id = code_rank(code + base, bitmap, word_rank);
+    if (M.frozen && !dict_has(dict, code + base)) continue;  // not in that dictionary
+    const uint32_t id = dict_rank(dict, code + base);
     uint32_t h = mix32(id) & (cap - 1u);
     uint32_t probe = 0;
     for (; probe < cap; ++probe) {  // a free slot always exists: cap > La >= distinct ids
@@ -253,7 +250,7 @@ template <int kThreads>
 __global__ void __launch_bounds__(kThreads)
     k_mv_build_smem(const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr,
                     const uint32_t* __restrict__ win_off, uint32_t n_genes, int k,
-                    const unsigned long long* __restrict__ bitmap, const uint32_t* __restrict__ word_rank, MvOut M,
+                    const uint32_t* __restrict__ dict, MvOut M,
                     uint32_t max_cap, const uint32_t* __restrict__ list, uint32_t n_list) {
   extern __shared__ unsigned long long table[];
   __shared__ uint8_t lut[256];
@@ -264,15 +261,15 @@ __global__ void __launch_bounds__(kThreads)
     const uint32_t g = list ? list[x] : x;
     const uint32_t cap = mv_table_cap(win_off[g + 1] - win_off[g]);
     if (cap > max_cap) continue;  // uniform over the block: built by a later launch
-    mv_build_one(g, table, cap, lut, warp_tmp, res, gene_ptr, win_off, k, bitmap, word_rank, M);
+    mv_build_one(g, table, cap, lut, warp_tmp, res, gene_ptr, win_off, k, dict, M);
   }
 }
 
 // Genes too long for shared memory: tables in global scratch (one per gene).
 __global__ void __launch_bounds__(kMvLongThreads)
     k_mv_build_long(const uint8_t* __restrict__ res, const int64_t* __restrict__ gene_ptr,
-                    const uint32_t* __restrict__ win_off, int k, const unsigned long long* __restrict__ bitmap,
-                    const uint32_t* __restrict__ word_rank, MvOut M, const uint32_t* __restrict__ long_genes,
+                    const uint32_t* __restrict__ win_off, int k, const uint32_t* __restrict__ dict, MvOut M,
+                    const uint32_t* __restrict__ long_genes,
                     uint32_t n_long, unsigned long long* scratch, const unsigned long long* __restrict__ scratch_off) {
   __shared__ uint8_t lut[256];
   __shared__ uint32_t warp_tmp[kMvLongThreads / 32 + 1];
@@ -280,7 +277,7 @@ __global__ void __launch_bounds__(kMvLongThreads)
   for (uint32_t x = blockIdx.x; x < n_long; x += gridDim.x) {
     const uint32_t g = long_genes[x];
     mv_build_one(g, scratch + scratch_off[x], mv_table_cap(win_off[g + 1] - win_off[g]), lut, warp_tmp, res,
-                 gene_ptr, win_off, k, bitmap, word_rank, M);
+                 gene_ptr, win_off, k, dict, M);
   }
 }
 
@@ -356,16 +353,19 @@ __global__ void k_gene_info(const int32_t* __restrict__ genome_ptr, uint32_t n_g
     }
 }
 
-__global__ void k_select_codes(const unsigned long long* __restrict__ bitmap, const uint32_t* __restrict__ word_rank,
-                               uint64_t n_words, unsigned long long* __restrict__ code_of_id) {
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_words;
+// Code of every dense id: the set bits of each dictionary block, in order.
+__global__ void k_select_codes(const uint32_t* __restrict__ dict, uint64_t n_blocks,
+                               unsigned long long* __restrict__ code_of_id) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_blocks;
        i += (uint64_t)gridDim.x * blockDim.x) {
-    unsigned long long w = bitmap[i];
-    uint32_t id = word_rank[i];
-    while (w) {
-      const int bit = __ffsll((long long)w) - 1;
-      code_of_id[id++] = i * 64ull + (unsigned long long)bit;
-      w &= w - 1ull;
+    uint32_t id = dict[i * 8];
+    for (uint32_t w = 1; w < 8; ++w) {
+      uint32_t bits = dict[i * 8 + w];
+      while (bits) {
+        const int bit = __ffs((int)bits) - 1;
+        code_of_id[id++] = i * kDictBits + (w - 1u) * 32u + (unsigned long long)bit;
+        bits &= bits - 1u;
+      }
     }
   }
 }
@@ -453,11 +453,11 @@ unsigned grid_for(uint64_t items, unsigned per_block, unsigned cap) {
   } while (0)
 
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
-                            unsigned long long* bitmap, const uint16_t* gene_genome,
+                            uint32_t* dict, const uint16_t* gene_genome,
                             const unsigned long long* genome_code_base, const int64_t* gene_src, int alpha,
                             uint64_t n_res, DevErr* err, cudaStream_t s) {
   const unsigned grid = grid_for((uint64_t)n_genes * 32, kEncThreads, 152u * 16u);
-  PD_LAUNCH(L, "encode_mark", k_encode_mark<<<grid, kEncThreads, 0, s>>>(res, gene_ptr, n_genes, k, bitmap,
+  PD_LAUNCH(L, "encode_mark", k_encode_mark<<<grid, kEncThreads, 0, s>>>(res, gene_ptr, n_genes, k, dict,
                                                                         gene_genome, genome_code_base, gene_src,
                                                                         alpha, n_res, err));
   return cudaSuccess;
@@ -480,8 +480,7 @@ cudaError_t run_narrow_u64(Launcher* L, const unsigned long long* in, uint64_t n
 }
 
 cudaError_t run_mv_build(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, const uint32_t* win_off,
-                         uint32_t n_genes, int k, const unsigned long long* bitmap, const uint32_t* word_rank,
-                         const MvOut& M, const uint32_t* mid_genes, uint32_t n_mid, const uint32_t* long_genes,
+                         uint32_t n_genes, int k, const uint32_t* dict, const MvOut& M, const uint32_t* mid_genes, uint32_t n_mid, const uint32_t* long_genes,
                          uint32_t n_long, unsigned long long* long_scratch, const unsigned long long* long_scratch_off,
                          cudaStream_t s) {
   const size_t smem1 = (size_t)kMvSmallCap * 8, smem2 = (size_t)kMvMidCap * 8;
@@ -492,16 +491,16 @@ cudaError_t run_mv_build(Launcher* L, const uint8_t* res, const int64_t* gene_pt
   if (ea != cudaSuccess) return ea;
   PD_LAUNCH(L, "mv_build",
             k_mv_build_smem<kMvThreads><<<grid_for(n_genes, 1, 152u * 64u), kMvThreads, smem1, s>>>(
-                res, gene_ptr, win_off, n_genes, k, bitmap, word_rank, M, kMvSmallCap, nullptr, 0u));
+                res, gene_ptr, win_off, n_genes, k, dict, M, kMvSmallCap, nullptr, 0u));
   if (n_mid) {
     PD_LAUNCH(L, "mv_build_mid",
               k_mv_build_smem<kMvLongThreads><<<grid_for(n_mid, 1, 152u), kMvLongThreads, smem2, s>>>(
-                  res, gene_ptr, win_off, n_genes, k, bitmap, word_rank, M, kMvMidCap, mid_genes, n_mid));
+                  res, gene_ptr, win_off, n_genes, k, dict, M, kMvMidCap, mid_genes, n_mid));
   }
   if (n_long) {
     PD_LAUNCH(L, "mv_build_long",
               k_mv_build_long<<<grid_for(n_long, 1, 152u), kMvLongThreads, 0, s>>>(
-                  res, gene_ptr, win_off, k, bitmap, word_rank, M, long_genes, n_long, long_scratch,
+                  res, gene_ptr, win_off, k, dict, M, long_genes, n_long, long_scratch,
                   long_scratch_off));
   }
   return cudaSuccess;
@@ -539,11 +538,10 @@ cudaError_t run_gene_info(Launcher* L, const int32_t* genome_ptr, uint32_t n_gen
   return cudaSuccess;
 }
 
-cudaError_t run_select_codes(Launcher* L, const unsigned long long* bitmap, const uint32_t* word_rank,
-                             uint64_t n_words, unsigned long long* code_of_id, cudaStream_t s) {
+cudaError_t run_select_codes(Launcher* L, const uint32_t* dict, uint64_t n_blocks, unsigned long long* code_of_id,
+                             cudaStream_t s) {
   PD_LAUNCH(L, "select_codes",
-            k_select_codes<<<grid_for(n_words, 256, 152u * 16u), 256, 0, s>>>(bitmap, word_rank, n_words,
-                                                                               code_of_id));
+            k_select_codes<<<grid_for(n_blocks, 256, 152u * 16u), 256, 0, s>>>(dict, n_blocks, code_of_id));
   return cudaSuccess;
 }
 

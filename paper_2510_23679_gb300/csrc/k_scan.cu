@@ -1,6 +1,6 @@
 // k_scan.cu -- device-wide exclusive prefix sums (reduce, spine, down-sweep).
 //
-// Used for: ranks of the k-mer bitmap words (dense ids), posting-list offsets
+// Used for: rank bases of the k-mer dictionary blocks (dense ids), posting-list offsets
 // from per-id counts, and Best Hit / BBH row offsets.  Three launches: each
 // tile of kTile elements is reduced, the tile sums are scanned by one block,
 // and each tile is rescanned with its offset.  Loads are striped over the
@@ -45,9 +45,16 @@ __device__ __forceinline__ unsigned long long block_excl_u64(unsigned long long 
   return r;
 }
 
-struct PopcIn {
-  const unsigned long long* w;
-  __device__ __forceinline__ unsigned long long operator()(uint64_t i) const { return (unsigned long long)__popcll(w[i]); }
+// Set bits of dictionary block i (its words 1..7; word 0 receives the scan).
+struct DictIn {
+  const uint32_t* d;
+  __device__ __forceinline__ unsigned long long operator()(uint64_t i) const {
+    const uint32_t* b = d + i * 8;
+    uint32_t n = 0;
+#pragma unroll
+    for (int w = 1; w < 8; ++w) n += (uint32_t)__popc(b[w]);
+    return n;
+  }
 };
 struct U32In {
   const uint32_t* a;
@@ -88,7 +95,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_spine(unsigned long long* par
 template <typename In, typename Out>
 __global__ void __launch_bounds__(kThreads) k_scan_down(In in, uint64_t n, const unsigned long long* partial,
                                                         const unsigned long long* total, Out* out,
-                                                        int write_last) {
+                                                        int write_last, uint32_t stride) {
   __shared__ unsigned long long tmp[kThreads / 32 + 1];
   const uint64_t base = (uint64_t)blockIdx.x * kTile;
   unsigned long long carry = partial[blockIdx.x];
@@ -98,10 +105,10 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(In in, uint64_t n, const
     unsigned long long v = (i < n) ? in(i) : 0ull;
     unsigned long long tot;
     unsigned long long ex = block_excl_u64(v, tmp, &tot);
-    if (i < n) out[i] = (Out)(carry + ex);
+    if (i < n) out[i * stride] = (Out)(carry + ex);
     carry += tot;
   }
-  if (write_last && blockIdx.x == 0 && threadIdx.x == 0) out[n] = (Out)(*total);
+  if (write_last && blockIdx.x == 0 && threadIdx.x == 0) out[n * stride] = (Out)(*total);
 }
 
 template <typename Out>
@@ -109,9 +116,11 @@ __global__ void k_store_total(const unsigned long long* total, Out* dst) {
   *dst = (Out)(*total);
 }
 
+// Exclusive scan of in(0..n-1) into out[i * stride] (and out[n * stride] =
+// total if write_last; *total_dst = total if not null).
 template <typename In, typename Out>
 cudaError_t scan_impl(Launcher* L, In in, uint64_t n, Out* out, int write_last, Out* total_dst, void* temp,
-                      cudaStream_t s) {
+                      cudaStream_t s, uint32_t stride = 1) {
   uint64_t nb = (n + kTile - 1) / kTile;
   if (nb == 0) nb = 1;
   unsigned long long* partial = (unsigned long long*)temp;
@@ -124,7 +133,7 @@ cudaError_t scan_impl(Launcher* L, In in, uint64_t n, Out* out, int write_last, 
   k_scan_spine<<<1, kThreads, 0, s>>>(partial, nb, total);
   if ((e = launch_end(L, "scan_spine")) != cudaSuccess) return e;
   if ((e = launch_begin(L, "scan_down")) != cudaSuccess) return e;
-  k_scan_down<In, Out><<<(unsigned)nb, kThreads, 0, s>>>(in, n, partial, total, out, write_last);
+  k_scan_down<In, Out><<<(unsigned)nb, kThreads, 0, s>>>(in, n, partial, total, out, write_last, stride);
   if ((e = launch_end(L, "scan_down")) != cudaSuccess) return e;
   if (total_dst) {
     if ((e = launch_begin(L, "scan_total")) != cudaSuccess) return e;
@@ -142,9 +151,10 @@ size_t scan_temp_bytes(uint64_t n) {
   return (size_t)(nb + 1) * sizeof(unsigned long long);
 }
 
-cudaError_t scan_popc_words(Launcher* L, const unsigned long long* words, uint64_t n, uint32_t* out_excl,
-                            uint32_t* total, void* temp, cudaStream_t s) {
-  return scan_impl<PopcIn, uint32_t>(L, PopcIn{words}, n, out_excl, 0, total, temp, s);
+cudaError_t scan_dict_blocks(Launcher* L, uint32_t* dict, uint64_t n_blocks, uint32_t* total, void* temp,
+                             cudaStream_t s) {
+  // in() reads words 1..7 of a block, out writes its word 0: no overlap
+  return scan_impl<DictIn, uint32_t>(L, DictIn{dict}, n_blocks, dict, 0, total, temp, s, 8u);
 }
 
 cudaError_t scan_u32(Launcher* L, const uint32_t* in, uint64_t n, uint32_t* out_excl_np1, void* temp,

@@ -253,8 +253,9 @@ static uint32_t ceil_log2_u64(uint64_t x) {
   return b;
 }
 
-// Maximum bitmap size of a segmented dataset (one bit per segment x 20^k code).
-static constexpr uint64_t kMaxBitmapBytes = (uint64_t)4 << 30;
+// Most codes a segmented dataset's dictionary may cover (segments x 20^k): one
+// bit each, 4 GiB of bits (4.6 GiB of rank blocks).
+static constexpr uint64_t kMaxDictCodes = (uint64_t)32 << 30;
 
 pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                                      uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, int k,
@@ -312,11 +313,11 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
       n_seg = std::max<uint64_t>(n_seg, (uint64_t)genome_seg[i] + 1);
       code_base[i] = (unsigned long long)genome_seg[i] * n_codes;
     }
-    if (n_seg * n_codes / 8 > kMaxBitmapBytes)
-      return fail(c, PD_ERR_BUDGET, "segments x 20^k exceed the dictionary bitmap limit (" +
-                                        std::to_string(kMaxBitmapBytes >> 30) + " GiB)");
+    if (n_seg * n_codes > kMaxDictCodes)
+      return fail(c, PD_ERR_BUDGET, "segments x 20^k exceed the dictionary limit (" +
+                                        std::to_string(kMaxDictCodes >> 30) + " Gi codes)");
   }
-  const uint64_t n_words = (n_seg * n_codes + 63) / 64;
+  const uint64_t n_dict = pdg::dict_blocks(n_seg * n_codes);
   const size_t G1 = std::max<uint32_t>(n_genes, 1);
   pdg::Launcher* L = &c->L;
 
@@ -368,21 +369,19 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
                        cudaMemcpyHostToDevice, c->stream));
   }
 
-  // ---- dictionary: bitmap of present codes and word ranks
-  ALLOC(P->bitmap, sizeof(unsigned long long) * n_words);
-  ALLOC(P->word_rank, sizeof(uint32_t) * n_words);
-  CK(cudaMemsetAsync(P->bitmap.p, 0, sizeof(unsigned long long) * n_words, c->stream));
+  // ---- dictionary: present codes in rank blocks, then the blocks' rank bases
+  ALLOC(P->dict, 8 * sizeof(uint32_t) * n_dict);
+  CK(cudaMemsetAsync(P->dict.p, 0, 8 * sizeof(uint32_t) * n_dict, c->stream));
   if (n_genes)
-    CK(pdg::run_encode_mark(L, res_dev, gp_devp, n_genes, k, P->bitmap.as<unsigned long long>(),
+    CK(pdg::run_encode_mark(L, res_dev, gp_devp, n_genes, k, P->dict.as<uint32_t>(),
                             P->gene_genome.as<uint16_t>(), d_code_base.as<unsigned long long>(), gene_src,
                             alphabet, n_res, c->d_err, c->stream));
   const uint32_t kOrderShift = 16;  // 65536 min-hash buckets
   const uint64_t n_order_b = (uint64_t)1 << (32 - kOrderShift);
-  ALLOC(tmp, pdg::scan_temp_bytes(std::max<uint64_t>(std::max<uint64_t>(n_words, n_order_b), 24577)) + 64);
+  ALLOC(tmp, pdg::scan_temp_bytes(std::max<uint64_t>(std::max<uint64_t>(n_dict, n_order_b), 24577)) + 64);
   ALLOC(d_counts, 4 * sizeof(uint32_t));  // [0] = D, [1] = max posting
   CK(cudaMemsetAsync(d_counts.p, 0, 4 * sizeof(uint32_t), c->stream));
-  CK(pdg::scan_popc_words(L, P->bitmap.as<unsigned long long>(), n_words, P->word_rank.as<uint32_t>(),
-                          d_counts.as<uint32_t>(), tmp.p, c->stream));
+  CK(pdg::scan_dict_blocks(L, P->dict.as<uint32_t>(), n_dict, d_counts.as<uint32_t>(), tmp.p, c->stream));
   // one synchronisation: the dictionary size, the window total, the gene
   // classes and any error found in the offsets or the letters
   unsigned long long* hb = c->h_build;
@@ -434,8 +433,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   M.length_buckets = length_buckets;
   M.frozen = 0;
   if (n_genes)
-    CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k,
-                         P->bitmap.as<unsigned long long>(), P->word_rank.as<uint32_t>(), M,
+    CK(pdg::run_mv_build(L, res_dev, gp_devp, P->win_off.as<uint32_t>(), n_genes, k, P->dict.as<uint32_t>(), M,
                          d_mid.as<uint32_t>(), n_mid, d_long.as<uint32_t>(), n_long,
                          d_long_scratch.as<unsigned long long>(), d_long_off.as<unsigned long long>(), c->stream));
 
@@ -499,9 +497,8 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   v.gene_genome = P->gene_genome.as<uint16_t>();
   v.ginfo = P->ginfo.as<uint32_t>();
   v.genome_ptr = P->genome_ptr.as<int32_t>();
-  v.bitmap = P->bitmap.as<unsigned long long>();
-  v.word_rank = P->word_rank.as<uint32_t>();
-  v.n_words = n_words;
+  v.dict = P->dict.as<uint32_t>();
+  v.n_dict_blocks = n_dict;
   v.post_ptr = P->post_ptr.as<uint32_t>();
   v.post = P->post.as<uint32_t>();
   v.order = P->order.as<uint32_t>();
@@ -517,7 +514,7 @@ pd_status pdh::build_profiles_impl(pd_ctx* c, const uint8_t* residues, uint64_t 
   in.count_bits = cnt_bits;
   in.alphabet = alphabet;
   in.device_bytes = P->genome_ptr.n + P->La.n + P->win_off.n + P->mv_n.n + P->mv_id.n + P->mv_cnt.n +
-                    P->mv_post.n + P->mv_plen.n + P->gene_genome.n + P->ginfo.n + P->bitmap.n + P->word_rank.n +
+                    P->mv_post.n + P->mv_plen.n + P->gene_genome.n + P->ginfo.n + P->dict.n +
                     P->post_ptr.n + P->post.n + P->order.n;
   *out = guard.release();
   return PD_OK;
@@ -618,7 +615,7 @@ PD_API pd_status pd_profiles_copy_mv(pd_ctx* c, const pd_profiles* P, int64_t* m
       CK(cudaMemcpyAsync(pad_off.p, off.data(), sizeof(unsigned long long) * (v.n_genes + 1), cudaMemcpyHostToDevice,
                          c->stream));
       ALLOC(code_of_id, sizeof(unsigned long long) * std::max<uint64_t>(v.n_distinct, 1));
-      CK(pdg::run_select_codes(L, v.bitmap, v.word_rank, v.n_words, code_of_id.as<unsigned long long>(), c->stream));
+      CK(pdg::run_select_codes(L, v.dict, v.n_dict_blocks, code_of_id.as<unsigned long long>(), c->stream));
       ALLOC(d_codes, sizeof(unsigned long long) * std::max<uint64_t>(v.n_entries, 1));
       ALLOC(d_counts, sizeof(uint32_t) * std::max<uint64_t>(v.n_entries, 1));
       CK(pdg::run_export_mv(L, v, ptr.as<unsigned long long>(), pad_off.as<unsigned long long>(),
@@ -656,7 +653,7 @@ PD_API pd_status pd_profiles_copy_index(pd_ctx* c, const pd_profiles* P, int64_t
     }
     if (codes) {
       ALLOC(code_of_id, sizeof(unsigned long long) * std::max<uint64_t>(v.n_distinct, 1));
-      CK(pdg::run_select_codes(L, v.bitmap, v.word_rank, v.n_words, code_of_id.as<unsigned long long>(), c->stream));
+      CK(pdg::run_select_codes(L, v.dict, v.n_dict_blocks, code_of_id.as<unsigned long long>(), c->stream));
     }
     if (genes) ALLOC(d_genes, sizeof(int32_t) * std::max<uint64_t>(v.n_entries, 1));
     if (counts) ALLOC(d_counts, sizeof(uint32_t) * std::max<uint64_t>(v.n_entries, 1));
@@ -858,8 +855,8 @@ pd_status pdh::query_profiles_impl(pd_ctx* c, const pd_profiles* P, const uint8_
   M.length_buckets = 0;
   M.frozen = 1;
   if (n_genes) {
-    CK(pdg::run_mv_build(L, residues_dev, d_gp.as<int64_t>(), Qp->win_off.as<uint32_t>(), n_genes, k, v.bitmap,
-                         v.word_rank, M, d_mid.as<uint32_t>(), (uint32_t)mid.size(), d_long.as<uint32_t>(),
+    CK(pdg::run_mv_build(L, residues_dev, d_gp.as<int64_t>(), Qp->win_off.as<uint32_t>(), n_genes, k, v.dict, M,
+                         d_mid.as<uint32_t>(), (uint32_t)mid.size(), d_long.as<uint32_t>(),
                          (uint32_t)lng.size(), d_long_scratch.as<unsigned long long>(),
                          d_long_off.as<unsigned long long>(), c->stream));
     CK(pdg::run_mv_post(L, Qp->win_off.as<uint32_t>(), Qp->mv_n.as<uint32_t>(), Qp->mv_id.as<uint32_t>(), n_genes,

@@ -4,7 +4,7 @@
 // 2-3 per job) are served by few launch sequences instead of one per job:
 //
 //   1. jobs are grouped by k and cut into chunks (bounded windows, bounded
-//      dictionary bitmap);
+//      dictionary: codes x segments);
 //   2. a chunk is ONE segmented profile build (each job its own k-mer
 //      namespace, so postings of one job never reach another job's genes),
 //      ONE all-pairs Best Hit pass (every gene of every job queried in the
@@ -40,8 +40,9 @@ struct pd_batch {
 namespace {
 
 constexpr uint64_t kDefaultChunkWindows = 1ull << 29;
-// Dictionary bitmap per chunk: small enough that its random marks mostly hit L2.
-constexpr uint64_t kChunkBitmapBytes = 256ull << 20;
+// Dictionary codes per chunk (segments x 20^k; one bit each, 256 MiB of
+// bits): small enough that its random marks mostly hit L2.
+constexpr uint64_t kChunkDictCodes = 2048ull << 20;
 
 // One job of a chunk: where its genes sit in the chunk and in the batch.
 struct ChunkJob {
@@ -205,7 +206,7 @@ pd_status batch_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const i
   CK(cudaMemsetAsync(row_len.p, 0, sizeof(uint32_t) * std::max<uint64_t>(n_rows, 1), c->stream));
   CK(cudaMemsetAsync(job_cnt.p, 0, sizeof(uint32_t) * (n_jobs + 1), c->stream));
 
-  // ---- chunks: jobs grouped by k (stable), cut by windows, bitmap and genome limits
+  // ---- chunks: jobs grouped by k (stable), cut by windows, dictionary and genome limits
   std::vector<uint32_t> by_k(n_jobs);
   for (uint32_t j = 0; j < n_jobs; ++j) by_k[j] = j;
   std::stable_sort(by_k.begin(), by_k.end(), [&](uint32_t x, uint32_t y) { return job_k[x] < job_k[y]; });
@@ -216,7 +217,7 @@ pd_status batch_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const i
     const int k = job_k[by_k[pos]];
     uint64_t n_codes = 1;
     for (int t = 0; t < k; ++t) n_codes *= 20;
-    uint64_t max_jobs = std::max<uint64_t>(1, kChunkBitmapBytes * 8 / n_codes);
+    uint64_t max_jobs = std::max<uint64_t>(1, kChunkDictCodes / n_codes);
     max_jobs = std::min<uint64_t>(max_jobs, PD_MAX_GENOMES / 2);
     if (tuning && tuning->max_chunk_jobs) max_jobs = std::min<uint64_t>(max_jobs, tuning->max_chunk_jobs);
     std::vector<uint32_t> cj;  // batch jobs of this chunk

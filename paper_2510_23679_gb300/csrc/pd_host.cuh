@@ -209,7 +209,7 @@ struct pd_profiles {
   pd_ctx* ctx = nullptr;
   pdg::ProfilesView view{};
   pd_profiles_info info{};
-  Buf genome_ptr, La, win_off, mv_n, mv_id, mv_cnt, mv_post, mv_plen, gene_genome, ginfo, bitmap, word_rank, post_ptr,
+  Buf genome_ptr, La, win_off, mv_n, mv_id, mv_cnt, mv_post, mv_plen, gene_genome, ginfo, dict, post_ptr,
       post, order;
   std::vector<int32_t> h_genome_ptr;
 };

@@ -14,11 +14,15 @@
 //   mv_post[W],    uint32  posting range of that k-mer (copied from post_ptr so
 //   mv_plen[W]             a query reads its list bounds with its own vector).
 //   gene_genome[G] uint16  genome of each gene; ginfo[G] = La | genome << 16.
-//   bitmap[20^k/64] uint64 one bit per possible k-mer code: set if it occurs.
-//   word_rank[...]  uint32 number of set bits before each bitmap word, so the
-//                          dense id of code c is word_rank[c>>6] +
-//                          popc(bitmap[c>>6] & ((1<<(c&63))-1)); ids are
-//                          therefore ascending in code order.
+//   dict[8 * ceil(20^k / 224)] uint32  the dictionary, one bit per possible
+//                          k-mer code in rank blocks of 32 bytes (one DRAM
+//                          sector): block b covers codes 224b .. 224b+223,
+//                          word 0 = number of codes present in blocks 0..b-1,
+//                          words 1..7 = the block's bits (code 224b + j is bit
+//                          j % 32 of word 1 + j / 32).  The dense id of a
+//                          present code is word 0 plus the set bits before it
+//                          in its block (ascending in code order), read with
+//                          one sector per lookup.
 //   post_ptr[D+1]  uint32  inverted index: postings of id w are
 //   post[E]        uint32  post[post_ptr[w] .. post_ptr[w+1]), ascending by
 //                          gene, each packed as (gene << cnt_bits) | min(count,
@@ -38,6 +42,43 @@
 namespace pdg {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
+
+// ---------------------------------------------------------------- dictionary
+constexpr uint32_t kDictBits = 224;  // codes per 32-byte rank block
+__host__ __device__ __forceinline__ uint64_t dict_blocks(uint64_t n_codes) {
+  return (n_codes + kDictBits - 1) / kDictBits;
+}
+// Block of a code, and the code's word (1..7) and bit inside it.
+__device__ __forceinline__ void dict_locate(unsigned long long code, unsigned long long* blk, uint32_t* word,
+                                            uint32_t* bit) {
+  const unsigned long long b = code / kDictBits;
+  const uint32_t off = (uint32_t)(code - b * kDictBits);
+  *blk = b;
+  *word = 1u + (off >> 5);
+  *bit = off & 31u;
+}
+__device__ __forceinline__ bool dict_has(const uint32_t* __restrict__ dict, unsigned long long code) {
+  unsigned long long b;
+  uint32_t w, bit;
+  dict_locate(code, &b, &w, &bit);
+  return (dict[b * 8 + w] >> bit) & 1u;
+}
+// Dense id of a present code: the block's base plus the set bits before it.
+__device__ __forceinline__ uint32_t dict_rank(const uint32_t* __restrict__ dict, unsigned long long code) {
+  unsigned long long b;
+  uint32_t w, bit;
+  dict_locate(code, &b, &w, &bit);
+  const uint4* q = reinterpret_cast<const uint4*>(dict + b * 8);
+  const uint4 lo = q[0], hi = q[1];
+  const uint32_t words[7] = {lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
+  uint32_t r = lo.x;
+#pragma unroll
+  for (uint32_t j = 0; j < 7; ++j) {
+    const uint32_t m = j + 1u < w ? 0xFFFFFFFFu : (j + 1u == w ? (1u << bit) - 1u : 0u);
+    r += (uint32_t)__popc(words[j] & m);
+  }
+  return r;
+}
 constexpr int kAlphabetSize = 20;
 
 // ---------------------------------------------------------------- errors
@@ -152,9 +193,8 @@ struct ProfilesView {
   const uint16_t* gene_genome;  // [G]   genome of each gene
   const uint32_t* ginfo;        // [G]   La | genome << 16
   const int32_t* genome_ptr;    // [n+1] device copy
-  const unsigned long long* bitmap;
-  const uint32_t* word_rank;
-  uint64_t n_words;
+  const uint32_t* dict;         // [8 * n_dict_blocks] dictionary rank blocks
+  uint64_t n_dict_blocks;
   const uint32_t* post_ptr;     // [D+1]
   const uint32_t* post;         // [E]   packed postings
   const uint32_t* order;        // [G]   all-pairs query order (min-hash buckets)
@@ -270,8 +310,10 @@ cudaError_t launch_end(Launcher* L, const char* name);
 
 // scans (k_scan.cu)
 size_t scan_temp_bytes(uint64_t n);
-cudaError_t scan_popc_words(Launcher* L, const unsigned long long* words, uint64_t n, uint32_t* out_excl,
-                            uint32_t* total, void* temp, cudaStream_t s);
+// Rank bases of the dictionary: word 0 of each of the n_blocks blocks gets
+// the set bits of the blocks before it; *total gets the number of codes.
+cudaError_t scan_dict_blocks(Launcher* L, uint32_t* dict, uint64_t n_blocks, uint32_t* total, void* temp,
+                             cudaStream_t s);
 cudaError_t scan_u32(Launcher* L, const uint32_t* in, uint64_t n, uint32_t* out_excl_np1, void* temp,
                      cudaStream_t s);
 cudaError_t scan_u32_to_u64(Launcher* L, const uint32_t* in, uint64_t n, unsigned long long* out_excl_np1,
@@ -294,7 +336,7 @@ cudaError_t run_narrow_u64(Launcher* L, const unsigned long long* in, uint64_t n
 // n_res bounds the residues of every gene read through gene_ptr (genes read
 // through gene_src are trusted).
 cudaError_t run_encode_mark(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, uint32_t n_genes, int k,
-                            unsigned long long* bitmap, const uint16_t* gene_genome,
+                            uint32_t* dict, const uint16_t* gene_genome,
                             const unsigned long long* genome_code_base, const int64_t* gene_src, int alpha,
                             uint64_t n_res, DevErr* err, cudaStream_t s);
 // Outputs of the multiplicity-vector build.
@@ -311,15 +353,14 @@ struct MvOut {
   const int64_t* gene_src;                     // per gene: first residue, or null (gene_ptr[g])
   int alpha;                                   // alphabet size: 20 or 4
   int length_buckets;                          // query order: length buckets first (1) or min-hash only (0)
-  int frozen;                                  // 1: the bitmap is another dataset's dictionary; windows
+  int frozen;                                  // 1: the dictionary is another dataset's; windows
                                                // whose code it lacks are left out of the vector
 };
 // Table slots used for a gene with La windows (genes above 16384 slots use
 // global scratch of that many 64-bit slots, listed in long_genes).
 uint32_t mv_build_table_cap(uint32_t La);
 cudaError_t run_mv_build(Launcher* L, const uint8_t* res, const int64_t* gene_ptr, const uint32_t* win_off,
-                         uint32_t n_genes, int k, const unsigned long long* bitmap, const uint32_t* word_rank,
-                         const MvOut& M, const uint32_t* mid_genes, uint32_t n_mid, const uint32_t* long_genes,
+                         uint32_t n_genes, int k, const uint32_t* dict, const MvOut& M, const uint32_t* mid_genes, uint32_t n_mid, const uint32_t* long_genes,
                          uint32_t n_long, unsigned long long* long_scratch, const unsigned long long* long_scratch_off,
                          cudaStream_t s);
 // Stable LSD radix sort of the n index records in `a` (ping-pong with `b`) by
@@ -340,8 +381,8 @@ cudaError_t run_order(Launcher* L, const uint32_t* minhash, uint32_t n_genes, ui
                       uint32_t* order, void* scan_tmp, cudaStream_t s);
 cudaError_t run_gene_info(Launcher* L, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* La,
                           uint16_t* gene_genome, uint32_t* ginfo, cudaStream_t s);
-cudaError_t run_select_codes(Launcher* L, const unsigned long long* bitmap, const uint32_t* word_rank,
-                             uint64_t n_words, unsigned long long* code_of_id, cudaStream_t s);
+cudaError_t run_select_codes(Launcher* L, const uint32_t* dict, uint64_t n_blocks, unsigned long long* code_of_id,
+                             cudaStream_t s);
 // pad_off: n_genes+1 offsets of power-of-two padded per-gene scratch regions in pad.
 cudaError_t run_export_mv(Launcher* L, const ProfilesView& P, const unsigned long long* mv_ptr,
                           const unsigned long long* pad_off, unsigned long long* pad,
