@@ -216,6 +216,20 @@ pd_status pd_best_hits_all(pd_ctx* ctx, const pd_profiles* prof, pd_hits** out);
  * query walks every other genome.  Errors: PD_ERR_ARG (null context). */
 pd_status pd_ctx_set_symmetric(pd_ctx* ctx, int enable);
 
+/* Posting walk of the sum-min kernel (no counterpart in the paper; results
+ * are identical for every choice, only the time differs).  A query's staged
+ * posting lists are read either by the merge-path walk (each thread a run of
+ * consecutive postings, batches of four) or by the warp-cooperative walk
+ * (each warp 32 consecutive postings per round; suits long lists).
+ * PD_WALK_AUTO (the default) takes the warp walk when the build's join
+ * (pd_profiles_info.n_join) is at least 16 postings per vector entry.
+ * Applies to every later Best Hit call on the context.  Errors: PD_ERR_ARG
+ * (null context, unknown mode). */
+#define PD_WALK_AUTO 0u
+#define PD_WALK_MERGE 1u
+#define PD_WALK_WARP 2u
+pd_status pd_ctx_set_walk(pd_ctx* ctx, uint32_t mode);
+
 /* One shard of pd_best_hits_all, for splitting one dataset's all-against-all
  * work across processes or GPUs that each hold the same profiles.  The paper
  * decomposes phase (b) by data, one query gene (a row of Algorithm 2) being
@@ -369,6 +383,7 @@ typedef struct {
                                  at most PD_MAX_GENOMES / 2) */
   uint32_t query_order;       /* sum-min work queue: 0 = length buckets (longest
                                  first), min-hash inside a bucket; 1 = min-hash only */
+  uint32_t walk;              /* posting walk of the sum-min kernel (PD_WALK_*) */
 } pd_batch_tuning;
 
 typedef struct {
@@ -409,12 +424,13 @@ pd_status pd_bbh_pairs(pd_ctx* ctx, const pd_profiles* prof, const uint32_t* job
                        pd_batch** out);
 pd_status pd_batch_get_info(const pd_batch* batch, pd_batch_info* info);
 /* Autotuner of pd_bbh_batch: runs the first n_sample jobs (0 = min(n_jobs,
- * 100)) once with each candidate tuning (jobs per chunk 8 / 32 / bitmap
- * default, windows per chunk 2^28 / 2^29, both query orders), timed with CUDA
- * events on the context's stream after one warm-up, and writes the fastest to
- * *best (and its time per sampled job, in milliseconds, to *ms_per_job if not
- * NULL).  Results never depend on the tuning, only the time does.  Arguments
- * as pd_bbh_batch. */
+ * 100)) once with each candidate tuning (jobs per chunk 8 / 32 / dictionary
+ * default, windows per chunk 2^28 / 2^29, both query orders, the automatic
+ * walk; then the fastest of these with each explicit posting walk), timed
+ * with CUDA events on the context's stream after one warm-up, and writes the
+ * fastest to *best (and its time per sampled job, in milliseconds, to
+ * *ms_per_job if not NULL).  Results never depend on the tuning, only the
+ * time does.  Arguments as pd_bbh_batch. */
 pd_status pd_batch_autotune(pd_ctx* ctx, const uint8_t* residues, uint64_t n_res, const int64_t* gene_ptr,
                             uint32_t n_genes, const int32_t* genome_ptr, uint32_t n_genomes, const uint32_t* jobs,
                             const int32_t* job_k, uint32_t n_jobs, uint32_t n_sample, pd_batch_tuning* best,

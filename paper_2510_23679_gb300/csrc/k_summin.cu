@@ -811,7 +811,8 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
   if (emit_all)
     e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutEmit, true, true, false, kT1Used>, L, "summin_pairs",
                     kT1Threads, T1E::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
-  else if (P.n_join < (uint64_t)kWarpWalkMinAvg * P.n_entries)  // short lists: merge-path walk
+  else if (Q.walk == PD_WALK_MERGE ||
+           (Q.walk != PD_WALK_WARP && P.n_join < (uint64_t)kWarpWalkMinAvg * P.n_entries))  // short lists: merge-path walk
     e = n_best <= kT1CompactGenomes
             ? launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false, false, kT1Used>, L,
                           "summin_bh", kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s)

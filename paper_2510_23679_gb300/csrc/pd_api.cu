@@ -176,6 +176,13 @@ PD_API pd_status pd_ctx_set_symmetric(pd_ctx* c, int enable) {
   return PD_OK;
 }
 
+PD_API pd_status pd_ctx_set_walk(pd_ctx* c, uint32_t mode) {
+  if (!c) return PD_ERR_ARG;
+  if (mode > PD_WALK_WARP) return fail(c, PD_ERR_ARG, "unknown walk mode");
+  c->walk = mode;
+  return PD_OK;
+}
+
 PD_API pd_status pd_ctx_set_timing(pd_ctx* c, int enable) {
   if (!c) return PD_ERR_ARG;
   c->timing = enable != 0;
@@ -727,7 +734,9 @@ static pd_status run_hits_on(pd_ctx* c, const pdg::ProfilesView& v, const pdg::Q
     O.row_len = H->row_len.as<uint32_t>();
     O.def1 = def1.as<uint32_t>();
     O.def2 = def2.as<uint32_t>();
-    CK(pdg::run_summin_tiers(L, v, Q, O, c->d_err, emit_all, c->stream));
+    pdg::QuerySet Qw = Q;  // the context's walk unless the call chose one
+    if (Qw.walk == PD_WALK_AUTO) Qw.walk = c->walk;
+    CK(pdg::run_summin_tiers(L, v, Qw, O, c->d_err, emit_all, c->stream));
     unsigned long long h[4];
     CK(cudaMemcpyAsync(h, counters.p, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
     pd_status st = check_dev_err(c);

@@ -271,6 +271,7 @@ pd_status batch_impl(pd_ctx* c, const uint8_t* residues, uint64_t n_res, const i
     Q.order = P->view.order;
     Q.q0 = 0;
     Q.n_queries = chunk_genes;
+    Q.walk = tuning ? tuning->walk : PD_WALK_AUTO;
     C->hits.ctx = c;
     C->hits.all_pairs = 1;
     if ((st = run_hits(c, P.get(), Q, false, &C->hits, 1)) != PD_OK) return st;
@@ -584,13 +585,23 @@ PD_API pd_status pd_batch_autotune(pd_ctx* c, const uint8_t* residues, uint64_t 
     std::vector<pd_batch_tuning> cand;
     for (uint32_t order : {0u, 1u})
       for (uint64_t w : {1ull << 28, 1ull << 29})
-        for (uint32_t j : {8u, 32u, 0u}) cand.push_back(pd_batch_tuning{w, j, order});
+        for (uint32_t j : {8u, 32u, 0u}) cand.push_back(pd_batch_tuning{w, j, order, PD_WALK_AUTO});
+    // after the chunking and order candidates: the fastest of them with each
+    // explicit posting walk (the automatic choice is one of the two)
+    const size_t n_first = cand.size();
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best_ms = -1.f;
     pd_status st = PD_OK;
-    for (size_t x = 0; x < cand.size() && st == PD_OK; ++x) {
+    for (size_t x = 0; st == PD_OK; ++x) {
+      if (x == n_first && best_ms >= 0.f)
+        for (uint32_t walk : {PD_WALK_MERGE, PD_WALK_WARP}) {
+          pd_batch_tuning t = *best;
+          t.walk = walk;
+          cand.push_back(t);
+        }
+      if (x >= cand.size()) break;
       for (int rep = 0; rep < 2 && st == PD_OK; ++rep) {  // one warm-up, one timed run
         pd_batch* B = nullptr;
         if (cudaEventRecord(e0, c->stream) != cudaSuccess) st = fail_cuda(c, cudaGetLastError(), "event");

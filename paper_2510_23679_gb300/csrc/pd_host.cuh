@@ -54,6 +54,7 @@ struct pd_ctx {
   uint64_t launches = 0;
   bool timing = false;
   bool symmetric = true;  // pd_best_hits_all walks each genome pair from one side (pd_ctx_set_symmetric)
+  uint32_t walk = PD_WALK_AUTO;  // posting walk of the sum-min kernel (pd_ctx_set_walk)
   std::string timing_filter;  // empty: time every kernel; else only launches of this name
   std::vector<PendingTiming> pending;
   std::vector<cudaEvent_t> event_pool;

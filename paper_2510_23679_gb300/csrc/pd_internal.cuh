@@ -264,6 +264,9 @@ struct QuerySet {
   // tau_den of Eq. (7); a numerator of 0 turns a filter off.
   int filter;
   uint32_t theta_num, theta_den, tau_num, tau_den;
+  // Posting walk of tier 1 (PD_WALK_*): automatic (from the join per vector
+  // entry), merge-path, or warp-cooperative.
+  uint32_t walk;
 };
 
 struct HitsOut {

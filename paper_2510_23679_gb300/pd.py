@@ -57,7 +57,8 @@ class Filter(C.Structure):
 
 
 class BatchTuning(C.Structure):
-    _fields_ = [("max_chunk_windows", C.c_uint64), ("max_chunk_jobs", C.c_uint32), ("query_order", C.c_uint32)]
+    _fields_ = [("max_chunk_windows", C.c_uint64), ("max_chunk_jobs", C.c_uint32), ("query_order", C.c_uint32),
+                ("walk", C.c_uint32)]
 
 
 class BatchInfo(C.Structure):
@@ -142,6 +143,7 @@ _SIGNATURES = [
     ("pd_best_hits_shard", C.c_int, [_P, _P, C.c_uint32, C.c_uint32, _PP]),
     ("pd_summin_list", C.c_int, [_P, _P, _P, _P, C.c_uint64, _P, _P]),
     ("pd_ctx_set_symmetric", C.c_int, [_P, C.c_int]),
+    ("pd_ctx_set_walk", C.c_int, [_P, C.c_uint32]),
     ("pd_hits_import", C.c_int, [_P, _P, C.c_uint32, _P, _P, _P, _P, _PP]),
     ("pd_index_genome_ptr", C.c_int, [_P, C.c_uint32, _P]),
     ("pd_index_free", None, [_P]),
@@ -304,6 +306,16 @@ def pd_ctx_set_symmetric(ctx: Ctx, enable: bool) -> None:
     """pd_best_hits_all walks each genome pair from one side (True, the
     default) or every genome from every query (False); same results."""
     _check(ctx, _lib.pd_ctx_set_symmetric(ctx.handle, 1 if enable else 0), "pd_ctx_set_symmetric")
+
+
+PD_WALK_AUTO, PD_WALK_MERGE, PD_WALK_WARP = 0, 1, 2
+
+
+def pd_ctx_set_walk(ctx: Ctx, mode: int) -> None:
+    """Posting walk of the sum-min kernel for later Best Hit calls:
+    PD_WALK_AUTO (from the build's join), PD_WALK_MERGE or PD_WALK_WARP; same
+    results."""
+    _check(ctx, _lib.pd_ctx_set_walk(ctx.handle, int(mode)), "pd_ctx_set_walk")
 
 
 def pd_ctx_set_timing_filter(ctx: Ctx, name: str | None) -> None:
@@ -643,7 +655,7 @@ def pd_best_hits_noalloc(ctx: Ctx, prof: Profiles, gi: int, gj: int, row_ptr, co
 
 
 def pd_bbh_batch(ctx: Ctx, residues, gene_ptr, genome_ptr, jobs, job_k, max_chunk_windows: int = 0,
-                 max_chunk_jobs: int = 0, query_order: int = 0) -> Batch:
+                 max_chunk_jobs: int = 0, query_order: int = 0, walk: int = 0) -> Batch:
     """Best Hits (both directions) and BBH of many genome-pair jobs: jobs is a
     host array [n_jobs, 2] of genome indices, job_k the k of each job."""
     n_res = int(residues.shape[0])
@@ -653,7 +665,7 @@ def pd_bbh_batch(ctx: Ctx, residues, gene_ptr, genome_ptr, jobs, job_k, max_chun
     kk = np.ascontiguousarray(job_k, dtype=np.int32)
     if jb.shape[0] != 2 * kk.shape[0]:
         raise ValueError("jobs must have two genome indices per entry of job_k")
-    tun = BatchTuning(int(max_chunk_windows), int(max_chunk_jobs), int(query_order))
+    tun = BatchTuning(int(max_chunk_windows), int(max_chunk_jobs), int(query_order), int(walk))
     h = C.c_void_p()
     st = _lib.pd_bbh_batch(ctx.handle, _ptr(residues), n_res, _ptr(gene_ptr), n_genes, _ptr(genome_ptr), n_genomes,
                            _ptr(jb) if jb.size else None, _ptr(kk) if kk.size else None, int(kk.shape[0]),
@@ -684,7 +696,7 @@ def pd_batch_autotune(ctx: Ctx, residues, gene_ptr, genome_ptr, jobs, job_k, n_s
                                        _ptr(jb), _ptr(kk), int(kk.shape[0]), int(n_sample), C.byref(best),
                                        C.byref(ms)), "pd_batch_autotune")
     return ({"max_chunk_windows": int(best.max_chunk_windows), "max_chunk_jobs": int(best.max_chunk_jobs),
-             "query_order": int(best.query_order)}, float(ms.value))
+             "query_order": int(best.query_order), "walk": int(best.walk)}, float(ms.value))
 
 
 def pd_batch_get_info(batch: Batch) -> BatchInfo:

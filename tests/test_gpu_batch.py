@@ -157,7 +157,12 @@ def test_query_order_and_autotuner(ctx, batch_data):
     a, _ = _run_batch(ctx, ds, jobs, ks, query_order=0)
     b, _ = _run_batch(ctx, ds, jobs, ks, query_order=1, max_chunk_jobs=4)
     assert a == b
+    # every posting walk gives the same bytes
+    for walk in (pd.PD_WALK_MERGE, pd.PD_WALK_WARP):
+        w, _ = _run_batch(ctx, ds, jobs, ks, walk=walk)
+        assert w == a, walk
     best, ms = pd.pd_batch_autotune(ctx, ds.residues, ds.gene_ptr, ds.genome_ptr, jobs, ks, n_sample=12)
     assert best["query_order"] in (0, 1) and best["max_chunk_jobs"] in (0, 8, 32) and ms > 0
+    assert best["walk"] in (pd.PD_WALK_AUTO, pd.PD_WALK_MERGE, pd.PD_WALK_WARP)
     c, _ = _run_batch(ctx, ds, jobs, ks, **best)
     assert c == a

@@ -64,3 +64,25 @@ def test_tie_list_larger_than_its_first_allocation(ctxs):
     ds = synth.from_strings([[b"ACDEFGHIK"] * 300, [b"ACDEFGHIK"] * 300])
     a, _ = _same(ctxs, ds, 4)
     assert len(a[1]) == 2 * 300 * 300  # every gene ties with every gene of the other genome
+
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_walk_modes_same_bytes(symmetric):
+    """Both posting walks of the sum-min kernel (forced through
+    pd_ctx_set_walk), in both all-pairs forms, give the automatic choice's
+    bytes -- on a dataset whose lists are long enough that the automatic
+    choice is the warp walk for some queries and short enough that lists of
+    one or two postings are common."""
+    ds = synth.workload("pan4x250", seed=11)
+    k = 4
+    runs = []
+    for mode in (pd.PD_WALK_AUTO, pd.PD_WALK_MERGE, pd.PD_WALK_WARP):
+        ctx = pd.pd_ctx_create(0)
+        pd.pd_ctx_set_symmetric(ctx, symmetric)
+        pd.pd_ctx_set_walk(ctx, mode)
+        runs.append(_run(ctx, ds, k))
+    for r in runs[1:]:
+        for x, y, name in zip(runs[0][:4], r[:4], ("row_ptr", "cols", "s", "bbh")):
+            assert np.array_equal(x, y), name
+    with pytest.raises(pd.PdError):
+        pd.pd_ctx_set_walk(pd.pd_ctx_create(0), 3)
