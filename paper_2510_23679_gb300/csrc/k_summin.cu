@@ -355,8 +355,11 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
         uint32_t lo = 0, len = 0;
         if (e < n_in) {
           lo = q_mv_post[m0 + c0 + e];
-          uint32_t hi = lo + q_mv_plen[m0 + c0 + e];
-          if (!Q.all_pairs) {
+          const uint32_t plen = q_mv_plen[m0 + c0 + e];
+          uint32_t hi = lo + plen;
+          if (!ext && plen == 1u) {
+            hi = lo;  // the list holds only the query's own posting: never a target
+          } else if (!Q.all_pairs) {
             lo = lower_bound_post(P.post, lo, hi, key_lo);
             hi = lower_bound_post(P.post, lo, hi, key_hi);
           } else if (Q.symbest) {
@@ -555,7 +558,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
         const uint32_t den = La_a + (gi & 0xFFFFu) - s;
         best_update(&best[Q.all_pairs ? (gi >> 16) : 0u], s, den);
         if (Q.colbest) best_update(&Q.colbest[(size_t)b * Q.col_stride + col], s, den);
-        if (Q.symbest) sym_update(Q, &Q.symbest[(size_t)b * P.n_genomes + col], b, a, s, den);
+        if (Q.symbest) sym_update(Q, &Q.symbest[(size_t)col * P.n_genes + b], b, a, s, den);
       }
       __syncthreads();
       for (uint32_t u = tid; u < n_occ; u += kThreads) {

@@ -24,18 +24,14 @@ __device__ __forceinline__ void unpack(unsigned long long w, uint32_t* s, uint32
   *a = (uint32_t)w & 0x7FFFFFFFu;
 }
 
-// One warp per gene: stored maxima of the genomes before its own.
+// One thread per gene: stored maxima of the genomes before its own (the
+// maxima are genome-major, so neighbouring threads read neighbouring words).
 __global__ void __launch_bounds__(256) k_sym_count(SymRows R, uint32_t* __restrict__ stored) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < R.n_genes; b += warps) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < R.n_genes; b += gridDim.x * blockDim.x) {
     const uint32_t gb = R.gene_genome[b];
-    const unsigned long long* row = R.symbest + (size_t)b * R.n_genomes;
     uint32_t n = 0;
-    for (uint32_t g = lane; g < gb; g += 32) n += row[g] != 0ull ? 1u : 0u;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n += __shfl_xor_sync(0xffffffffu, n, o);
-    if (lane == 0) stored[b] = n;
+    for (uint32_t g = 0; g < gb; ++g) n += R.symbest[(size_t)g * R.n_genes + b] != 0ull ? 1u : 0u;
+    stored[b] = n;
   }
 }
 
@@ -62,7 +58,7 @@ __global__ void k_sym_ties(SymRows R, uint32_t* __restrict__ tiecnt, uint8_t* __
        t += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long r = R.tie_rec[2 * t];
     const uint32_t b = (uint32_t)(r >> 32), a = (uint32_t)r, s = (uint32_t)R.tie_rec[2 * t + 1];
-    const unsigned long long w = R.symbest[(size_t)b * R.n_genomes + R.gene_genome[a]];
+    const unsigned long long w = R.symbest[(size_t)R.gene_genome[a] * R.n_genes + b];
     uint32_t ms, md, ma;
     unpack(w, &ms, &md, &ma);
     const bool ok = w != 0ull && ma != a && ratio_equal(s, R.La[a] + R.La[b] - s, ms, md) &&
@@ -78,8 +74,27 @@ __global__ void k_sym_total(SymRows R, const uint32_t* __restrict__ stored, cons
     total[b] = stored[b] + tiecnt[b] + R.fwd_len[b];
 }
 
-// One warp per gene: the stored maxima in genome order, then (after room for
-// the gene's ties) the forward part.
+// One thread per gene: the stored maxima in genome order.
+__global__ void __launch_bounds__(256)
+    k_sym_write_rev(SymRows R, const unsigned long long* __restrict__ row_ptr, uint32_t* __restrict__ out_b,
+                    uint32_t* __restrict__ out_s) {
+  for (uint32_t b = blockIdx.x * blockDim.x + threadIdx.x; b < R.n_genes; b += gridDim.x * blockDim.x) {
+    const uint32_t gb = R.gene_genome[b];
+    unsigned long long at = row_ptr[b];
+    for (uint32_t g = 0; g < gb; ++g) {
+      const unsigned long long w = R.symbest[(size_t)g * R.n_genes + b];
+      if (w == 0ull) continue;
+      uint32_t s, den, a;
+      unpack(w, &s, &den, &a);
+      out_b[at] = a;
+      out_s[at] = s;
+      ++at;
+    }
+  }
+}
+
+// One warp per gene: the forward part, after the stored maxima and room for
+// the gene's ties.
 __global__ void __launch_bounds__(256)
     k_sym_write(SymRows R, const uint32_t* __restrict__ stored, const uint32_t* __restrict__ tiecnt,
                 const unsigned long long* __restrict__ row_ptr, uint32_t* __restrict__ out_b,
@@ -87,23 +102,7 @@ __global__ void __launch_bounds__(256)
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t warps = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < R.n_genes; b += warps) {
-    const uint32_t gb = R.gene_genome[b];
-    const unsigned long long* row = R.symbest + (size_t)b * R.n_genomes;
     const unsigned long long base = row_ptr[b];
-    uint32_t pos = 0;
-    for (uint32_t g0 = 0; g0 < gb; g0 += 32) {
-      const uint32_t g = g0 + lane;
-      const unsigned long long w = g < gb ? row[g] : 0ull;
-      const uint32_t m = __ballot_sync(0xffffffffu, w != 0ull);
-      if (w != 0ull) {
-        uint32_t s, den, a;
-        unpack(w, &s, &den, &a);
-        const unsigned long long at = base + pos + __popc(m & ((1u << lane) - 1u));
-        out_b[at] = a;
-        out_s[at] = s;
-      }
-      pos += __popc(m);
-    }
     const unsigned long long fwd = base + stored[b] + tiecnt[b];
     const unsigned long long fo = R.fwd_off[b];
     const uint32_t fl = R.fwd_len[b];
@@ -169,7 +168,7 @@ __global__ void __launch_bounds__(256) k_sym_bbh_count(SymRows R, uint8_t* __res
     uint32_t n = 0;
     for (uint32_t e = lane; e < fl; e += 32) {
       const uint32_t b = R.fwd_b[fo + e], sv = R.fwd_s[fo + e];
-      const unsigned long long w = R.symbest[(size_t)b * R.n_genomes + ga];
+      const unsigned long long w = R.symbest[(size_t)ga * R.n_genes + b];
       const bool f = ratio_equal(sv, La + R.La[b] - sv, (uint32_t)(w >> 48), (uint32_t)(w >> 31) & 0x1FFFFu);
       flag[fo + e] = f ? 1 : 0;
       n += f ? 1u : 0u;
@@ -216,7 +215,7 @@ cudaError_t run_sym_count(Launcher* L, const SymRows& R, uint32_t* stored, uint3
                           uint32_t* total, cudaStream_t s) {
   cudaError_t e = launch_begin(L, "sym_count");
   if (e != cudaSuccess) return e;
-  k_sym_count<<<grid_of((uint64_t)R.n_genes * 32, 256, 152u * 16u), 256, 0, s>>>(R, stored);
+  k_sym_count<<<grid_of((uint64_t)R.n_genes, 256, 152u * 16u), 256, 0, s>>>(R, stored);
   if ((e = launch_end(L, "sym_count")) != cudaSuccess) return e;
   if (R.n_ties) {
     if ((e = launch_begin(L, "sym_ties")) != cudaSuccess) return e;
@@ -231,8 +230,11 @@ cudaError_t run_sym_count(Launcher* L, const SymRows& R, uint32_t* stored, uint3
 cudaError_t run_sym_write(Launcher* L, const SymRows& R, const uint32_t* stored, const uint32_t* tiecnt,
                           const uint8_t* tie_ok, const unsigned long long* row_ptr, uint32_t* tie_fill,
                           uint32_t* out_b, uint32_t* out_s, cudaStream_t s) {
-  cudaError_t e = launch_begin(L, "sym_write");
+  cudaError_t e = launch_begin(L, "sym_write_rev");
   if (e != cudaSuccess) return e;
+  k_sym_write_rev<<<grid_of((uint64_t)R.n_genes, 256, 152u * 16u), 256, 0, s>>>(R, row_ptr, out_b, out_s);
+  if ((e = launch_end(L, "sym_write_rev")) != cudaSuccess) return e;
+  if ((e = launch_begin(L, "sym_write")) != cudaSuccess) return e;
   k_sym_write<<<grid_of((uint64_t)R.n_genes * 32, 256, 152u * 16u), 256, 0, s>>>(R, stored, tiecnt, row_ptr, out_b,
                                                                                  out_s);
   if ((e = launch_end(L, "sym_write")) != cudaSuccess) return e;

@@ -919,7 +919,9 @@ static pd_status sym_hits_impl(pd_ctx* c, const pd_profiles* P, pd_hits* H) {
     ALLOC(ties, 2 * sizeof(unsigned long long) * tie_cap);
     pdg::QuerySet Q{};  // run_hits clears the maxima and the tie count before each launch
     Q.all_pairs = 1;
-    Q.order = v.order;
+    // queries in gene order, i.e. genome by genome: the reverse maxima of the
+    // query genome in flight (its slice of the genome-major array) stay in L2
+    Q.order = nullptr;
     Q.q0 = 0;
     Q.n_queries = G;
     Q.symbest = symbest.as<unsigned long long>();

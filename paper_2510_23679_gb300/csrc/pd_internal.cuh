@@ -229,7 +229,7 @@ struct QuerySet {
   // Symmetric all-pairs form (symbest not null): each unordered genome pair is
   // walked from one side.  Query a walks only the targets in genomes after its
   // own; for every candidate b it keeps the best (s, den, a) of b over a's
-  // genome at symbest[b * n_genomes + genome(a)] -- the reverse-direction
+  // genome at symbest[genome(a) * n_genes + b] -- the reverse-direction
   // maximum, packed s << 48 | den << 31 | a -- and lists exact ties of that
   // maximum as the pair of words (b << 32 | a, s) in tie_rec (tie_cap pairs;
   // the count keeps counting past it).
@@ -409,7 +409,7 @@ struct SymRows {
   uint32_t n_genes, n_genomes;
   const uint16_t* gene_genome;
   const uint32_t* La;
-  const unsigned long long* symbest;  // [n_genes * n_genomes]
+  const unsigned long long* symbest;  // [n_genomes * n_genes], genome-major: b over genome g at g * n_genes + b
   const unsigned long long* tie_rec;  // [2 * n_ties]: (b << 32 | a), s
   unsigned long long n_ties;
   unsigned long long* tie_set;        // [tie_set_mask + 1] all-ones: the pairs already counted
