@@ -93,6 +93,44 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// The same through shared memory, for datasets of at most kRevTileGenomes
+// genomes: a block reads the maxima of 32 consecutive genes genome by genome
+// (coalesced) into a tile, then one warp per gene writes its row part
+// (coalesced).  Genes are numbered genome by genome, so the tile's last gene
+// has the largest genome of the 32.
+constexpr uint32_t kRevTileGenomes = 372;  // 372 x 33 x 8 bytes < 96 KB of shared memory
+__global__ void __launch_bounds__(256)
+    k_sym_write_rev_tile(SymRows R, const unsigned long long* __restrict__ row_ptr, uint32_t* __restrict__ out_b,
+                         uint32_t* __restrict__ out_s) {
+  extern __shared__ unsigned long long tile[];  // [genome][33]
+  const uint32_t lane = threadIdx.x & 31u, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+  for (uint32_t b0 = blockIdx.x * 32u; b0 < R.n_genes; b0 += gridDim.x * 32u) {
+    const uint32_t nb = min(32u, R.n_genes - b0);
+    const uint32_t gmax = R.gene_genome[b0 + nb - 1];
+    for (uint32_t g = warp; g < gmax; g += n_warps)
+      tile[g * 33u + lane] = lane < nb ? R.symbest[(size_t)g * R.n_genes + b0 + lane] : 0ull;
+    __syncthreads();
+    for (uint32_t j = warp; j < nb; j += n_warps) {
+      const uint32_t b = b0 + j, gb = R.gene_genome[b];
+      unsigned long long at = row_ptr[b];
+      for (uint32_t g0 = 0; g0 < gb; g0 += 32) {
+        const uint32_t g = g0 + lane;
+        const unsigned long long w = g < gb ? tile[g * 33u + j] : 0ull;
+        const uint32_t m = __ballot_sync(0xffffffffu, w != 0ull);
+        if (w != 0ull) {
+          uint32_t s, den, a;
+          unpack(w, &s, &den, &a);
+          const unsigned long long x = at + __popc(m & ((1u << lane) - 1u));
+          out_b[x] = a;
+          out_s[x] = s;
+        }
+        at += __popc(m);
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // One warp per gene: the forward part, after the stored maxima and room for
 // the gene's ties.
 __global__ void __launch_bounds__(256)
@@ -232,7 +270,15 @@ cudaError_t run_sym_write(Launcher* L, const SymRows& R, const uint32_t* stored,
                           uint32_t* out_b, uint32_t* out_s, cudaStream_t s) {
   cudaError_t e = launch_begin(L, "sym_write_rev");
   if (e != cudaSuccess) return e;
-  k_sym_write_rev<<<grid_of((uint64_t)R.n_genes, 256, 152u * 16u), 256, 0, s>>>(R, row_ptr, out_b, out_s);
+  if (R.n_genomes <= kRevTileGenomes) {
+    const size_t smem = (size_t)R.n_genomes * 33u * sizeof(unsigned long long);
+    if ((e = cudaFuncSetAttribute(k_sym_write_rev_tile, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+      return e;
+    k_sym_write_rev_tile<<<grid_of((uint64_t)R.n_genes, 32, 152u * 8u), 256, smem, s>>>(R, row_ptr, out_b, out_s);
+  } else {
+    k_sym_write_rev<<<grid_of((uint64_t)R.n_genes, 256, 152u * 16u), 256, 0, s>>>(R, row_ptr, out_b, out_s);
+  }
   if ((e = launch_end(L, "sym_write_rev")) != cudaSuccess) return e;
   if ((e = launch_begin(L, "sym_write")) != cudaSuccess) return e;
   k_sym_write<<<grid_of((uint64_t)R.n_genes * 32, 256, 152u * 16u), 256, 0, s>>>(R, stored, tiecnt, row_ptr, out_b,
