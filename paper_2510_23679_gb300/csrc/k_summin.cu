@@ -746,27 +746,35 @@ __global__ void __launch_bounds__(256) k_summin_global(ProfilesView P, QuerySet 
 // Tier 1 (packed 4096-slot table, several blocks per SM) and tier 2 (split
 // 16384-slot table, one 1024-thread block per SM) geometries.
 constexpr int kT1Threads = 256, kT1MinBlocks = 6;
-// Two tier-1 layouts, chosen per launch.  The compact one keeps six blocks
+// Three tier-1 layouts, chosen per launch.  The compact one keeps six blocks
 // within the 164 KB shared-memory carveout of an SM, which leaves 92 KB of
 // the SM's 256 KB as L1 for the posting loads of the walk (with 4 KB more per
 // block the carveout steps up to 196 KB and L1 shrinks to 60 KB): at most 3072
 // listed occupied slots and 448 hits per query, a query beyond either moving
-// to tier 2.  Past kT1CompactGenomes target genomes the per-genome maxima no
-// longer leave room for that, and the full layout (4096 slots listed, 512
-// hits) defers fewer of the longer Best Hit rows of many-genome datasets.
+// to tier 2.  Past kT1CompactGenomes target genomes the per-genome maxima (12
+// bytes each) no longer leave room for that; the middle layout lists at most
+// 2048 occupied slots and 384 hits and stays within 164 KB up to
+// kT1MidGenomes genomes; past that the full layout (4096 slots listed, 512
+// hits) takes the 196 KB carveout.
 constexpr uint32_t kT1Cap = 4096, kT1OutEmit = 3072;
 constexpr uint32_t kT1Out = 448, kT1Used = 3072;          // compact layout
 constexpr uint32_t kT1OutFull = 512, kT1UsedFull = 4096;  // full layout
+constexpr uint32_t kT1UsedMid = 2048, kT1OutMid = 384;    // middle layout
 constexpr int kT2Threads = 1024;
 constexpr uint32_t kT2Cap = 16384, kT2Out = 2048, kT2OutEmit = 4096;
 using T1 = SmemTier<kT1Threads, kT1Cap, kT1Out, true, false, kT1Used>;
 using T1F = SmemTier<kT1Threads, kT1Cap, kT1OutFull, true, false, kT1UsedFull>;
+using T1M = SmemTier<kT1Threads, kT1Cap, kT1OutMid, true, false, kT1UsedMid>;
 using T1E = SmemTier<kT1Threads, kT1Cap, kT1OutEmit, true, false, kT1Used>;
 // genomes up to which six compact blocks (with their static scalars and the
 // 1 KB the runtime reserves per block) fit a 164 KB carveout
 constexpr uint32_t kT1CompactGenomes =
     (uint32_t)((164u * 1024u / kT1MinBlocks - 1024u - sizeof(Scalars) - T1::kTable - T1::kUnion - 4u) / 12u);
 static_assert(kT1CompactGenomes >= 50, "compact tier-1 layout holds tens of genomes");
+// ... and six middle-layout blocks (a shorter occupied-slot list)
+constexpr uint32_t kT1MidGenomes =
+    (uint32_t)((164u * 1024u / kT1MinBlocks - 1024u - sizeof(Scalars) - T1M::kTable - T1M::kUnion - 4u) / 12u);
+static_assert(kT1MidGenomes >= 200, "middle tier-1 layout holds hundreds of genomes");
 using T2 = SmemTier<kT2Threads, kT2Cap, kT2Out, false>;
 using T2E = SmemTier<kT2Threads, kT2Cap, kT2OutEmit, false>;
 static_assert(T1F::bytes(PD_MAX_GENOMES) <= 227 * 1024, "tier 1 shared memory");
@@ -819,12 +827,18 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
     e = n_best <= kT1CompactGenomes
             ? launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false, false, kT1Used>, L,
                           "summin_bh", kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s)
+        : n_best <= kT1MidGenomes
+            ? launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutMid, true, false, false, kT1UsedMid>, L,
+                          "summin_bh", kT1Threads, T1M::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s)
             : launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutFull, true, false, false, kT1UsedFull>,
                           L, "summin_bh", kT1Threads, T1F::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   else  // long lists: warp-cooperative walk
     e = n_best <= kT1CompactGenomes
             ? launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false, false, kT1Used, true>,
                           L, "summin_bh", kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s)
+        : n_best <= kT1MidGenomes
+            ? launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutMid, true, false, false, kT1UsedMid, true>,
+                          L, "summin_bh", kT1Threads, T1M::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s)
             : launch_smem(
                   k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutFull, true, false, false, kT1UsedFull, true>, L,
                   "summin_bh", kT1Threads, T1F::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
