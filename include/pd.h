@@ -222,7 +222,9 @@ pd_status pd_ctx_set_symmetric(pd_ctx* ctx, int enable);
  * consecutive postings, batches of four) or by the warp-cooperative walk
  * (each warp 32 consecutive postings per round; suits long lists).
  * PD_WALK_AUTO (the default) takes the warp walk when the build's join
- * (pd_profiles_info.n_join) is at least 16 postings per vector entry.
+ * (pd_profiles_info.n_join) is at least 16 postings per vector entry and the
+ * postings take at least 512 MB (smaller indexes stay close enough to L2
+ * for the merge-path walk).
  * Applies to every later Best Hit call on the context.  Errors: PD_ERR_ARG
  * (null context, unknown mode). */
 #define PD_WALK_AUTO 0u

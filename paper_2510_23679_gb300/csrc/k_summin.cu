@@ -237,6 +237,10 @@ struct Chunk {
 // sectors it has already loaded.
 constexpr uint32_t kRounds = 4;
 constexpr uint32_t kWarpWalkMinAvg = 16;
+// ... and the smallest index (4-byte postings) for which the warp walk is
+// taken: below a few L2 sizes the merge-path walk's runs of postings keep
+// hitting the sectors they have already brought in.
+constexpr uint64_t kWarpWalkMinIndexBytes = 512ull << 20;
 // Target genomes from which a query's Best Hits are ranked through per-genome
 // positions rather than pairwise.
 constexpr uint32_t kRankByGenomeMin = 64;
@@ -823,7 +827,8 @@ cudaError_t run_summin_tiers(Launcher* L, const ProfilesView& P, const QuerySet&
     e = launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1OutEmit, true, true, false, kT1Used>, L, "summin_pairs",
                     kT1Threads, T1E::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s);
   else if (Q.walk == PD_WALK_MERGE ||
-           (Q.walk != PD_WALK_WARP && P.n_join < (uint64_t)kWarpWalkMinAvg * P.n_entries))  // short lists: merge-path walk
+           (Q.walk != PD_WALK_WARP && (P.n_join < (uint64_t)kWarpWalkMinAvg * P.n_entries ||
+                                       P.n_entries * 4ull < kWarpWalkMinIndexBytes)))  // merge-path walk
     e = n_best <= kT1CompactGenomes
             ? launch_smem(k_summin_smem<kT1Threads, kT1MinBlocks, kT1Cap, kT1Out, true, false, false, kT1Used>, L,
                           "summin_bh", kT1Threads, T1::bytes(n_best), Q.n_queries, P, Q, O, t1, err, s)
