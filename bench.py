@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--no-per-pair", action="store_true", help="skip the one-pair-per-launch comparison")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--walk", default="auto", choices=["auto", "merge", "warp"],
+                    help="posting walk of the sum-min kernel (pd_ctx_set_walk); same results")
     ap.add_argument("--no-served", action="store_true",
                     help="skip the genome-add latency probe of the plain workload's line")
     ap.add_argument("--served-rate", type=float, default=20.0,
@@ -678,6 +680,7 @@ def main():
     alpha = alphabet_of(args.workload)
     k = pd.pd_choose_k(ds.n_residues, alpha)
     ctx = pd.pd_ctx_create(local)
+    pd.pd_ctx_set_walk(ctx, {"auto": pd.PD_WALK_AUTO, "merge": pd.PD_WALK_MERGE, "warp": pd.PD_WALK_WARP}[args.walk])
     stream = torch.cuda.current_stream(dev)
 
     res_d = torch.from_numpy(ds.residues).to(dev)
@@ -888,7 +891,8 @@ def main():
             "metric": "gene-pair GJ evals/s", "value": value, "unit": "gene-pairs/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": config_of(ds, args.workload, k, L2_NOTE, parallelism_of(world, "replicas")),
+            "config": dict(config_of(ds, args.workload, k, L2_NOTE, parallelism_of(world, "replicas")),
+                           **({} if args.walk == "auto" else {"walk": args.walk})),
             "genome_pairs_per_s": genome_pairs_all / (ms_per_step / 1e3),
             "step_ms": step_ms,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
