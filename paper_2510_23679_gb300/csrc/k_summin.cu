@@ -72,6 +72,10 @@ struct Acc {
   uint32_t* vpb;   // filtered only: sum of mult_b over the shared k-mers (b -> a)
   uint32_t cnt_bits;
   uint32_t hash_shift;  // 32 - log2(cap)
+  // Target genes [dense_lo, dense_lo + cap) of a query whose targets fit the
+  // table: slot = gene - dense_lo (direct, the first probe always lands);
+  // kEmpty: hashed slots.
+  uint32_t dense_lo;
 
   __device__ __forceinline__ void bump(uint32_t h, uint32_t m, uint32_t ca, uint32_t cb) const {
     atomicAdd(&vals[h], m);
@@ -81,7 +85,10 @@ struct Acc {
     }
   }
 
-  __device__ __forceinline__ uint32_t home(uint32_t key) const { return (key * 0x9E3779B1u) >> hash_shift; }
+  __device__ __forceinline__ uint32_t home(uint32_t key) const {
+    if (dense_lo != kEmpty) return (kPacked ? key >> cnt_bits : key) - dense_lo;
+    return (key * 0x9E3779B1u) >> hash_shift;
+  }
 
   // key: bkey (packed) or b (split).  Returns false after kMaxProbe probes.
   // ca, cb (the two multiplicities) feed the directional sums of filtered queries.
@@ -266,7 +273,7 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
                                               const Table<TIdx>& tb, uint32_t* c_post, uint32_t* c_off,
                                               uint16_t* c_cnt, unsigned long long* best, Scalars* sh) {
   constexpr uint32_t kChunk = Chunk<kThreads>::kSize, kItems = Chunk<kThreads>::kItems;
-  const Acc<kPacked, kFilter> acc{tb.keys, tb.vals, tb.vpa, tb.vpb, P.cnt_bits, 32u - (31u - (uint32_t)__clz(tb.cap))};
+  Acc<kPacked, kFilter> acc{tb.keys, tb.vals, tb.vpa, tb.vpb, P.cnt_bits, 32u - (31u - (uint32_t)__clz(tb.cap)), kEmpty};
   uint16_t* c_ent = c_cnt + Chunk<kThreads>::kSize;  // chunk entry of each staged k-mer
   unsigned long long* out = tb.out;
   const uint32_t mask = tb.cap - 1u;
@@ -314,6 +321,11 @@ __device__ __forceinline__ void process_query(uint32_t qi, const ProfilesView& P
     row = qi;
     key_lo = (unsigned long long)tlo << P.cnt_bits;
     key_hi = (unsigned long long)thi << P.cnt_bits;
+  }
+  // one target range that fits the table: direct slots instead of hashing
+  if (!Q.all_pairs) {
+    const uint32_t tlo = (uint32_t)(key_lo >> P.cnt_bits), thi = (uint32_t)(key_hi >> P.cnt_bits);
+    if (thi > tlo && thi - tlo <= tb.cap) acc.dense_lo = tlo;
   }
   // the query's own vector (its dataset's, or the external query arrays)
   const bool ext = P.q_win_off != nullptr;
