@@ -17,7 +17,7 @@ def decode_code(code: int, k: int) -> bytes:
     return bytes(out)
 
 
-class GpuRun:
+class DeviceRun:
     """One dataset profiled on the GPU (device handles kept for queries)."""
 
     def __init__(self, ctx, ds, k, device_inputs=False):

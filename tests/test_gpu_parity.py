@@ -15,7 +15,7 @@ import pytest
 import oracle
 from paper_2510_23679_gb300 import pd, synth
 from tests import _golden
-from tests._gpu import GpuRun, all_pairs_row_slice, csr_lists, oracle_nonzero, oracle_pairs
+from tests._gpu import DeviceRun, all_pairs_row_slice, csr_lists, oracle_nonzero, oracle_pairs
 
 pytestmark = pytest.mark.gpu
 
@@ -34,7 +34,7 @@ def pan4(ctx):
     ds = synth.workload("pan4x250")
     k = oracle.choose_k(ds.n_residues)
     assert k == 5
-    run = GpuRun(ctx, ds, k)
+    run = DeviceRun(ctx, ds, k)
     pairs = list(itertools.permutations(range(ds.n_genomes), 2))
     return run, oracle_pairs(ds, k, pairs, n_threads=4)
 
@@ -44,7 +44,7 @@ def pan4(ctx):
 def test_golden_on_gpu(ctx, fname):
     g = _golden.load(fname)
     ds = synth.from_strings([g.rows, g.cols])
-    run = GpuRun(ctx, ds, g.k)
+    run = DeviceRun(ctx, ds, g.k)
     want = {(a, b): s for a, row in enumerate(g.S) for b, (s, _) in enumerate(row) if s > 0}
     assert run.summin(0, 1) == want
     rows, _ = run.best_hits(0, 1)
@@ -138,7 +138,7 @@ def test_all_pairs_is_deterministic(pan4):
 
 def test_device_inputs_match_host_inputs(pan4, ctx):
     run, _ = pan4
-    dev = GpuRun(ctx, run.ds, run.k, device_inputs=True)
+    dev = DeviceRun(ctx, run.ds, run.k, device_inputs=True)
     for x, y in zip(run.all_pairs()[:4], dev.all_pairs()[:4]):
         assert np.array_equal(x, y)
 
@@ -149,7 +149,7 @@ def test_device_inputs_match_host_inputs(pan4, ctx):
 def test_tiny_random_against_oracle(ctx, seed, k):
     letters = [b"AC", b"ACD", b"ACDEFGHIKL", synth.ALPHABET][seed % 4]
     ds = synth.random_tiny(1000 + seed * 3 + k, n_genomes=3, max_genes=7, max_len=40, letters=letters)
-    run = GpuRun(ctx, ds, k)
+    run = DeviceRun(ctx, ds, k)
     pairs = list(itertools.permutations(range(ds.n_genomes), 2))
     ref = oracle_pairs(ds, k, pairs)
     for (gi, gj), R in ref.items():
@@ -165,7 +165,7 @@ def test_tiny_random_against_oracle(ctx, seed, k):
 
 def test_empty_genes_and_genomes(ctx):
     ds = synth.from_strings([[b"", b"ACDEF", b"A"], [], [b"ACDEG", b""], [b"CDEF"]])
-    run = GpuRun(ctx, ds, 3)
+    run = DeviceRun(ctx, ds, 3)
     ref = oracle_pairs(ds, 3, [(0, 2), (2, 0), (0, 3), (2, 3)])
     for (gi, gj), R in ref.items():
         assert run.summin(gi, gj) == oracle_nonzero(R)
@@ -177,7 +177,7 @@ def test_empty_genes_and_genomes(ctx):
 
 def test_k_equal_to_gene_length(ctx):
     ds = synth.from_strings([[b"ACDEFGHIKL", b"ACDEFGHIKM"], [b"ACDEFGHIKL", b"ACDEFGHIK"]])
-    run = GpuRun(ctx, ds, 8)
+    run = DeviceRun(ctx, ds, 8)
     ref = oracle_pairs(ds, 8, [(0, 1)])[(0, 1)]
     assert run.summin(0, 1) == oracle_nonzero(ref)
     assert run.bbh(0, 1) == [tuple(x) for x in ref.bbh.tolist()]
@@ -197,7 +197,7 @@ def test_errors_are_reported(ctx):
     with pytest.raises(pd.PdError) as e:
         pd.pd_build_profiles(ctx, long.residues, long.gene_ptr, long.genome_ptr, 1)
     assert e.value.status == 3
-    run = GpuRun(ctx, ok, 2)
+    run = DeviceRun(ctx, ok, 2)
     with pytest.raises(pd.PdError) as e:
         pd.pd_best_hits(ctx, run.prof, 0, 0)
     assert e.value.status == 1
@@ -212,7 +212,7 @@ def test_accumulator_overflow_takes_the_large_path(ctx):
     letters = np.frombuffer(b"FGHIKLMNPQRSTVWY", np.uint8)
     targets = [b"AC" + rng.choice(letters, size=6).tobytes() for _ in range(5000)]
     ds = synth.from_strings([[b"ACDE", b"GGGG"], targets])
-    run = GpuRun(ctx, ds, 2)
+    run = DeviceRun(ctx, ds, 2)
     R = oracle_pairs(ds, 2, [(0, 1)])[(0, 1)]
     assert run.summin(0, 1) == oracle_nonzero(R)
     rows, _ = run.best_hits(0, 1)
@@ -228,7 +228,7 @@ def test_saturated_posting_counts_and_long_genes(ctx):
     # long one-letter genes exceed it, so the exact count is looked up.
     n_empty = 70000
     ds = synth.from_strings([[b"A" * 20000] + [b""] * n_empty, [b"A" * 17000 + b"C"] + [b""] * n_empty])
-    run = GpuRun(ctx, ds, 1)
+    run = DeviceRun(ctx, ds, 1)
     assert run.info.count_bits == 14
     pair = synth.from_strings([[b"A" * 20000], [b"A" * 17000 + b"C"]])
     prof = oracle.Profiles(pair.residues, pair.gene_ptr, 1)
@@ -253,7 +253,7 @@ def test_saturated_count_in_a_gene_with_many_kmers(ctx, letter):
     target = sat * 20000 + tail * 3
     query = sat * 17000 + other
     ds = synth.from_strings([[query] + [b""] * n_empty, [target] + [b""] * n_empty])
-    run = GpuRun(ctx, ds, 1)
+    run = DeviceRun(ctx, ds, 1)
     assert run.info.count_bits == 14
     pair = synth.from_strings([[query], [target]])
     prof = oracle.Profiles(pair.residues, pair.gene_ptr, 1)
@@ -386,7 +386,7 @@ def test_occupied_list_and_hit_list_bounds(ctx, n_targets, n_tied):
         extra = 6 if t < n_tied else 7 + int(rng.integers(0, 20))
         targets.append(b"AC" + rng.choice(letters, size=extra).tobytes())
     ds = synth.from_strings([[b"ACDE", b"GGGG"], targets])
-    run = GpuRun(ctx, ds, 2)
+    run = DeviceRun(ctx, ds, 2)
     R = oracle_pairs(ds, 2, [(0, 1)])[(0, 1)]
     rows, _ = run.best_hits(0, 1)
     assert rows == csr_lists(R.row_ptr, R.row_col)
@@ -404,7 +404,7 @@ def test_both_tier1_layouts_against_oracle(ctx, n_genomes):
                         length_dist=("uniform", 40, 160), core_frac=0.5, accessory_draw=None, subst_max=0.2,
                         indel_max=0.03, paralog_frac=0.1, singleton_frac=0.05, seed=11)
     k = 3
-    run = GpuRun(ctx, ds, k)
+    run = DeviceRun(ctx, ds, k)
     rp, cols, s, bbh, info = run.all_pairs()
     for gi, gj in [(0, 1), (n_genomes - 1, 0), (37, n_genomes - 2)]:
         R = oracle.pair_for_dataset(ds, gi, gj, k)
