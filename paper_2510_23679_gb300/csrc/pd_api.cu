@@ -254,12 +254,6 @@ PD_API int pd_choose_k(uint64_t total, int alphabet) {
 }
 
 // ------------------------------------------------------------------ profiles
-static uint32_t ceil_log2_u64(uint64_t x) {
-  uint32_t b = 0;
-  while (b < 64 && ((uint64_t)1 << b) < x) ++b;
-  return b;
-}
-
 // Most codes a segmented dataset's dictionary may cover (segments x 20^k): one
 // bit each, 4 GiB of bits (4.6 GiB of rank blocks).
 static constexpr uint64_t kMaxDictCodes = (uint64_t)32 << 30;
