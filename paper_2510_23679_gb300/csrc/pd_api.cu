@@ -984,6 +984,7 @@ static pd_status sym_hits_impl(pd_ctx* c, const pd_profiles* P, pd_hits* H) {
     st = check_dev_err(c);  // synchronizes: the forward rows and the tables end here
     if (st != PD_OK) return st;
     H->has_bbh = true;
+    H->csr = true;
     H->n_bbh = n_bbh;
     H->row_off = std::move(row_ptr);
     H->row_len = std::move(total);
@@ -1227,6 +1228,15 @@ PD_API pd_status pd_hits_copy(pd_ctx* c, const pd_hits* H, int64_t* row_ptr, int
   try {
     CK(cudaSetDevice(c->device));
     const uint32_t n_rows = H->all_pairs ? H->n_rows : H->nA;
+    if (H->csr) {  // rows assembled in order already: copy them as they are
+      pd_status st = PD_OK;
+      if (n_hits) *n_hits = H->n_hits;
+      if ((st = copy_out(c, row_ptr, H->row_off.p, sizeof(int64_t) * (n_rows + 1))) != PD_OK) return st;
+      if ((st = copy_out(c, cols, H->out_b.p, sizeof(int32_t) * H->n_hits)) != PD_OK) return st;
+      if ((st = copy_out(c, s, H->out_s.p, sizeof(uint32_t) * H->n_hits)) != PD_OK) return st;
+      CK(cudaStreamSynchronize(c->stream));
+      return PD_OK;
+    }
     Buf rp, cb, sb;
     uint64_t n = 0;
     pd_status st = hits_to_csr(c, H, n_rows, H->all_pairs ? 0 : H->col_base, rp, cb, sb, &n);

@@ -224,8 +224,11 @@ struct pd_hits {
   uint64_t n_hits = 0, walked = 0;
   uint32_t n_deferred = 0;
   Buf row_off, row_len, out_b, out_s;
-  // the symmetric all-pairs form finds the BBH pairs with the rows
+  // the symmetric all-pairs form finds the BBH pairs with the rows, and its
+  // rows are already one CSR: row_off holds n_rows + 1 offsets into
+  // out_b / out_s, in row order
   bool has_bbh = false;
+  bool csr = false;
   uint64_t n_bbh = 0;
   Buf bbh_a, bbh_b;
 };
