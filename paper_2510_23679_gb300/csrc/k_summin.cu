@@ -4,15 +4,20 @@
 // One thread block owns one query gene a at a time:
 //   1. stage a chunk of a's multiplicity vector in shared memory: for each
 //      k-mer its multiplicity and posting range (stored with the vector, so
-//      this read is coalesced; in the pair form the range is narrowed by
-//      binary search to the target genome), and a block prefix sum of the
-//      range lengths: the chunk's postings form one flat index space;
-//   2. merge-path walk: thread t takes the flat range [t*P, (t+1)*P), finds
-//      its first k-mer by one binary search and then advances sequentially;
-//      postings are loaded in batches of four before any is used; each
-//      posting (b, mult_b) adds min(mult_a, mult_b) to b's accumulator in an
-//      open-addressing hash.  After all chunks acc[b] = s(a, b), the Eq. (5)
-//      numerator, exactly;
+//      this read is coalesced; in the pair forms the range is narrowed by
+//      binary search to the target genome, in the symmetric all-pairs form to
+//      the genomes after a's own), and a block prefix sum of the range
+//      lengths: the chunk's postings form one flat index space;
+//   2. walk the postings, one of two ways chosen per launch: the merge-path
+//      walk (thread t takes the flat range [t*P, (t+1)*P), finds its first
+//      k-mer by one binary search and advances sequentially, four postings
+//      loaded before any is used) or the warp-cooperative walk (each warp
+//      reads 32 consecutive flat positions per round, the k-mer of each lane
+//      found from the staged list starts by a warp OR-reduction); each
+//      posting (b, mult_b) adds min(mult_a, mult_b) to b's accumulator in
+//      shared memory: an open-addressing hash, or direct slots when the
+//      query's targets are one gene range that fits the table.  After all
+//      chunks acc[b] = s(a, b), the Eq. (5) numerator, exactly;
 //   3. Best Hits: per target genome the maximum ratio s / (La + Lb - s) is
 //      kept as an (s, den) pair updated by compare-and-swap under a 64-bit
 //      cross-multiplication order; every accumulator whose ratio equals its
@@ -21,6 +26,9 @@
 //      table is clean for the next query.  Each hit is written at its rank
 //      among the query's hits (ascending gene): rows come out sorted without a
 //      sorting network.
+// In the symmetric all-pairs form each candidate b also keeps, in global
+// memory, its best ratio over a's genome (the column maximum of Algorithm 3,
+// with exact ties listed), from which k_sym.cu assembles the reverse rows.
 // Served queries (new genomes against a resident set) may limit the targets
 // to genes below a bound, and may also keep each target's best ratio over the
 // query's genome in global memory (the reverse-direction maximum needed for
@@ -28,9 +36,8 @@
 // The similarity matrix S_ij is never materialised: only pairs sharing a
 // k-mer are touched.  A query whose insertions probe too far (a nearly full
 // table), or whose Best Hit list does not fit, is deferred to the next tier:
-// 4096 slots
-// in shared memory (256 threads) -> 16384 slots in shared memory (1024
-// threads, one block per SM) -> a global-memory table sized for every
+// 4096 slots in shared memory (256 threads) -> 16384 slots in shared memory
+// (1024 threads, one block per SM) -> a global-memory table sized for every
 // possible target.  Results are exact and independent of the tier.
 #include <algorithm>
 
